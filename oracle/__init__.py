@@ -1,0 +1,286 @@
+"""CPU oracle for the k-NN graph method of arXiv:1307.7852 (Wang et al.).
+
+TEST INFRASTRUCTURE.  This package is the plain, slow reference that the CUDA
+path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it; the library in
+``paper_1307_7852_gb300`` never does, and the two share no code.
+
+The arithmetic lives in ``knng_oracle.c`` (plain C, FP64 distances, compiled
+with ``-ffp-contract=off``); this module compiles it with gcc, loads it with
+ctypes and composes the stages in the order of the paper:
+
+* ``partition``   -- one random partition tree (Sec. 3.1; App. after Lemma 1)
+* ``leaf_knn``    -- brute force inside every leaf (Sec. 3.1)
+* ``merge``       -- union of the T base graphs, k nearest kept (Sec. 3.1)
+* ``propagate``   -- one first-order propagation round (Sec. 3.2, Theorem 1)
+* ``knn_exact``   -- exact k-NN lists by brute force (Def. 1; Sec. 4)
+* ``build_graph`` -- the whole method: T trees, merge, R rounds
+
+Inputs of dtype float16 are widened to float32 first (exact).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "knng_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile knng_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i64, i32, u32, u64 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+            lib.orc_philox4x32_10.argtypes = [P, P, P]
+            lib.orc_direction.argtypes = [u64, u32, u32, u32, i32, P]
+            lib.orc_project.argtypes = [P, P, i32]
+            lib.orc_project.restype = ctypes.c_float
+            lib.orc_ord.argtypes = [ctypes.c_float]
+            lib.orc_ord.restype = u32
+            lib.orc_leaf_count.argtypes = [i64, i32]
+            lib.orc_leaf_count.restype = i64
+            lib.orc_partition.argtypes = [P, i64, i32, i64, u64, u32, i32, P, P]
+            lib.orc_leaf_knn.argtypes = [P, i64, i32, i64, P, P, i64, i32, P, P]
+            lib.orc_leaf_knn_quant.argtypes = [P, i64, i32, i64, P, P, P, i64, i32, i32, P, P]
+            lib.orc_merge.argtypes = [P, i64, i32, i64, i32, i32, P, P, P]
+            lib.orc_propagate.argtypes = [P, i64, i32, i64, i32, P, P, P]
+            lib.orc_knn_exact.argtypes = [P, i64, i32, i64, i32, P, i64, P, P]
+            lib.orc_pair_dist.argtypes = [P, i32, i64, P, P, i64, P]
+            lib.orc_bf16_round.argtypes = [ctypes.c_float]
+            lib.orc_bf16_round.restype = ctypes.c_float
+            lib.orc_e4m3_round.argtypes = [ctypes.c_float]
+            lib.orc_e4m3_round.restype = ctypes.c_float
+            lib.orc_quantize_rows.argtypes = [P, i64, i32, i64, i32, P, P]
+            lib.orc_num_threads.restype = i32
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _as_f32(X) -> np.ndarray:
+    X = np.asarray(X)
+    if X.dtype == np.float16:
+        X = X.astype(np.float32)
+    return np.ascontiguousarray(X, dtype=np.float32)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+# --------------------------------------------------------------------- RNG --
+def philox4x32_10(ctr, key) -> np.ndarray:
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def direction(seed: int, t: int, level: int, node: int, d: int) -> np.ndarray:
+    lib = _load()
+    a = np.zeros(d, dtype=np.float32)
+    lib.orc_direction(seed, t, level, node, d, _ptr(a))
+    return a
+
+
+def project(x, a) -> np.float32:
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    assert x.shape == a.shape
+    return np.float32(lib.orc_project(_ptr(x), _ptr(a), x.shape[0]))
+
+
+def ord32(f: float) -> int:
+    return int(_load().orc_ord(float(np.float32(f))))
+
+
+# --------------------------------------------------------------- partition --
+def leaf_count(n: int, g: int) -> int:
+    return int(_load().orc_leaf_count(n, g))
+
+
+def partition(X, seed: int, t: int, g: int):
+    """Canonical leaf set of tree t: (perm int32[n], leaf_off int64[L+1])."""
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    perm = np.zeros(n, dtype=np.int32)
+    off = np.zeros(leaf_count(n, g) + 1, dtype=np.int64)
+    lib.orc_partition(_ptr(X), n, d, d, seed, t, g, _ptr(perm), _ptr(off))
+    return perm, off
+
+
+# -------------------------------------------------------------- leaf graph --
+def leaf_knn(X, perm, leaf_off, k: int):
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    leaf_off = np.ascontiguousarray(leaf_off, dtype=np.int64)
+    ids = np.empty((n, k), dtype=np.int32)
+    dists = np.empty((n, k), dtype=np.float32)
+    lib.orc_leaf_knn(_ptr(X), n, d, d, _ptr(perm), _ptr(leaf_off), leaf_off.shape[0] - 1, k,
+                     _ptr(ids), _ptr(dists))
+    return ids, dists
+
+
+def quantize_rows(X, precision: int):
+    """Dequantised FP64 rows and per-row scales of the candidate-stage input."""
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    Xq = np.empty((n, d), dtype=np.float64)
+    sc = np.empty(n, dtype=np.float32)
+    lib.orc_quantize_rows(_ptr(X), n, d, d, int(precision), _ptr(Xq), _ptr(sc))
+    return Xq, sc
+
+
+def leaf_knn_quant(X, perm, leaf_off, k: int, kprime: int, precision: int):
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    Xq, _ = quantize_rows(X, precision)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    leaf_off = np.ascontiguousarray(leaf_off, dtype=np.int64)
+    ids = np.empty((n, k), dtype=np.int32)
+    dists = np.empty((n, k), dtype=np.float32)
+    lib.orc_leaf_knn_quant(_ptr(X), n, d, d, _ptr(Xq), _ptr(perm), _ptr(leaf_off),
+                           leaf_off.shape[0] - 1, k, kprime, _ptr(ids), _ptr(dists))
+    return ids, dists
+
+
+def bf16_round(x: float) -> np.float32:
+    return np.float32(_load().orc_bf16_round(float(np.float32(x))))
+
+
+def e4m3_round(x: float) -> np.float32:
+    return np.float32(_load().orc_e4m3_round(float(np.float32(x))))
+
+
+# ------------------------------------------------------ merge / propagate --
+def merge(X, lists, k: int):
+    """lists: int32 [T, n, k] ids (-1 empty) -> (ids, dists) [n, k]."""
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    lists = np.ascontiguousarray(lists, dtype=np.int32)
+    T = lists.shape[0]
+    assert lists.shape == (T, n, k)
+    ids = np.empty((n, k), dtype=np.int32)
+    dists = np.empty((n, k), dtype=np.float32)
+    lib.orc_merge(_ptr(X), n, d, d, T, k, _ptr(lists), _ptr(ids), _ptr(dists))
+    return ids, dists
+
+
+def propagate(X, ids_in, k: int):
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    ids_in = np.ascontiguousarray(ids_in, dtype=np.int32)
+    assert ids_in.shape == (n, k)
+    ids = np.empty((n, k), dtype=np.int32)
+    dists = np.empty((n, k), dtype=np.float32)
+    lib.orc_propagate(_ptr(X), n, d, d, k, _ptr(ids_in), _ptr(ids), _ptr(dists))
+    return ids, dists
+
+
+def knn_exact(X, k: int, queries=None):
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    q = np.arange(n, dtype=np.int32) if queries is None else np.ascontiguousarray(queries, dtype=np.int32)
+    ids = np.empty((q.shape[0], k), dtype=np.int32)
+    dists = np.empty((q.shape[0], k), dtype=np.float32)
+    lib.orc_knn_exact(_ptr(X), n, d, d, k, _ptr(q), q.shape[0], _ptr(ids), _ptr(dists))
+    return ids, dists
+
+
+def pair_dist(X, a, b) -> np.ndarray:
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    a = np.ascontiguousarray(a, dtype=np.int32).ravel()
+    b = np.ascontiguousarray(b, dtype=np.int32).ravel()
+    out = np.empty(a.shape[0], dtype=np.float64)
+    lib.orc_pair_dist(_ptr(X), d, d, _ptr(a), _ptr(b), a.shape[0], _ptr(out))
+    return out
+
+
+# ------------------------------------------------------------ whole method --
+def build_graph(X, k: int, T: int, g: int, R: int, seed: int,
+                precision: int = PREC_FP32, rescore_mult: int = 2):
+    """T random divisions, leaf graphs, merge, then R propagation rounds."""
+    X = _as_f32(X)
+    n = X.shape[0]
+    lists = np.empty((T, n, k), dtype=np.int32)
+    for t in range(T):
+        perm, off = partition(X, seed, t, g)
+        if precision == PREC_FP32:
+            lists[t], _ = leaf_knn(X, perm, off, k)
+        else:
+            lists[t], _ = leaf_knn_quant(X, perm, off, k, rescore_mult * k, precision)
+    ids, dists = merge(X, lists, k)
+    for _ in range(R):
+        ids, dists = propagate(X, ids, k)
+    return ids, dists
+
+
+# ------------------------------------------------------------------ recall --
+def recall(X, ids, k: int, sample, exact=None):
+    """Accuracy of Sec. 4 on a sample of points.
+
+    Returns (tie_tolerant, id_set): the first counts a returned neighbour j of
+    p when D(p, j) <= D_k(p), the k-th exact distance; the second is
+    |returned ids & exact ids| / k.  ``exact`` may pass precomputed
+    knn_exact(X, k, sample) output.
+    """
+    X = _as_f32(X)
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    if exact is None:
+        exact = knn_exact(X, k, sample)
+    e_ids, e_d = exact
+    got = np.asarray(ids)[sample]
+    a = np.repeat(sample, k)
+    b = got.ravel()
+    valid = b >= 0
+    dd = np.full(b.shape[0], np.inf)
+    if valid.any():
+        dd[valid] = pair_dist(X, a[valid], b[valid])
+    dd = dd.reshape(-1, k)
+    kth = np.array([pair_dist(X, [p], [e_ids[r, -1]])[0] for r, p in enumerate(sample)])
+    tie = float(np.mean(np.sum(dd <= kth[:, None], axis=1) / k))
+    idset = float(np.mean([len(set(got[r][got[r] >= 0]) & set(e_ids[r])) / k
+                           for r in range(len(sample))]))
+    return tie, idset

@@ -1,0 +1,527 @@
+/*
+ * CPU oracle for the k-NN graph construction of Wang, Wang, Zeng, Tu, Gan and
+ * Li, "Scalable k-NN graph construction" (arXiv:1307.7852).
+ *
+ * THIS FILE IS TEST INFRASTRUCTURE.  It is the plain, slow, obviously correct
+ * statement of what the GPU path computes.  Only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark may load it.  It shares no source
+ * with the CUDA library and includes none of its headers.
+ *
+ * Arithmetic: distances in FP64 (reported rounded to FP32).  The projection
+ * used to split a node is the one FP32 quantity that must match the GPU bit
+ * for bit, so it is written out in the fixed summation order that defines it
+ * (see orc_project).  Compile with -ffp-contract=off so that the compiler
+ * fuses nothing that is not written as fmaf.
+ *
+ * Where the paper is silent, the readings below are used (each is listed in
+ * the design doc of the repository):
+ *   - rho is the squared Euclidean distance (ranks like the Euclidean
+ *     distance of Def. 1; the square root is not taken).
+ *   - Ties are broken by point id: lists are ordered by (D, id) ascending.
+ *   - Random directions (App., after the proof of Lemma 1, which draws the
+ *     projection vector a at random) use Philox4x32-10 and a triangular law
+ *     on multiples of 2^-16 instead of a Gaussian, so that host and device
+ *     agree bit for bit without transcendental functions.
+ *   - A node is split at the median of the projections (App., after Lemma 1)
+ *     into the floor(m/2) smallest keys (left child 2v) and the rest (right
+ *     child 2v+1); the key is (ord(s) << 32 | id).  A node with m <= g is a
+ *     leaf (Sec. 3.1 stops at "smaller than g"; the leaf-size bound used here
+ *     is "at most g").
+ *   - Propagation (Sec. 3.2) is the first-order form analysed in Theorem 1:
+ *     one synchronous round replaces every list by the k best of its own
+ *     members and its neighbours' members.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10: Salmon, Moraes, Dror and Shaw, "Parallel random numbers:   */
+/* as easy as 1, 2, 3", SC'11.  Ten rounds of the 4x32 Philox S-box with the */
+/* published multipliers and Weyl key increments.                           */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Random direction of node v at level `level` of tree t (App., after the    */
+/* proof of Lemma 1: the projection vector a is drawn at random; one vector  */
+/* per node as in a random projection tree).  Entry j takes word j mod 4 of  */
+/* Philox(key = seed, counter = (t, level, v, j / 4)) and maps the 32-bit    */
+/* word u to ((u & 0xFFFF) + (u >> 16) - 65535) / 65536, a triangular value  */
+/* in (-1, 1) that FP32 holds exactly.                                       */
+/* ------------------------------------------------------------------------ */
+void orc_direction(uint64_t seed, uint32_t t, uint32_t level, uint32_t v, int d, float* a)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    for (int j = 0; j < d; ++j) {
+        uint32_t ctr[4] = {t, level, v, (uint32_t)(j / 4)};
+        uint32_t word[4];
+        orc_philox4x32_10(ctr, key, word);
+        uint32_t u = word[j % 4];
+        int32_t num = (int32_t)(u & 0xFFFFu) + (int32_t)(u >> 16) - 65535;
+        a[j] = (float)num / 65536.0f; /* exact: |num| < 2^17 */
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection s = a^T x in FP32, in the fixed order that defines it:         */
+/* 32 partial sums ("lanes"); lane l takes the entries j = 128c + 4l + e for */
+/* chunk c = 0, 1, ... and e = 0..3 (j < d), each as s_l = fmaf(x_j, a_j,    */
+/* s_l) starting from +0; then five pairwise rounds s_l <- s_l + s_(l xor o) */
+/* for o = 16, 8, 4, 2, 1.  The value of lane 0 is the projection.          */
+/* ------------------------------------------------------------------------ */
+float orc_project(const float* x, const float* a, int d)
+{
+    float s[32];
+    for (int l = 0; l < 32; ++l) s[l] = 0.0f;
+    int nchunks = (d + 127) / 128;
+    for (int l = 0; l < 32; ++l)
+        for (int c = 0; c < nchunks; ++c)
+            for (int e = 0; e < 4; ++e) {
+                int j = 128 * c + 4 * l + e;
+                if (j < d) s[l] = fmaf(x[j], a[j], s[l]);
+            }
+    for (int o = 16; o >= 1; o >>= 1) {
+        float nxt[32];
+        for (int l = 0; l < 32; ++l) nxt[l] = s[l] + s[l ^ o];
+        for (int l = 0; l < 32; ++l) s[l] = nxt[l];
+    }
+    return s[0];
+}
+
+/* Order-preserving map of an FP32 value to an unsigned 32-bit integer:      */
+/* sign bit clear -> set the sign bit; sign bit set -> invert every bit.     */
+uint32_t orc_ord(float f)
+{
+    uint32_t b;
+    memcpy(&b, &f, sizeof b);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Distances and (D, id) ordering.                                          */
+/* ------------------------------------------------------------------------ */
+static double sqdist64(const float* x, const float* y, int d)
+{
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = (double)x[j] - (double)y[j];
+        s += t * t;
+    }
+    return s;
+}
+
+static double sqdist64_dd(const double* x, const double* y, int d)
+{
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double t = x[j] - y[j];
+        s += t * t;
+    }
+    return s;
+}
+
+typedef struct {
+    double D;
+    int32_t id;
+} cand_t;
+
+static int cmp_cand(const void* pa, const void* pb)
+{
+    const cand_t* a = (const cand_t*)pa;
+    const cand_t* b = (const cand_t*)pb;
+    if (a->D < b->D) return -1;
+    if (a->D > b->D) return 1;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
+static int cmp_u64(const void* pa, const void* pb)
+{
+    uint64_t a = *(const uint64_t*)pa, b = *(const uint64_t*)pb;
+    return (a > b) - (a < b);
+}
+
+static int cmp_i32(const void* pa, const void* pb)
+{
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    return (a > b) - (a < b);
+}
+
+/* Sort the candidates by (D, id) and write the first k; pad with id -1 and
+ * distance +inf when fewer than k exist. */
+static void emit_topk(cand_t* c, int64_t cnt, int k, int32_t* ids, float* dists)
+{
+    qsort(c, (size_t)cnt, sizeof(cand_t), cmp_cand);
+    for (int e = 0; e < k; ++e) {
+        if (e < cnt) {
+            ids[e] = c[e].id;
+            dists[e] = (float)c[e].D;
+        } else {
+            ids[e] = -1;
+            dists[e] = INFINITY;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One random partition tree (Sec. 3.1): recursive bisection at the median   */
+/* of the projections until a subset holds at most g points.  Leaves are     */
+/* emitted left to right, each with its member ids sorted ascending; this is */
+/* the canonical leaf set.                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const float* X;
+    int d;
+    int64_t ld;
+    uint64_t seed;
+    uint32_t t;
+    int g;
+    int32_t* perm;     /* output, n entries */
+    int64_t* leaf_off; /* output, nleaves + 1 entries */
+    int64_t nleaves;
+    int64_t pos;
+} part_ctx;
+
+static void split_node(part_ctx* c, int32_t* ids, int64_t m, uint32_t level, uint32_t v)
+{
+    if (m <= c->g) {
+        qsort(ids, (size_t)m, sizeof(int32_t), cmp_i32);
+        memcpy(c->perm + c->pos, ids, (size_t)m * sizeof(int32_t));
+        c->leaf_off[c->nleaves++] = c->pos;
+        c->pos += m;
+        return;
+    }
+    float* a = (float*)malloc((size_t)c->d * sizeof(float));
+    uint64_t* keys = (uint64_t*)malloc((size_t)m * sizeof(uint64_t));
+    orc_direction(c->seed, c->t, level, v, c->d, a);
+    for (int64_t i = 0; i < m; ++i) {
+        float s = orc_project(c->X + (int64_t)ids[i] * c->ld, a, c->d);
+        keys[i] = ((uint64_t)orc_ord(s) << 32) | (uint32_t)ids[i];
+    }
+    qsort(keys, (size_t)m, sizeof(uint64_t), cmp_u64);
+    int64_t ml = m / 2;
+    int32_t* left = (int32_t*)malloc((size_t)ml * sizeof(int32_t));
+    int32_t* right = (int32_t*)malloc((size_t)(m - ml) * sizeof(int32_t));
+    for (int64_t i = 0; i < ml; ++i) left[i] = (int32_t)(keys[i] & 0xFFFFFFFFu);
+    for (int64_t i = ml; i < m; ++i) right[i - ml] = (int32_t)(keys[i] & 0xFFFFFFFFu);
+    free(keys);
+    free(a);
+    split_node(c, left, ml, level + 1, 2 * v);
+    split_node(c, right, m - ml, level + 1, 2 * v + 1);
+    free(left);
+    free(right);
+}
+
+/* Number of leaves of a tree over n points with leaf size g (depends on n, g
+ * only: every split halves a node into floor(m/2) and ceil(m/2)). */
+static int64_t count_leaves(int64_t m, int g)
+{
+    if (m <= g) return 1;
+    return count_leaves(m / 2, g) + count_leaves(m - m / 2, g);
+}
+
+int64_t orc_leaf_count(int64_t n, int g)
+{
+    return count_leaves(n, g);
+}
+
+/* perm: n entries; leaf_off: orc_leaf_count(n, g) + 1 entries. */
+int orc_partition(const float* X, int64_t n, int d, int64_t ld, uint64_t seed, uint32_t t, int g,
+                  int32_t* perm, int64_t* leaf_off)
+{
+    part_ctx c;
+    c.X = X;
+    c.d = d;
+    c.ld = ld;
+    c.seed = seed;
+    c.t = t;
+    c.g = g;
+    c.perm = perm;
+    c.leaf_off = leaf_off;
+    c.nleaves = 0;
+    c.pos = 0;
+    int32_t* ids = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    for (int64_t i = 0; i < n; ++i) ids[i] = (int32_t)i;
+    split_node(&c, ids, n, 0, 0);
+    free(ids);
+    leaf_off[c.nleaves] = n;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Leaf graph (Sec. 3.1): brute force inside each subset.  For every point i */
+/* of a leaf, the k nearest other members by (D, id).  ids/dists: [n, k],    */
+/* row i belongs to point i.                                                 */
+/* ------------------------------------------------------------------------ */
+int orc_leaf_knn(const float* X, int64_t n, int d, int64_t ld, const int32_t* perm,
+                 const int64_t* leaf_off, int64_t nleaves, int k, int32_t* ids, float* dists)
+{
+    (void)n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t L = 0; L < nleaves; ++L) {
+        int64_t b = leaf_off[L], e = leaf_off[L + 1];
+        cand_t* c = (cand_t*)malloc((size_t)(e - b) * sizeof(cand_t));
+        for (int64_t a = b; a < e; ++a) {
+            int32_t i = perm[a];
+            int64_t cnt = 0;
+            for (int64_t q = b; q < e; ++q) {
+                int32_t j = perm[q];
+                if (j == i) continue;
+                c[cnt].D = sqdist64(X + (int64_t)i * ld, X + (int64_t)j * ld, d);
+                c[cnt].id = j;
+                ++cnt;
+            }
+            emit_topk(c, cnt, k, ids + (int64_t)i * k, dists + (int64_t)i * k);
+        }
+        free(c);
+    }
+    return 0;
+}
+
+/* Leaf graph through a reduced-precision candidate stage: for every point i
+ * of a leaf, the kp nearest other members by (Dq, id), where Dq is the FP64
+ * squared distance between the quantised-and-dequantised rows Xq (n x d,
+ * row-major), then the k nearest of those kp by the exact (D, id). */
+int orc_leaf_knn_quant(const float* X, int64_t n, int d, int64_t ld, const double* Xq,
+                       const int32_t* perm, const int64_t* leaf_off, int64_t nleaves, int k,
+                       int kp, int32_t* ids, float* dists)
+{
+    (void)n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t L = 0; L < nleaves; ++L) {
+        int64_t b = leaf_off[L], e = leaf_off[L + 1];
+        cand_t* c = (cand_t*)malloc((size_t)(e - b) * sizeof(cand_t));
+        for (int64_t a = b; a < e; ++a) {
+            int32_t i = perm[a];
+            int64_t cnt = 0;
+            for (int64_t q = b; q < e; ++q) {
+                int32_t j = perm[q];
+                if (j == i) continue;
+                c[cnt].D = sqdist64_dd(Xq + (int64_t)i * d, Xq + (int64_t)j * d, d);
+                c[cnt].id = j;
+                ++cnt;
+            }
+            qsort(c, (size_t)cnt, sizeof(cand_t), cmp_cand);
+            int64_t keep = cnt < kp ? cnt : kp;
+            for (int64_t r = 0; r < keep; ++r)
+                c[r].D = sqdist64(X + (int64_t)i * ld, X + (int64_t)c[r].id * ld, d);
+            emit_topk(c, keep, k, ids + (int64_t)i * k, dists + (int64_t)i * k);
+        }
+        free(c);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Combination of the T base graphs (Sec. 3.1): unite the adjacency lists of */
+/* every point and keep its k nearest.  lists: [T, n, k] ids (-1 = empty).   */
+/* Distances are recomputed from X, so duplicates collapse by id.           */
+/* ------------------------------------------------------------------------ */
+int orc_merge(const float* X, int64_t n, int d, int64_t ld, int T, int k, const int32_t* lists,
+              int32_t* ids, float* dists)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t p = 0; p < n; ++p) {
+        int32_t* u = (int32_t*)malloc((size_t)T * k * sizeof(int32_t));
+        int64_t cnt = 0;
+        for (int t = 0; t < T; ++t)
+            for (int e = 0; e < k; ++e) {
+                int32_t q = lists[((int64_t)t * n + p) * k + e];
+                if (q < 0 || q == p) continue;
+                u[cnt++] = q;
+            }
+        qsort(u, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        cand_t* c = (cand_t*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(cand_t));
+        int64_t m = 0;
+        for (int64_t e = 0; e < cnt; ++e) {
+            if (e > 0 && u[e] == u[e - 1]) continue;
+            c[m].id = u[e];
+            c[m].D = sqdist64(X + p * ld, X + (int64_t)u[e] * ld, d);
+            ++m;
+        }
+        emit_topk(c, m, k, ids + p * k, dists + p * k);
+        free(c);
+        free(u);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One round of first-order neighbourhood propagation (Sec. 3.2, Theorem 1): */
+/* the candidates of p are its current neighbours and their neighbours,     */
+/* without p; the new list is the k best candidates by (D, id).  All lists   */
+/* are read from the input graph (a synchronous round).                     */
+/* ------------------------------------------------------------------------ */
+int orc_propagate(const float* X, int64_t n, int d, int64_t ld, int k, const int32_t* in_ids,
+                  int32_t* ids, float* dists)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t p = 0; p < n; ++p) {
+        int64_t cap = (int64_t)k + (int64_t)k * k;
+        int32_t* u = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
+        int64_t cnt = 0;
+        for (int e = 0; e < k; ++e) {
+            int32_t q = in_ids[p * k + e];
+            if (q < 0) continue;
+            if (q != p) u[cnt++] = q;
+            for (int f = 0; f < k; ++f) {
+                int32_t o = in_ids[(int64_t)q * k + f];
+                if (o < 0 || o == p) continue;
+                u[cnt++] = o;
+            }
+        }
+        qsort(u, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        cand_t* c = (cand_t*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(cand_t));
+        int64_t m = 0;
+        for (int64_t e = 0; e < cnt; ++e) {
+            if (e > 0 && u[e] == u[e - 1]) continue;
+            c[m].id = u[e];
+            c[m].D = sqdist64(X + p * ld, X + (int64_t)u[e] * ld, d);
+            ++m;
+        }
+        emit_topk(c, m, k, ids + p * k, dists + p * k);
+        free(c);
+        free(u);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact k-NN lists (Def. 1) of the query points against all n points, by    */
+/* brute force; the accuracy of Sec. 4 is measured against these.           */
+/* ------------------------------------------------------------------------ */
+int orc_knn_exact(const float* X, int64_t n, int d, int64_t ld, int k, const int32_t* queries,
+                  int64_t nq, int32_t* ids, float* dists)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t a = 0; a < nq; ++a) {
+        int32_t p = queries[a];
+        cand_t* c = (cand_t*)malloc((size_t)n * sizeof(cand_t));
+        int64_t cnt = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == p) continue;
+            c[cnt].D = sqdist64(X + (int64_t)p * ld, X + j * ld, d);
+            c[cnt].id = (int32_t)j;
+            ++cnt;
+        }
+        emit_topk(c, cnt, k, ids + a * k, dists + a * k);
+        free(c);
+    }
+    return 0;
+}
+
+/* FP64 squared distances of given pairs (a helper for tests and recall). */
+int orc_pair_dist(const float* X, int d, int64_t ld, const int32_t* a, const int32_t* b,
+                  int64_t npairs, double* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < npairs; ++e)
+        out[e] = sqdist64(X + (int64_t)a[e] * ld, X + (int64_t)b[e] * ld, d);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reduced-precision encodings of the candidate stage.                      */
+/* ------------------------------------------------------------------------ */
+
+/* Round to the nearest value with `sig` significant bits whose exponent is
+ * at least emin (below it the spacing stays 2^(emin - sig + 1)), ties to
+ * even.  Written from the definition: scale by the spacing, rint (the
+ * default rounding mode rounds half to even), scale back. */
+static double round_to_grid(double x, int sig, int emin)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int E;
+    frexp(x, &E); /* |x| = f * 2^E, f in [0.5, 1): exponent of x is E - 1 */
+    int e = E - 1;
+    if (e < emin) e = emin;
+    double spacing = ldexp(1.0, e - (sig - 1));
+    return rint(x / spacing) * spacing;
+}
+
+/* bfloat16: 8 significant bits, FP32's exponent range (min normal 2^-126). */
+float orc_bf16_round(float x)
+{
+    double r = round_to_grid((double)x, 8, -126);
+    const double maxbf = ldexp(255.0, 120); /* (2 - 2^-7) * 2^127 */
+    if (fabs(r) > maxbf) r = copysign(INFINITY, r);
+    return (float)r;
+}
+
+/* FP8 E4M3 (the "fn" variant without infinities): 4 significant bits, min
+ * normal 2^-6, largest finite 448; out-of-range values saturate to +-448. */
+float orc_e4m3_round(float x)
+{
+    double r = round_to_grid((double)x, 4, -6);
+    if (r > 448.0) r = 448.0;
+    if (r < -448.0) r = -448.0;
+    return (float)r;
+}
+
+/* Quantise rows for the candidate stage and return them dequantised in
+ * FP64.  mode 1: bfloat16 per entry.  mode 2: E4M3 with one FP32 scale per
+ * row, s = max_j |x_j| / 448 (s = 1 for an all-zero row), code = E4M3(x/s)
+ * with the division done in FP32; value = s * code. */
+int orc_quantize_rows(const float* X, int64_t n, int d, int64_t ld, int mode, double* Xq,
+                      float* scales)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const float* x = X + i * ld;
+        double* q = Xq + i * d;
+        if (mode == 1) {
+            for (int j = 0; j < d; ++j) q[j] = (double)orc_bf16_round(x[j]);
+            if (scales) scales[i] = 1.0f;
+        } else if (mode == 2) {
+            float mx = 0.0f;
+            for (int j = 0; j < d; ++j) {
+                float ax = fabsf(x[j]);
+                if (ax > mx) mx = ax;
+            }
+            float s = (mx > 0.0f) ? mx / 448.0f : 1.0f;
+            for (int j = 0; j < d; ++j) {
+                float code = orc_e4m3_round(x[j] / s);
+                q[j] = (double)s * (double)code;
+            }
+            if (scales) scales[i] = s;
+        } else {
+            for (int j = 0; j < d; ++j) q[j] = (double)x[j];
+            if (scales) scales[i] = 1.0f;
+        }
+    }
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
