@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of k-NN graph construction (Wang et al., arXiv:1307.7852) on GB300.
+
+One step = one whole graph build (T random divisions, leaf graphs, merge, R
+propagation rounds) over a synthetic point set resident in HBM.  Default
+workload: 1,000,000 SIFT-like points (d = 128, integer values 0..255 from a
+1,024-centre Gaussian mixture), k = 20, T = 8, leaf size 256, 2 rounds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is whole-job points/s (n x ranks / max-over-
+ranks seconds per step), measured with CUDA events on the build's stream;
+``e2e`` is the same metric through the host-buffer C ABI call with the
+host<->device copies inside the timed region.  Under torchrun every rank builds
+an independent replica (the method is not sharded: "replicas only").
+``--impl reference`` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: generator args and method parameters
+    "sift1m": dict(gen="sift_like", n=1_000_000, d=128, centers=1024, k=20, T=8, g=256, R=2,
+                   desc="1M x 128 SIFT-like integer mixture (1,024 centres, std 20), k=20, T=8, g=256, R=2"),
+    "sift10k": dict(gen="sift_like", n=10_000, d=128, centers=64, k=10, T=4, g=64, R=1,
+                    desc="10k x 128 SIFT-like integer mixture (64 centres), k=10, T=4, g=64, R=1"),
+    "gist1m": dict(gen="gist_like", n=1_000_000, d=960, centers=256, k=10, T=8, g=512, R=1,
+                   desc="1M x 960 GIST-like normalised mixture (256 centres), k=10, T=8, g=512, R=1"),
+}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+METRIC = "points/sec to build the k-NN graph (recall@k reported on a 10k-point sample)"
+
+
+def make_data(w, seed):
+    from paper_1307_7852_gb300 import synthetic
+    if w["gen"] == "sift_like":
+        return synthetic.sift_like(w["n"], w["d"], centers=w["centers"], seed=seed)
+    if w["gen"] == "gist_like":
+        return synthetic.gist_like(w["n"], w["d"], centers=w["centers"], seed=seed)
+    raise ValueError(w["gen"])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        return float(P["hbm_gbs"]), float(P["bf16_tflops"]), float(P.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+def unique_candidates(ids: np.ndarray, sample: np.ndarray) -> float:
+    """Mean number of candidates a first-order round scores per point: the
+    distinct ids of the neighbours' lists that are not p and not already in
+    p's list."""
+    tot = 0
+    for p in sample:
+        own = ids[p]
+        own = own[own >= 0]
+        c = ids[own].ravel()
+        c = c[(c >= 0) & (c != p)]
+        c = np.setdiff1d(np.unique(c), own, assume_unique=False)
+        tot += c.size
+    return tot / max(1, len(sample))
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, w, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    X = make_data(w, seed=args.data_seed)
+    ns = args.ref_sample
+    Xs = np.ascontiguousarray(X[:ns])
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.build_graph(Xs, w["k"], w["T"], w["g"], w["R"], args.seed)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    sec = statistics.mean(times)
+    val = ns / sec
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "points/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_points": ns, **{k: w[k] for k in ("d", "k", "T", "g", "R")}},
+        "cpu_baseline": {"value": val, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {ns} points of the {args.workload} workload, whole method"},
+        "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- ours
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sift1m")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
+    ap.add_argument("--seed", type=int, default=12345)
+    ap.add_argument("--data-seed", type=int, default=2013)
+    ap.add_argument("--recall-sample", type=int, default=10000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=50000)
+    ap.add_argument("--ref-sample", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="timed builds only (for profiler runs)")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, w, rank)
+
+    import torch
+    import paper_1307_7852_gb300 as knng
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    # CPU oracle work runs before the first CUDA call (no fork after CUDA init)
+    X = make_data(w, seed=args.data_seed + rank)
+    n, d, k, T, g, R = w["n"], w["d"], w["k"], w["T"], w["g"], w["R"]
+    prec = PRECISIONS[args.precision]
+    Xd = torch.from_numpy(X).to(dev)
+    ids = torch.empty((n, k), dtype=torch.int32, device=dev)
+    dists = torch.empty((n, k), dtype=torch.float32, device=dev)
+    h = knng.Handle(local)
+    stream = torch.cuda.current_stream(dev)
+    nev = 4 + R
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(args.steps)]
+
+    def step(events=None):
+        if events is not None:
+            knng.knng_set_stage_events(events, h)
+        knng.knng_build(Xd, k, T, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = knng.knng_launch_counter()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        t_start.record(stream)
+        for s in range(args.steps):
+            step(ev[s])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    knng.knng_set_stage_events(None, h)
+    launches = knng.knng_launch_counter() - l0
+    el = t_start.elapsed_time(t_end) / 1e3
+    if dist:
+        tt = torch.tensor([el], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
+    sec = el / args.steps
+    value = n * world / sec
+    names = ["partition", "leaf_knn", "merge"] + [f"propagate_r{r}" for r in range(R)]
+    stage_ms = {nm: statistics.mean(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(args.steps))
+                for i, nm in enumerate(names)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "n": n, "d": d, "k": k, "T": T,
+                   "leaf_size": g, "rounds": R, "precision": args.precision, "seed": args.seed,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": f"inputs larger than L2 (X = {X.nbytes / 2**20:.0f} MiB > 126 MiB)"},
+        "stage_ms": {k_: round(v, 4) for k_, v in stage_ms.items()},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_extras and rank == 0:
+        hbm, bf16, sm_mhz, src = peaks()
+        # ---- per-stage roofline figures (algorithmic work / measured time)
+        off = knng.knng_leaf_offsets(n, g)
+        m = np.diff(off).astype(np.float64)
+        perm = knng.knng_partition(Xd, T, g, args.seed, h=h)
+        li, ld_ = knng.knng_leaf_knn(Xd, T, g, perm, k, prec, 2, h=h)
+        mi, md = knng.knng_merge(li, ld_, h=h)
+        graphs = [mi]
+        cur_i, cur_d = mi, md
+        for _ in range(R):
+            cur_i, cur_d = knng.knng_propagate(Xd, cur_i, cur_d, 1, h=h)
+            graphs.append(cur_i)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(7)
+        samp = rng.choice(n, size=min(n, 20000), replace=False)
+        u = [unique_candidates(gph.cpu().numpy(), samp) for gph in graphs[:R]]
+        del perm, li, ld_, graphs
+        s_el = 4  # FP32 rows
+        roof = {}
+        if R > 0:
+            per_launch = [n * (k * k * 4 + u_r * d * s_el + 2 * k * 8 + d * s_el) for u_r in u]
+            t_prop = [stage_ms[f"propagate_r{r}"] / 1e3 for r in range(R)]
+            ach = sum(per_launch) / sum(t_prop) / 1e9
+            roof["propagate"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                 "frac": ach / hbm, "traffic": None,
+                                 "algorithmic_bytes_per_launch": statistics.mean(per_launch),
+                                 "unique_candidates_per_point": u, "ms": sum(t_prop) * 1e3 / R}
+        gram_flops = T * float(np.sum(2.0 * d * m * (m - 1) / 2.0))
+        t_leaf = stage_ms["leaf_knn"] / 1e3
+        if prec == 0:
+            alu = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            ach = gram_flops / t_leaf / 1e12
+            roof["leaf_knn"] = {"bound": "alu", "achieved": ach, "peak": alu, "unit": "TFLOP/s",
+                                "frac": ach / alu, "traffic": None, "algorithmic_flops_per_launch": gram_flops}
+        else:
+            ach = gram_flops / t_leaf / 1e12
+            roof["leaf_knn"] = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                                "frac": ach / bf16, "traffic": None, "algorithmic_flops_per_launch": gram_flops}
+        merge_bytes = n * (T + 1) * k * 8
+        ach = merge_bytes / (stage_ms["merge"] / 1e3) / 1e9
+        roof["merge"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": None, "algorithmic_bytes_per_launch": merge_bytes}
+        # the dominant kernel of the step carries the headline roofline object
+        stage_of = {"leaf_knn": stage_ms["leaf_knn"], "merge": stage_ms["merge"]}
+        if R > 0:
+            stage_of["propagate"] = sum(stage_ms[f"propagate_r{r}"] for r in range(R)) / R
+        dom = max(stage_of, key=stage_of.get)
+        line["roofline"] = dict(roof[dom], kernel=dom, peak_source=src)
+        line["roofline_all"] = roof
+
+        # ---- recall on a sample against exact brute force (GPU, same FP32 distance)
+        if not args.no_recall:
+            import oracle  # noqa: F401  (recall helpers only; exact lists from the GPU kernel)
+            from paper_1307_7852_gb300 import synthetic
+            q = synthetic.sample_ids(n, args.recall_sample, args.seed + 1)
+            qd = torch.from_numpy(q).to(dev)
+            ei, ed = knng.knng_exact_knn(Xd, qd, k, h=h)
+            got_i = ids[qd.long()]
+            got_d = dists[qd.long()]
+            kth = ed[:, -1:]
+            tie = (got_d <= kth).sum(1).float().mean().item() / k
+            gi = got_i.cpu().numpy()
+            eii = ei.cpu().numpy()
+            idset = float(np.mean([len(set(gi[r]) & set(eii[r])) / k for r in range(len(q))]))
+            line["recall"] = {"tie_tolerant": tie, "id_set": idset, "sample": int(len(q)),
+                              "reference": "exact brute force over all n (GPU, FP32 distances)"}
+
+        # ---- end to end through the host-buffer C ABI call
+        if not args.no_e2e:
+            Xp = torch.from_numpy(X).pin_memory()
+            oi = torch.empty((n, k), dtype=torch.int32).pin_memory()
+            od = torch.empty((n, k), dtype=torch.float32).pin_memory()
+            Xn, oin, odn = Xp.numpy(), oi.numpy(), od.numpy()
+            knng.knng_build_host(Xn, k, T, g, R, args.seed, prec, 2, ids=oin, dists=odn, device=local, h=h)
+            tt = []
+            for _ in range(args.e2e_steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                knng.knng_build_host(Xn, k, T, g, R, args.seed, prec, 2, ids=oin, dists=odn, device=local, h=h)
+                tt.append(time.perf_counter() - t0)
+            e2e_sec = statistics.mean(tt)
+            line["e2e"] = {"value": n / e2e_sec, "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes),
+                           "d2h_bytes_per_step": int(n * k * 8), "ms_per_step": e2e_sec * 1e3,
+                           "api": "knng_build_host (pinned host buffers)"}
+
+    # ---- the CPU oracle on a bounded sample (rank 0, N = 1 only)
+    if not args.no_extras and not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        ns = min(args.cpu_sample, n)
+        Xs = np.ascontiguousarray(X[:ns])
+        t0 = time.perf_counter()
+        oracle.build_graph(Xs, k, T, g, R, args.seed)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ns / dt, "unit": "points/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"first {ns} points of the workload, whole method "
+                                                            f"({dt:.1f} s)"}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

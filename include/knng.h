@@ -1,0 +1,166 @@
+/*
+ * knng.h -- C ABI of the GB300 k-NN graph library.
+ *
+ * The library builds an approximate k-nearest-neighbour graph by the method of
+ * Wang, Wang, Zeng, Tu, Gan and Li, "Scalable k-NN graph construction"
+ * (arXiv:1307.7852): T random hierarchical divisions of the points (Sec. 3.1),
+ * an exact brute-force graph inside every leaf subset (Sec. 3.1), the union of
+ * the T base graphs keeping the k nearest (Sec. 3.1), and neighbourhood
+ * propagation (Sec. 3.2; the first-order form of Theorem 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named X, ids, dists, perm, *_in are DEVICE pointers (cudaMalloc,
+ *    torch tensors, ...), owned by the caller; the library never frees them.
+ *    Entry points whose name ends in _host take HOST pointers instead.
+ *  - X is row-major: point i starts at element i*ld; ld >= d.  dtype is
+ *    KNNG_DTYPE_F32 (float) or KNNG_DTYPE_F16 (IEEE half, widened exactly).
+ *  - Graph outputs are ids[n][k] (int32) and dists[n][k] (float): the
+ *    neighbours of point i in row i, ordered by (distance, id) ascending,
+ *    never containing i, without duplicates.  A distance is the SQUARED
+ *    Euclidean distance (it ranks like the Euclidean distance of Def. 1).
+ *    Rows are padded with id -1 / distance +inf only when fewer than k other
+ *    candidates exist.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *    work is enqueued on it; calls return after enqueueing, except those
+ *    ending in _host, which return after the results are on the host.
+ *  - Return value: KNNG_OK (0) or a negative KNNG_ERR_* code.  Nothing aborts
+ *    and nothing throws across the ABI.  knng_last_error() describes the last
+ *    failure of a handle.
+ *  - A handle owns a device workspace, grown on demand with the stream-ordered
+ *    allocator; calls on one handle must not run concurrently from several
+ *    host threads.
+ */
+#ifndef KNNG_H
+#define KNNG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define KNNG_OK 0
+#define KNNG_ERR_INVALID_ARG (-1) /* a size, pointer or parameter is out of range */
+#define KNNG_ERR_UNSUPPORTED (-2) /* valid request this build does not serve     */
+#define KNNG_ERR_OOM (-3)         /* device workspace allocation failed          */
+#define KNNG_ERR_CUDA (-4)        /* a CUDA runtime call or launch failed        */
+#define KNNG_ERR_TIMEOUT (-5)     /* a bounded device wait gave up               */
+#define KNNG_ERR_INTERNAL (-6)
+
+/* ---- enumerations ---------------------------------------------------- */
+#define KNNG_DTYPE_F32 0
+#define KNNG_DTYPE_F16 1
+
+/* Precision of the leaf candidate stage.  The leaf top-k' is chosen on
+ * distances computed from rows at this precision, then every candidate is
+ * rescored in FP32 by direct differences and the k best are kept. */
+#define KNNG_PREC_FP32 0
+#define KNNG_PREC_BF16 1
+#define KNNG_PREC_FP8E4M3 2
+
+#define KNNG_PART_RANDOM 0
+
+/* ---- parameters ------------------------------------------------------ */
+typedef struct knng_params {
+    int32_t k;            /* neighbours per point, 1 <= k <= 64, k < leaf_size/2     */
+    int32_t T;            /* random divisions (trees), 1 <= T <= 32 (Sec. 3.1's M)   */
+    int32_t leaf_size;    /* g: a node with at most g points is a leaf, 2..512 (Sec. 3.1) */
+    int32_t prop_rounds;  /* R: first-order propagation rounds, 0..16 (Sec. 3.2)     */
+    uint64_t seed;        /* key of the Philox directions; same seed -> same trees   */
+    int32_t precision;    /* KNNG_PREC_*                                             */
+    int32_t rescore_mult; /* k' = rescore_mult * k candidates per leaf row, 1..4     */
+    int32_t partitioner;  /* KNNG_PART_RANDOM                                        */
+    int32_t reserved;     /* must be 0                                               */
+} knng_params;
+
+typedef struct knng_handle knng_handle;
+
+/* ---- handle ---------------------------------------------------------- */
+/* Creates a handle bound to CUDA device `device` (made current for the call).
+ * *out receives the handle; returns KNNG_ERR_INVALID_ARG for a bad device. */
+int knng_create(knng_handle** out, int32_t device);
+/* Frees the workspace (after synchronising the device) and the handle. */
+int knng_destroy(knng_handle* h);
+/* Static description of a status code; never NULL. */
+const char* knng_status_string(int32_t status);
+/* Message of the last failure on h ("" if none); valid until the next call. */
+const char* knng_last_error(const knng_handle* h);
+
+/* ---- tree shape (host only) ------------------------------------------ */
+/* Every split halves a node of m points into floor(m/2) (left) and
+ * ceil(m/2) (right) points, so the leaf layout of a tree depends on (n, g)
+ * only and is shared by all trees.  knng_leaf_count writes the number of
+ * leaves; knng_leaf_offsets writes the nleaves+1 start offsets of the leaves
+ * (left to right) into the HOST array leaf_off. */
+int knng_leaf_count(int64_t n, int32_t leaf_size, int64_t* nleaves);
+int knng_leaf_offsets(int64_t n, int32_t leaf_size, int64_t* leaf_off);
+
+/* ---- whole method ---------------------------------------------------- */
+/* Builds the approximate k-NN graph of X[n][d] (Sec. 3): p->T divisions,
+ * leaf graphs, merge, p->prop_rounds propagation rounds.  ids, dists: device
+ * [n][k].  2 <= n < 2^31, 1 <= d <= 4096. */
+int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+               const knng_params* p, int32_t* ids, float* dists, void* stream);
+/* Same as knng_build with HOST X, ids and dists: copies X to the device,
+ * builds, copies the graph back and synchronises `stream` before returning. */
+int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d,
+                    int64_t ld, const knng_params* p, int32_t* ids, float* dists, void* stream);
+
+/* ---- stages ---------------------------------------------------------- */
+/* Random divisions (Sec. 3.1; split rule of the appendix after Lemma 1).
+ * perm: device int32 [T][n].  Row t lists the point ids of tree t leaf by
+ * leaf, left to right, ids ascending inside each leaf (the canonical leaf
+ * set; leaf boundaries from knng_leaf_offsets).  Tree t depends only on
+ * (X, seed, t, leaf_size). */
+int knng_partition(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                   int32_t T, int32_t leaf_size, uint64_t seed, int32_t* perm, void* stream);
+
+/* Leaf graphs (Sec. 3.1): for every tree t and point i, the k nearest other
+ * members of i's leaf.  perm: device [T][n] as written by knng_partition.
+ * ids, dists: device [T][n][k] (row t*n+i is point i in tree t). */
+int knng_leaf_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                  int32_t T, int32_t leaf_size, const int32_t* perm, int32_t k,
+                  int32_t precision, int32_t rescore_mult, int32_t* ids, float* dists,
+                  void* stream);
+
+/* Combination of base graphs (Sec. 3.1): for every point, the union of its T
+ * lists (ids_in/dists_in device [T][n][k], each row ordered by (distance,
+ * id)), duplicates removed by id, the k best kept.  ids, dists: [n][k]. */
+int knng_merge(knng_handle* h, int64_t n, int32_t T, int32_t k, const int32_t* ids_in,
+               const float* dists_in, int32_t* ids, float* dists, void* stream);
+
+/* Neighbourhood propagation (Sec. 3.2, first-order form of Theorem 1):
+ * `rounds` synchronous rounds; in each, every point p takes the k best of
+ * its list and its neighbours' lists (without p), scoring new candidates by
+ * exact FP32 distances.  ids_in/dists_in: device [n][k]; ids, dists: [n][k].
+ * The input and output may not overlap. */
+int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                   int32_t k, int32_t rounds, const int32_t* ids_in, const float* dists_in,
+                   int32_t* ids, float* dists, void* stream);
+
+/* ---- measurement ----------------------------------------------------- */
+/* Exact k-NN lists (Def. 1) of nq query points against all n points, by
+ * brute force with the same FP32 distance as the graph (the yardstick of the
+ * accuracy measure of Sec. 4).  queries: device int32 [nq] point ids;
+ * ids, dists: device [nq][k], ordered by (distance, id). */
+int knng_exact_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                   const int32_t* queries, int64_t nq, int32_t k, int32_t* ids, float* dists,
+                   void* stream);
+
+/* Stage timing.  With events set (nevents >= 4 + prop_rounds, each a
+ * cudaEvent_t created by the caller), knng_build records events[0] before
+ * the divisions, [1] after them, [2] after the leaf graphs, [3] after the
+ * merge and [4 + r] after propagation round r, all on the build's stream.
+ * Pass NULL / 0 to stop recording. */
+int knng_set_stage_events(knng_handle* h, void* const* events, int32_t nevents);
+
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all handles); a diagnostic for counting launches per build. */
+int knng_launch_counter(uint64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNNG_H */

@@ -1,0 +1,315 @@
+"""ctypes binding of libknng.so (the C ABI declared in include/knng.h).
+
+Argument marshalling only: tensors become device pointers, the current torch
+stream becomes the cudaStream_t, and every step of the computation runs in
+the library's CUDA kernels.  There is no fallback: if the shared library is
+missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libknng.so")
+
+KNNG_OK = 0
+DTYPE_F32, DTYPE_F16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
+PART_RANDOM = 0
+
+_lock = threading.Lock()
+_lib = None
+_handles = {}
+
+
+class KnngError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"knng error {code}: {msg}")
+        self.code = code
+
+
+class knng_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("T", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("prop_rounds", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int32), ("rescore_mult", ctypes.c_int32),
+                ("partitioner", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# exported entry points -> argtypes
+_P, _I32, _I64, _U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+SIGNATURES = {
+    "knng_create": [ctypes.POINTER(ctypes.c_void_p), _I32],
+    "knng_destroy": [_P],
+    "knng_status_string": [_I32],
+    "knng_last_error": [_P],
+    "knng_leaf_count": [_I64, _I32, ctypes.POINTER(ctypes.c_int64)],
+    "knng_leaf_offsets": [_I64, _I32, _P],
+    "knng_build": [_P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P],
+    "knng_build_host": [_P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P],
+    "knng_partition": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _U64, _P, _P],
+    "knng_leaf_knn": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _I32, _I32, _I32, _P, _P, _P],
+    "knng_merge": [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P],
+    "knng_propagate": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
+    "knng_exact_knn": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _I32, _P, _P, _P],
+    "knng_set_stage_events": [_P, _P, _I32],
+    "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it was not built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                                   "(the k-NN graph path has no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, argt in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = argt
+                fn.restype = ctypes.c_int
+            L.knng_status_string.restype = ctypes.c_char_p
+            L.knng_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+class Handle:
+    """Owns a knng_handle (device workspace + cached tree plan)."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        rc = lib().knng_create(ctypes.byref(h), self.device)
+        if rc != KNNG_OK:
+            raise KnngError(rc, lib().knng_status_string(rc).decode())
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def check(self, rc: int, what: str):
+        if rc != KNNG_OK:
+            detail = lib().knng_last_error(self._h).decode()
+            raise KnngError(rc, f"{what}: {lib().knng_status_string(rc).decode()}: {detail}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().knng_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def handle(device: int = 0) -> Handle:
+    """A per-device handle shared by the convenience calls below."""
+    with _lock:
+        h = _handles.get(device)
+    if h is None:
+        h = Handle(device)
+        with _lock:
+            _handles[device] = h
+    return h
+
+
+# ------------------------------------------------------------ marshalling --
+def _torch():
+    import torch
+    return torch
+
+
+def _xdesc(X):
+    torch = _torch()
+    if not isinstance(X, torch.Tensor) or not X.is_cuda:
+        raise TypeError("X must be a CUDA tensor")
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be 2-D with unit stride along d")
+    if X.dtype == torch.float32:
+        dt = DTYPE_F32
+    elif X.dtype == torch.float16:
+        dt = DTYPE_F16
+    else:
+        raise TypeError("X must be float32 or float16")
+    return ctypes.c_void_p(X.data_ptr()), dt, X.shape[0], X.shape[1], X.stride(0)
+
+
+def _stream(dev, stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _out(shape, dtype, device, given):
+    torch = _torch()
+    if given is not None:
+        if tuple(given.shape) != tuple(shape) or given.dtype != dtype or not given.is_contiguous():
+            raise ValueError(f"output must be contiguous {dtype} {tuple(shape)}")
+        return given
+    return torch.empty(shape, dtype=dtype, device=device)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
+                partitioner=PART_RANDOM) -> knng_params:
+    return knng_params(int(k), int(T), int(leaf_size), int(prop_rounds), int(seed) & (2**64 - 1),
+                       int(precision), int(rescore_mult), int(partitioner), 0)
+
+
+# ----------------------------------------------------------- entry points --
+def knng_leaf_count(n: int, leaf_size: int) -> int:
+    out = ctypes.c_int64()
+    rc = lib().knng_leaf_count(int(n), int(leaf_size), ctypes.byref(out))
+    if rc != KNNG_OK:
+        raise KnngError(rc, "knng_leaf_count")
+    return int(out.value)
+
+
+def knng_leaf_offsets(n: int, leaf_size: int) -> np.ndarray:
+    off = np.zeros(knng_leaf_count(n, leaf_size) + 1, dtype=np.int64)
+    rc = lib().knng_leaf_offsets(int(n), int(leaf_size), ctypes.c_void_p(off.ctypes.data))
+    if rc != KNNG_OK:
+        raise KnngError(rc, "knng_leaf_offsets")
+    return off
+
+
+def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
+               ids=None, dists=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    ids = _out((n, k), torch.int32, X.device, ids)
+    dists = _out((n, k), torch.float32, X.device, dists)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    h.check(lib().knng_build(h.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
+                             _stream(X.device, stream)), "knng_build")
+    return ids, dists
+
+
+def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32,
+                    rescore_mult=2, ids=None, dists=None, stream=None, device: int = 0,
+                    h: Handle = None):
+    """Host arrays in and out (X float32/float16 [n, d], C-contiguous rows)."""
+    X = np.asarray(X)
+    if X.ndim != 2 or X.strides[1] != X.itemsize:
+        raise ValueError("X must be 2-D with unit stride along d")
+    dt = DTYPE_F16 if X.dtype == np.float16 else DTYPE_F32
+    if X.dtype not in (np.float16, np.float32):
+        raise TypeError("X must be float32 or float16")
+    n, d = X.shape
+    ld = X.strides[0] // X.itemsize
+    if ids is None:
+        ids = np.empty((n, k), dtype=np.int32)
+    if dists is None:
+        dists = np.empty((n, k), dtype=np.float32)
+    h = h or handle(device)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    torch = _torch()
+    st = _stream(torch.device("cuda", device), stream)
+    h.check(lib().knng_build_host(h.ptr, ctypes.c_void_p(X.ctypes.data), dt, n, d, ld, ctypes.byref(p),
+                                  ctypes.c_void_p(ids.ctypes.data), ctypes.c_void_p(dists.ctypes.data), st),
+            "knng_build_host")
+    return ids, dists
+
+
+def knng_partition(X, T, leaf_size, seed, perm=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    perm = _out((T, n), torch.int32, X.device, perm)
+    h.check(lib().knng_partition(h.ptr, xp, dt, n, d, ld, int(T), int(leaf_size), int(seed) & (2**64 - 1),
+                                 _ptr(perm), _stream(X.device, stream)), "knng_partition")
+    return perm
+
+
+def knng_leaf_knn(X, T, leaf_size, perm, k, precision=PREC_FP32, rescore_mult=2, ids=None,
+                  dists=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    if perm.dtype != torch.int32 or tuple(perm.shape) != (T, n) or not perm.is_contiguous():
+        raise ValueError("perm must be contiguous int32 [T, n]")
+    ids = _out((T, n, k), torch.int32, X.device, ids)
+    dists = _out((T, n, k), torch.float32, X.device, dists)
+    h.check(lib().knng_leaf_knn(h.ptr, xp, dt, n, d, ld, int(T), int(leaf_size), _ptr(perm), int(k),
+                                int(precision), int(rescore_mult), _ptr(ids), _ptr(dists),
+                                _stream(X.device, stream)), "knng_leaf_knn")
+    return ids, dists
+
+
+def knng_merge(ids_in, dists_in, ids=None, dists=None, stream=None, h: Handle = None):
+    torch = _torch()
+    T, n, k = ids_in.shape
+    for t_, dt_ in ((ids_in, torch.int32), (dists_in, torch.float32)):
+        if t_.dtype != dt_ or not t_.is_contiguous() or not t_.is_cuda or tuple(t_.shape) != (T, n, k):
+            raise ValueError("inputs must be contiguous CUDA [T, n, k] int32 / float32")
+    h = h or handle(ids_in.device.index or 0)
+    ids = _out((n, k), torch.int32, ids_in.device, ids)
+    dists = _out((n, k), torch.float32, ids_in.device, dists)
+    h.check(lib().knng_merge(h.ptr, n, T, k, _ptr(ids_in), _ptr(dists_in), _ptr(ids), _ptr(dists),
+                             _stream(ids_in.device, stream)), "knng_merge")
+    return ids, dists
+
+
+def knng_propagate(X, ids_in, dists_in, rounds=1, ids=None, dists=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    k = ids_in.shape[1]
+    for t_, dt_ in ((ids_in, torch.int32), (dists_in, torch.float32)):
+        if t_.dtype != dt_ or not t_.is_contiguous() or tuple(t_.shape) != (n, k):
+            raise ValueError("inputs must be contiguous [n, k] int32 / float32")
+    h = h or handle(X.device.index or 0)
+    ids = _out((n, k), torch.int32, X.device, ids)
+    dists = _out((n, k), torch.float32, X.device, dists)
+    h.check(lib().knng_propagate(h.ptr, xp, dt, n, d, ld, int(k), int(rounds), _ptr(ids_in),
+                                 _ptr(dists_in), _ptr(ids), _ptr(dists), _stream(X.device, stream)),
+            "knng_propagate")
+    return ids, dists
+
+
+def knng_exact_knn(X, queries, k, ids=None, dists=None, stream=None, h: Handle = None):
+    """Exact k-NN lists of the query ids (device int32 [nq]) against all points."""
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    if queries.dtype != torch.int32 or not queries.is_contiguous() or not queries.is_cuda:
+        raise ValueError("queries must be a contiguous CUDA int32 tensor")
+    nq = queries.shape[0]
+    h = h or handle(X.device.index or 0)
+    ids = _out((nq, k), torch.int32, X.device, ids)
+    dists = _out((nq, k), torch.float32, X.device, dists)
+    h.check(lib().knng_exact_knn(h.ptr, xp, dt, n, d, ld, _ptr(queries), nq, int(k), _ptr(ids),
+                                 _ptr(dists), _stream(X.device, stream)), "knng_exact_knn")
+    return ids, dists
+
+
+def knng_set_stage_events(events, h: Handle):
+    """Record the given torch.cuda.Event objects at the stage boundaries of
+    knng_build on handle h (events=None stops recording)."""
+    if not events:
+        h.check(lib().knng_set_stage_events(h.ptr, None, 0), "knng_set_stage_events")
+        return
+    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    h.check(lib().knng_set_stage_events(h.ptr, arr, len(events)), "knng_set_stage_events")
+
+
+def knng_launch_counter() -> int:
+    """Kernels launched by the library in this process so far."""
+    out = ctypes.c_uint64()
+    rc = lib().knng_launch_counter(ctypes.byref(out))
+    if rc != KNNG_OK:
+        raise KnngError(rc, "knng_launch_counter")
+    return int(out.value)

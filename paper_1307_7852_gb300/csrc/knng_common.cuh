@@ -1,0 +1,287 @@
+// Device-side building blocks shared by the kernels of the library:
+// Philox4x32-10, the order-preserving float key, row loads, the canonical
+// FP32 squared distance, and warp-level selection and sorting.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define KNNG_FULL_MASK 0xFFFFFFFFu
+
+namespace knng {
+
+constexpr uint64_t kKeyMax = ~0ull;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key increments
+// 0x9E3779B9 / 0xBB67AE85.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Triangular direction entry from one Philox word: (lo16 + hi16 - 65535)/2^16.
+__host__ __device__ inline float tri_entry(uint32_t u)
+{
+    return (float)((int32_t)(u & 0xFFFFu) + (int32_t)(u >> 16) - 65535) * (1.0f / 65536.0f);
+}
+
+// Order-preserving map of FP32 bits to u32: sign clear -> set sign bit;
+// sign set -> invert all bits.  -0 orders just below +0.
+__device__ __forceinline__ uint32_t ord_key(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float unord_key(uint32_t o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
+}
+__device__ __forceinline__ uint64_t pack_key(float dist, uint32_t id)
+{
+    return ((uint64_t)ord_key(dist) << 32) | id;
+}
+
+// ---------------------------------------------------------------------------
+// Row loads.  Point i of X starts at element i*ld; d entries.  load4 returns
+// entries j..j+3 (zero past d) widened to FP32.
+// ---------------------------------------------------------------------------
+template <bool kF16>
+struct RowLoader {
+    const void* X;
+    int64_t ld;
+    int d;
+    bool vec;  // rows 16-byte (F32) / 8-byte (F16) aligned and ld multiple of 4
+
+    __device__ __forceinline__ float4 load4(int64_t i, int j) const
+    {
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kF16) {
+            const __half* row = static_cast<const __half*>(X) + i * ld;
+            if (vec && j + 3 < d) {
+                const uint2 u = __ldg(reinterpret_cast<const uint2*>(row + j));
+                const __half2 a = *reinterpret_cast<const __half2*>(&u.x);
+                const __half2 b = *reinterpret_cast<const __half2*>(&u.y);
+                const float2 fa = __half22float2(a), fb = __half22float2(b);
+                r = make_float4(fa.x, fa.y, fb.x, fb.y);
+            } else {
+                if (j + 0 < d) r.x = __half2float(row[j + 0]);
+                if (j + 1 < d) r.y = __half2float(row[j + 1]);
+                if (j + 2 < d) r.z = __half2float(row[j + 2]);
+                if (j + 3 < d) r.w = __half2float(row[j + 3]);
+            }
+        } else {
+            const float* row = static_cast<const float*>(X) + i * ld;
+            if (vec && j + 3 < d) {
+                r = __ldg(reinterpret_cast<const float4*>(row + j));
+            } else {
+                if (j + 0 < d) r.x = __ldg(row + j + 0);
+                if (j + 1 < d) r.y = __ldg(row + j + 1);
+                if (j + 2 < d) r.z = __ldg(row + j + 2);
+                if (j + 3 < d) r.w = __ldg(row + j + 3);
+            }
+        }
+        return r;
+    }
+    __device__ __forceinline__ float load1(int64_t i, int j) const
+    {
+        if (kF16) return __half2float(static_cast<const __half*>(X)[i * ld + j]);
+        return __ldg(static_cast<const float*>(X) + i * ld + j);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Canonical FP32 squared distance between points a and b, computed by a full
+// warp: lane l accumulates s = fmaf(t, t, s), t = x_a[j] - x_b[j], over
+// j = 128c + 4l + e (chunk c ascending, e = 0..3), then pairwise rounds at
+// offsets 16, 8, 4, 2, 1.  Every lane returns the same value, and the value
+// depends only on the two rows (so D(a, b) == D(b, a) bit for bit).
+// ---------------------------------------------------------------------------
+template <bool kF16>
+__device__ __forceinline__ float warp_canon_dist(const RowLoader<kF16>& L, int64_t a, int64_t b)
+{
+    const int lane = threadIdx.x & 31;
+    float s = 0.0f;
+    for (int j = 4 * lane; j < L.d; j += 128) {
+        const float4 xa = L.load4(a, j), xb = L.load4(b, j);
+        float t;
+        t = xa.x - xb.x; s = fmaf(t, t, s);
+        t = xa.y - xb.y; s = fmaf(t, t, s);
+        t = xa.z - xb.z; s = fmaf(t, t, s);
+        t = xa.w - xb.w; s = fmaf(t, t, s);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
+    return s;
+}
+// Note: for entries past d both loads return 0, so t = 0 and fmaf(0,0,s) = s
+// (s >= +0 never becomes -0), leaving the partial sums unchanged.
+
+// ---------------------------------------------------------------------------
+// Warp bitonic sort of 32*E 64-bit keys, E per lane; element index
+// i = lane*E + e.  Ascending on return.
+// ---------------------------------------------------------------------------
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[E])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kk = 2; kk <= 32 * E; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                const int lj = j / E;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = lane * E + e;
+                    const uint64_t other = __shfl_xor_sync(KNNG_FULL_MASK, v[e], lj);
+                    const bool up = (i & kk) == 0;
+                    const bool lower = (i & j) == 0;
+                    const bool keep_min = (lower == up);
+                    const uint64_t mn = v[e] < other ? v[e] : other;
+                    const uint64_t mx = v[e] < other ? other : v[e];
+                    v[e] = keep_min ? mn : mx;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int p = e ^ j;
+                    if (p > e) {
+                        const int i = lane * E + e;
+                        const bool up = (i & kk) == 0;
+                        const uint64_t a = v[e], b = v[p];
+                        const bool sw = up ? (a > b) : (a < b);
+                        v[e] = sw ? b : a;
+                        v[p] = sw ? a : b;
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Warp radix select.  Among cnt unique 64-bit keys key(idx), idx in [0, cnt),
+// returns the threshold K such that exactly min(want, cnt) keys are <= K
+// (want >= 1).  8-bit digits from the most significant end; a pass stops the
+// search as soon as every key that matches the prefix must be taken.  hist:
+// 256 words of shared memory private to the warp.  Collective: all 32 lanes.
+// ---------------------------------------------------------------------------
+template <class KeyFn>
+__device__ uint64_t warp_select_threshold(const KeyFn& key, int cnt, int want, uint32_t* hist)
+{
+    if (want >= cnt) return kKeyMax;
+    const int lane = threadIdx.x & 31;
+    uint64_t prefix = 0, mask = 0;
+    int rank = want;
+    for (int shift = 56;; shift -= 8) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
+        __syncwarp();
+        for (int idx = lane; idx < cnt; idx += 32) {
+            const uint64_t kv = key(idx);
+            if ((kv & mask) == prefix) atomicAdd(&hist[(kv >> shift) & 0xFF], 1u);
+        }
+        __syncwarp();
+        uint32_t c[8];
+        uint32_t lsum = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            c[b] = hist[lane * 8 + b];
+            lsum += c[b];
+        }
+        uint32_t incl = lsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(KNNG_FULL_MASK, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t excl = incl - lsum;
+        const bool mine = excl < (uint32_t)rank && (uint32_t)rank <= incl;
+        const uint32_t owner = __ffs(__ballot_sync(KNNG_FULL_MASK, mine)) - 1;
+        uint32_t digit = 0, before = 0, inbin = 0;
+        if (mine) {
+            uint32_t run = excl;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                if (run < (uint32_t)rank && (uint32_t)rank <= run + c[b] && inbin == 0) {
+                    digit = lane * 8 + b;
+                    before = run;
+                    inbin = c[b];
+                }
+                run += c[b];
+            }
+        }
+        digit = __shfl_sync(KNNG_FULL_MASK, digit, owner);
+        before = __shfl_sync(KNNG_FULL_MASK, before, owner);
+        inbin = __shfl_sync(KNNG_FULL_MASK, inbin, owner);
+        prefix |= (uint64_t)digit << shift;
+        mask |= (uint64_t)0xFF << shift;
+        rank -= (int)before;
+        __syncwarp();
+        if ((uint32_t)rank == inbin || shift == 0) {
+            const uint64_t low = shift ? ((1ull << shift) - 1) : 0ull;
+            return prefix | low;
+        }
+    }
+}
+
+// Writes the indices of the keys <= thr, in index order, to out[] (shared or
+// global memory); returns their count.  Collective: all 32 lanes.
+template <class KeyFn>
+__device__ int warp_compact_le(const KeyFn& key, int cnt, uint64_t thr, int* out)
+{
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    for (int it = 0; it < cnt; it += 32) {
+        const int idx = it + lane;
+        const bool sel = idx < cnt && key(idx) <= thr;
+        const uint32_t b = __ballot_sync(KNNG_FULL_MASK, sel);
+        if (sel) out[base + __popc(b & lanemask_lt())] = idx;
+        base += __popc(b);
+    }
+    return base;
+}
+
+// Open-addressing set of point ids in shared memory (EMPTY = -1), linear
+// probing, multiplicative hash on the high bits.  Returns true if id was not
+// yet present.  The caller sizes the table above the number of insertions,
+// so the probe loop always finds a free slot or the id.
+__device__ __forceinline__ bool hash_insert(int* tab, uint32_t hshift, uint32_t hmask, int id)
+{
+    uint32_t h = ((uint32_t)id * 0x9E3779B1u) >> hshift;
+    while (true) {
+        const int old = atomicCAS(&tab[h], -1, id);
+        if (old == -1) return true;
+        if (old == id) return false;
+        h = (h + 1) & hmask;
+    }
+}
+
+}  // namespace knng

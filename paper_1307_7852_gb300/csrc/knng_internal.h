@@ -1,0 +1,125 @@
+// Host-side plan of a partition tree and the launchers of every stage.
+// Not part of the public ABI (include/knng.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace knng {
+
+// A node that is split at its level.  childL/childR index the split nodes of
+// the next level, or are -1 when that child is a leaf.
+struct SplitNode {
+    uint32_t v;     // node number within its level (children are 2v, 2v+1)
+    int32_t off;    // first position of the node in the permutation
+    int32_t size;   // number of points (> leaf size)
+    int32_t childL;
+    int32_t childR;
+    int32_t pad[3];
+};
+
+// A slice of a large node, processed by one block in the multi-block split.
+struct Chunk {
+    int32_t node;   // index into the level's split nodes
+    int32_t start;  // absolute position of the slice
+    int32_t len;
+    int32_t first;  // index of the node's first chunk in the level's chunk list
+};
+
+struct SelState {
+    unsigned long long prefix;
+    unsigned long long mask;
+    unsigned long long thr;
+    int32_t rank;
+    int32_t done;
+};
+
+constexpr int kSmallCap = 8192;    // nodes up to this size split in one block
+constexpr int kChunk = 4096;       // slice size of the multi-block split
+constexpr int kMaxLeaf = 512;      // largest leaf size g
+constexpr int kMaxK = 64;
+constexpr int kMaxT = 32;
+
+struct LevelPlan {
+    int64_t node_base;   // offset of this level's SplitNode array in the plan table
+    int32_t nnodes;
+    int32_t max_size;
+    bool small;          // every split node <= kSmallCap
+    int64_t chunk_base;  // offset of this level's Chunk array (large levels)
+    int32_t nchunks;
+};
+
+// Shape of every tree over n points with leaf size g (shared by all trees).
+struct TreePlan {
+    int64_t n = -1;
+    int g = -1;
+    std::vector<LevelPlan> levels;
+    std::vector<SplitNode> nodes;  // all levels, concatenated
+    std::vector<Chunk> chunks;     // large levels, concatenated
+    std::vector<int32_t> leaf_off; // nleaves + 1
+    int32_t max_nodes = 0;         // widest level
+    int32_t max_chunks = 0;
+    int32_t max_big_nodes = 0;     // widest level split by the multi-block path
+    int32_t max_leaf = 0;          // largest leaf
+};
+
+void make_tree_plan(int64_t n, int g, TreePlan& plan);
+
+// Device copy of a TreePlan.
+struct DevPlan {
+    const SplitNode* nodes = nullptr;
+    const Chunk* chunks = nullptr;
+    const int32_t* leaf_off = nullptr;
+};
+
+// Bump allocator over the handle's workspace.  With base == nullptr it only
+// measures.
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct XDesc {
+    const void* X;
+    int dtype;  // 0 f32, 1 f16
+    int64_t n;
+    int d;
+    int64_t ld;
+    bool vec;
+};
+
+// ---- stages (each carves its scratch from the arena) -------------------
+cudaError_t run_partition(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
+                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st);
+
+cudaError_t run_leaf_knn(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
+                         const int32_t* perm, int k, int precision, int rescore_mult,
+                         int32_t* ids, float* dists, Arena& ar, cudaStream_t st);
+
+cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
+                      int32_t* ids, float* dists, cudaStream_t st);
+
+cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
+                          const float* d_in, int32_t* ids, float* dists, cudaStream_t st);
+
+cudaError_t run_exact_knn(const XDesc& x, const int32_t* queries, int nq, int k, int32_t* ids,
+                          float* dists, cudaStream_t st);
+
+int num_sms();
+
+// Count of kernels this library has launched (all handles, all devices).
+void note_launches(int count);
+unsigned long long launch_count();
+
+}  // namespace knng

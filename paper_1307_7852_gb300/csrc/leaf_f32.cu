@@ -1,0 +1,221 @@
+// Leaf graphs, FP32 candidate stage (Sec. 3.1 of arXiv:1307.7852: a brute-
+// force k-NN graph inside every leaf subset).
+//
+// One block per (leaf, tree).  For every block of 32 rows of the leaf:
+//   1. Gram S = X_rows X_leaf^T in FP32 SIMT (register-tiled, K in slices of
+//      32 staged transposed in shared memory), D~ = |x|^2 + |y|^2 - 2 S;
+//   2. one warp per row picks the k' smallest (D~, id) by radix select;
+//   3. the k' candidates are rescored by the canonical FP32 direct-difference
+//      distance and sorted; the k best are written.
+// Leaf members are in ascending id order, so a local index ranks like the id.
+#include <algorithm>
+
+#include "knng_common.cuh"
+#include "knng_internal.h"
+
+namespace knng {
+
+namespace {
+constexpr int kRB = 32;   // rows per block pass
+constexpr int kKC = 32;   // K slice
+constexpr int kNT = 256;  // threads
+constexpr int kCandCap = 128;
+
+struct LeafSmem {
+    int32_t* lid;
+    float* nrm;
+    float* Bt;
+    float* D;
+    uint32_t* hist;  // 256 per warp
+    int* cand;       // kCandCap per warp
+};
+
+__host__ __device__ inline size_t leaf_smem_bytes(int m_pad)
+{
+    return sizeof(int32_t) * m_pad + sizeof(float) * m_pad + sizeof(float) * kKC * (m_pad + 1) +
+           sizeof(float) * kRB * m_pad + (kNT / 32) * (256 * sizeof(uint32_t) + kCandCap * sizeof(int));
+}
+}  // namespace
+
+template <int CT, int E, bool kF16>
+__global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, int64_t n,
+                                                           const int32_t* __restrict__ perm,
+                                                           const int32_t* __restrict__ leaf_off, int k,
+                                                           int kp, int32_t* __restrict__ out_ids,
+                                                           float* __restrict__ out_d)
+{
+    constexpr int m_pad = 32 * CT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafSmem sm;
+    {
+        unsigned char* p = smem_raw;
+        sm.lid = reinterpret_cast<int32_t*>(p); p += sizeof(int32_t) * m_pad;
+        sm.nrm = reinterpret_cast<float*>(p); p += sizeof(float) * m_pad;
+        sm.Bt = reinterpret_cast<float*>(p); p += sizeof(float) * kKC * (m_pad + 1);
+        sm.D = reinterpret_cast<float*>(p); p += sizeof(float) * kRB * m_pad;
+        sm.hist = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * 256 * (kNT / 32);
+        sm.cand = reinterpret_cast<int*>(p);
+    }
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tx = tid & 31, ty = tid >> 5;
+    const int t = blockIdx.y;
+    const int b = leaf_off[blockIdx.x];
+    const int m = leaf_off[blockIdx.x + 1] - b;
+    const int32_t* prow = perm + (int64_t)t * n + b;
+    for (int j = tid; j < m_pad; j += kNT) {
+        sm.lid[j] = j < m ? prow[j] : -1;
+        sm.nrm[j] = 0.f;
+    }
+    __syncthreads();
+    // squared norms (any order: they only feed the candidate distances)
+    for (int r = w; r < m; r += kNT / 32) {
+        float s = 0.f;
+        for (int j = 4 * lane; j < L.d; j += 128) {
+            const float4 x = L.load4(sm.lid[r], j);
+            s = fmaf(x.x, x.x, s); s = fmaf(x.y, x.y, s); s = fmaf(x.z, x.z, s); s = fmaf(x.w, x.w, s);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
+        if (lane == 0) sm.nrm[r] = s;
+    }
+    const int want = min(kp, m - 1);
+    uint32_t* hist = sm.hist + 256 * w;
+    int* cand = sm.cand + kCandCap * w;
+    constexpr int mp1 = m_pad + 1;
+
+    for (int rb = 0; rb < m; rb += kRB) {
+        float acc[4][CT];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[rr][c] = 0.f;
+        for (int k0 = 0; k0 < L.d; k0 += kKC) {
+            __syncthreads();
+            for (int idx = tid; idx < m_pad * kKC; idx += kNT) {
+                const int row = idx / kKC, kk = idx % kKC;
+                float v = 0.f;
+                if (row < m && k0 + kk < L.d) v = L.load1(sm.lid[row], k0 + kk);
+                sm.Bt[kk * mp1 + row] = v;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < kKC; ++kk) {
+                float a[4], bb[CT];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) a[rr] = sm.Bt[kk * mp1 + rb + ty * 4 + rr];
+#pragma unroll
+                for (int c = 0; c < CT; ++c) bb[c] = sm.Bt[kk * mp1 + tx + 32 * c];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) acc[rr][c] = fmaf(a[rr], bb[c], acc[rr][c]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int r = ty * 4 + rr;
+            const float ni = sm.nrm[min(rb + r, m_pad - 1)];
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const int col = tx + 32 * c;
+                sm.D[r * m_pad + col] = ni + sm.nrm[col] - 2.f * acc[rr][c];
+            }
+        }
+        __syncthreads();
+        for (int r = w; r < kRB; r += kNT / 32) {
+            const int row = rb + r;
+            if (row >= m) break;
+            const float* Drow = sm.D + r * m_pad;
+            auto key = [&](int j) -> uint64_t {
+                return j == row ? kKeyMax : pack_key(Drow[j], (uint32_t)j);
+            };
+            int nsel = 0;
+            if (want > 0) {
+                const uint64_t thr = warp_select_threshold(key, m, want, hist);
+                nsel = warp_compact_le(key, m, thr, cand);
+            }
+            __syncwarp();
+            uint64_t v[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = kKeyMax;
+            const int gi = sm.lid[row];
+            for (int c = 0; c < nsel; ++c) {
+                const int gj = sm.lid[cand[c]];
+                const float dd = warp_canon_dist(L, gi, gj);
+                const uint64_t kv = pack_key(dd, (uint32_t)gj);
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (lane * E + e == c) v[e] = kv;
+            }
+            warp_bitonic_sort<E>(v);
+            int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
+            float* od = out_d + ((int64_t)t * n + gi) * k;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane * E + e;
+                if (i < k) {
+                    const bool ok = i < nsel;
+                    oi[i] = ok ? (int32_t)(uint32_t)v[e] : -1;
+                    od[i] = ok ? unord_key((uint32_t)(v[e] >> 32)) : __int_as_float(0x7f800000);
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int CT, int E, bool kF16>
+static cudaError_t launch_leaf_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                                   const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
+                                   cudaStream_t st)
+{
+    const size_t smem = leaf_smem_bytes(32 * CT);
+    auto kern = leaf_knn_f32_kernel<CT, E, kF16>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)leaf_smem_bytes(32 * CT));
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    RowLoader<kF16> rl{x.X, x.ld, x.d, x.vec};
+    const int nleaves = (int)P.leaf_off.size() - 1;
+    kern<<<dim3(nleaves, T), kNT, smem, st>>>(rl, x.n, perm, dp.leaf_off, k, kp, ids, dists);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <int CT, bool kF16>
+static cudaError_t dispatch_e(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                              const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
+                              cudaStream_t st)
+{
+    if (kp <= 32) return launch_leaf_f32<CT, 1, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (kp <= 64) return launch_leaf_f32<CT, 2, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    return launch_leaf_f32<CT, 4, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+}
+
+template <bool kF16>
+static cudaError_t dispatch_ct(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                               const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
+                               cudaStream_t st)
+{
+    const int m = P.max_leaf;
+    if (m <= 32) return dispatch_e<1, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 64) return dispatch_e<2, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 128) return dispatch_e<4, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 256) return dispatch_e<8, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    return dispatch_e<16, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+}
+
+cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                             const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
+                             cudaStream_t st)
+{
+    if (kp > kCandCap) kp = kCandCap;
+    if (x.dtype == 1) return dispatch_ct<true>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    return dispatch_ct<false>(x, P, dp, T, perm, k, kp, ids, dists, st);
+}
+
+}  // namespace knng

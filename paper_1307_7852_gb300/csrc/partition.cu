@@ -1,0 +1,575 @@
+// Random divisions (Sec. 3.1 of arXiv:1307.7852; split rule of the appendix
+// after Lemma 1): every tree recursively bisects its nodes at the median of
+// the projections onto a Philox random direction, until a node holds at most
+// g points.
+//
+// GPU form: all T trees advance together, one level per step.
+//   1. gen_dirs   -- the directions of the level's split nodes, from Philox.
+//   2. project    -- one warp per point reads the point's row ONCE and
+//                    projects it on the direction of its node in every tree
+//                    (fixed-order FP32, bit-identical to the CPU definition);
+//                    the 32-bit key lands at the point's current position.
+//   3. select     -- per node, the floor(m/2)-th smallest 64-bit key
+//                    (ord(s) << 32 | id) by radix select: one block per node
+//                    for nodes <= kSmallCap, otherwise block-private
+//                    histograms merged in global memory, one digit per pass.
+//   4. scatter    -- stable partition of each node into its two children.
+// Stability makes every node's segment ascend by id, so the leaves come out
+// in canonical order without a final sort.
+#include <algorithm>
+
+#include "knng_common.cuh"
+#include "knng_internal.h"
+
+namespace knng {
+
+// ---------------------------------------------------------------------------
+// Host: the tree shape.  Sizes at a level are floor/ceil halves, so the
+// shape depends on (n, g) only and is shared by all trees.
+// ---------------------------------------------------------------------------
+void make_tree_plan(int64_t n, int g, TreePlan& P)
+{
+    P.n = n;
+    P.g = g;
+    P.levels.clear();
+    P.nodes.clear();
+    P.chunks.clear();
+    P.leaf_off.clear();
+    P.max_nodes = 0;
+    P.max_chunks = 0;
+    P.max_big_nodes = 0;
+    P.max_leaf = 0;
+
+    struct Tmp { uint32_t v; int64_t off, size; };
+    std::vector<Tmp> cur;
+    std::vector<std::pair<int64_t, int64_t>> leaves;  // (off, size)
+    if (n > g) cur.push_back({0u, 0, n});
+    else leaves.push_back({0, n});
+    while (!cur.empty()) {
+        LevelPlan L;
+        L.node_base = (int64_t)P.nodes.size();
+        L.nnodes = (int32_t)cur.size();
+        L.max_size = 0;
+        std::vector<Tmp> nxt;
+        for (const Tmp& t : cur) {
+            SplitNode s{};
+            s.v = t.v;
+            s.off = (int32_t)t.off;
+            s.size = (int32_t)t.size;
+            const int64_t ml = t.size / 2, mr = t.size - ml;
+            if (ml > g) { s.childL = (int32_t)nxt.size(); nxt.push_back({2 * t.v, t.off, ml}); }
+            else { s.childL = -1; leaves.push_back({t.off, ml}); }
+            if (mr > g) { s.childR = (int32_t)nxt.size(); nxt.push_back({2 * t.v + 1, t.off + ml, mr}); }
+            else { s.childR = -1; leaves.push_back({t.off + ml, mr}); }
+            P.nodes.push_back(s);
+            if (t.size > L.max_size) L.max_size = (int32_t)t.size;
+        }
+        L.small = L.max_size <= kSmallCap;
+        L.chunk_base = (int64_t)P.chunks.size();
+        L.nchunks = 0;
+        if (!L.small) {
+            for (int32_t s = 0; s < L.nnodes; ++s) {
+                const SplitNode& sn = P.nodes[L.node_base + s];
+                const int32_t first = L.nchunks;
+                for (int64_t a = 0; a < sn.size; a += kChunk) {
+                    Chunk c;
+                    c.node = s;
+                    c.start = (int32_t)(sn.off + a);
+                    c.len = (int32_t)std::min<int64_t>(kChunk, sn.size - a);
+                    c.first = first;
+                    P.chunks.push_back(c);
+                    ++L.nchunks;
+                }
+            }
+        }
+        P.max_nodes = std::max(P.max_nodes, L.nnodes);
+        if (!L.small) P.max_big_nodes = std::max(P.max_big_nodes, L.nnodes);
+        P.max_chunks = std::max(P.max_chunks, L.nchunks);
+        P.levels.push_back(L);
+        cur.swap(nxt);
+    }
+    std::sort(leaves.begin(), leaves.end());
+    for (auto& l : leaves) {
+        P.leaf_off.push_back((int32_t)l.first);
+        P.max_leaf = std::max<int32_t>(P.max_leaf, (int32_t)l.second);
+    }
+    P.leaf_off.push_back((int32_t)n);
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+__global__ void init_perm_kernel(int64_t n, int T, int first_node, int32_t* perm, int32_t* pos_of,
+                                 int32_t* node_of)
+{
+    const int64_t total = (int64_t)T * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)(e % n);
+        perm[e] = i;
+        pos_of[e] = i;
+        node_of[e] = first_node;
+    }
+}
+
+// dirs[t][s][0..d_pad): direction of split node s of this level in tree t.
+__global__ void gen_dirs_kernel(float* dirs, int T, int S, int d, int d_pad,
+                                const SplitNode* nodes, uint32_t level, uint64_t seed)
+{
+    const int q4 = d_pad / 4;
+    const int64_t total = (int64_t)T * S * q4;
+    const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e % q4);
+        const int s = (int)((e / q4) % S);
+        const int t = (int)(e / ((int64_t)q4 * S));
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)t, level, nodes[s].v, (uint32_t)q), key);
+        const int j = 4 * q;
+        float4 a;
+        a.x = (j + 0 < d) ? tri_entry(w.x) : 0.f;
+        a.y = (j + 1 < d) ? tri_entry(w.y) : 0.f;
+        a.z = (j + 2 < d) ? tri_entry(w.z) : 0.f;
+        a.w = (j + 3 < d) ? tri_entry(w.w) : 0.f;
+        reinterpret_cast<float4*>(dirs)[e] = a;
+    }
+}
+
+// One warp per point; up to 8 trees per pass over the row.  The projection
+// order is the canonical one: lane l, j = 128c + 4l + e, fmaf, then the
+// pairwise rounds 16..1.
+template <bool kF16>
+__global__ void __launch_bounds__(256) project_kernel(RowLoader<kF16> L, int64_t n, int T,
+                                                      const float* __restrict__ dirs, int S,
+                                                      int d_pad, const int32_t* __restrict__ node_of,
+                                                      const int32_t* __restrict__ pos_of,
+                                                      uint32_t* __restrict__ keys)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        for (int t0 = 0; t0 < T; t0 += 8) {
+            const int tl = t0 + lane;
+            const int my_s = (lane < 8 && tl < T) ? node_of[(int64_t)tl * n + i] : -1;
+            if (__ballot_sync(KNNG_FULL_MASK, my_s >= 0) == 0) continue;
+            int sv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[u] = __shfl_sync(KNNG_FULL_MASK, my_s, u);
+            float acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = 0.0f;
+            for (int j = 4 * lane; j < L.d; j += 128) {
+                const float4 x = L.load4(i, j);
+                const bool full = j + 3 < L.d;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (sv[u] < 0) continue;
+                    const float4 a = *reinterpret_cast<const float4*>(
+                        dirs + ((int64_t)(t0 + u) * S + sv[u]) * d_pad + j);
+                    if (full) {
+                        acc[u] = fmaf(x.x, a.x, acc[u]);
+                        acc[u] = fmaf(x.y, a.y, acc[u]);
+                        acc[u] = fmaf(x.z, a.z, acc[u]);
+                        acc[u] = fmaf(x.w, a.w, acc[u]);
+                    } else {
+                        acc[u] = fmaf(x.x, a.x, acc[u]);
+                        if (j + 1 < L.d) acc[u] = fmaf(x.y, a.y, acc[u]);
+                        if (j + 2 < L.d) acc[u] = fmaf(x.z, a.z, acc[u]);
+                    }
+                }
+            }
+            float mine = 0.0f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) acc[u] += __shfl_xor_sync(KNNG_FULL_MASK, acc[u], o);
+                if (lane == u) mine = acc[u];
+            }
+            if (my_s >= 0) {
+                const int64_t row = (int64_t)tl * n;
+                keys[row + pos_of[row + i]] = ord_key(mine);
+            }
+        }
+    }
+}
+
+// ---- block radix select (one block, keys in shared memory) ---------------
+template <int NT>
+__device__ unsigned long long block_select(const unsigned long long* k64, int m, int want,
+                                           uint32_t* hist, uint32_t* bcast)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    unsigned long long prefix = 0, mask = 0;
+    int rank = want;
+    for (int shift = 56;; shift -= 8) {
+        for (int b = tid; b < 256; b += NT) hist[b] = 0;
+        __syncthreads();
+        for (int e = tid; e < m; e += NT) {
+            const unsigned long long kv = k64[e];
+            if ((kv & mask) == prefix) atomicAdd(&hist[(kv >> shift) & 0xFF], 1u);
+        }
+        __syncthreads();
+        if (w == 0) {
+            uint32_t c[8], lsum = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) { c[b] = hist[lane * 8 + b]; lsum += c[b]; }
+            uint32_t incl = lsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(KNNG_FULL_MASK, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t excl = incl - lsum;
+            if (excl < (uint32_t)rank && (uint32_t)rank <= incl) {
+                uint32_t run = excl;
+                bool found = false;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    if (!found && run < (uint32_t)rank && (uint32_t)rank <= run + c[b]) {
+                        bcast[0] = lane * 8 + b;
+                        bcast[1] = run;
+                        bcast[2] = c[b];
+                        found = true;
+                    }
+                    run += c[b];
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t digit = bcast[0], before = bcast[1], inbin = bcast[2];
+        prefix |= (unsigned long long)digit << shift;
+        mask |= 0xFFull << shift;
+        rank -= (int)before;
+        __syncthreads();
+        if ((uint32_t)rank == inbin || shift == 0)
+            return prefix | (shift ? ((1ull << shift) - 1) : 0ull);
+    }
+}
+
+// Exclusive block scan of one int per thread; returns the prefix, and the
+// total in *total.
+template <int NT>
+__device__ int block_excl_scan(int v, int* sh, int* total)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(KNNG_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < NT / 32 ? sh[lane] : 0;
+        int si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(KNNG_FULL_MASK, si, o);
+            if (lane >= o) si += t;
+        }
+        if (lane < NT / 32) sh[lane] = si - s;
+        if (lane == NT / 32 - 1) sh[32] = si;
+    }
+    __syncthreads();
+    const int r = sh[w] + incl - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Stable two-way scatter of elements [0, len) of a slice (keys in shared
+// memory), contiguous runs per thread.  lbase/rbase: destination of the
+// slice's first left / right element.
+template <int NT>
+__device__ void stable_scatter(const unsigned long long* k64, int len, unsigned long long thr,
+                               int32_t lbase, int32_t rbase, int32_t childL, int32_t childR,
+                               int32_t* perm_nxt, int32_t* pos_of, int32_t* node_of, int* sh)
+{
+    const int tid = threadIdx.x;
+    const int per = (len + NT - 1) / NT;
+    const int e0 = min(len, tid * per), e1 = min(len, e0 + per);
+    int cl = 0;
+    for (int e = e0; e < e1; ++e) cl += (k64[e] <= thr);
+    int total;
+    const int lb = block_excl_scan<NT>(cl, sh, &total);
+    int lp = lbase + lb, rp = rbase + (e0 - lb);
+    for (int e = e0; e < e1; ++e) {
+        const unsigned long long kv = k64[e];
+        const int32_t id = (int32_t)(uint32_t)kv;
+        int32_t dst, child;
+        if (kv <= thr) { dst = lp++; child = childL; }
+        else { dst = rp++; child = childR; }
+        perm_nxt[dst] = id;
+        pos_of[id] = dst;
+        node_of[id] = child;
+    }
+}
+
+// One block per (split node, tree), node <= kSmallCap points.
+template <int NT>
+__global__ void __launch_bounds__(NT) split_small_kernel(int64_t n, const SplitNode* __restrict__ nodes,
+                                                         const uint32_t* __restrict__ keys,
+                                                         const int32_t* __restrict__ perm_cur,
+                                                         int32_t* perm_nxt, int32_t* pos_of,
+                                                         int32_t* node_of)
+{
+    extern __shared__ unsigned long long k64[];
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t bcast[4];
+    __shared__ int sh[33];
+    const SplitNode nd = nodes[blockIdx.x];
+    const int64_t row = (int64_t)blockIdx.y * n;
+    const int m = nd.size;
+    for (int e = threadIdx.x; e < m; e += NT)
+        k64[e] = ((unsigned long long)keys[row + nd.off + e] << 32) | (uint32_t)perm_cur[row + nd.off + e];
+    __syncthreads();
+    const unsigned long long thr = block_select<NT>(k64, m, m / 2, hist, bcast);
+    stable_scatter<NT>(k64, m, thr, nd.off, nd.off + m / 2, nd.childL, nd.childR, perm_nxt + row,
+                       pos_of + row, node_of + row, sh);
+}
+
+// ---- multi-block split of large nodes ------------------------------------
+__global__ void big_init_kernel(int S, int T, const SplitNode* nodes, SelState* st)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S * T) return;
+    SelState s;
+    s.prefix = 0;
+    s.mask = 0;
+    s.thr = 0;
+    s.rank = nodes[e % S].size / 2;
+    s.done = 0;
+    st[e] = s;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) big_hist_kernel(int64_t n, int shift, int S, const Chunk* __restrict__ chunks,
+                                                      const uint32_t* __restrict__ keys,
+                                                      const int32_t* __restrict__ perm,
+                                                      const SelState* __restrict__ st, uint32_t* ghist)
+{
+    __shared__ uint32_t h[256];
+    const Chunk c = chunks[blockIdx.x];
+    const int t = blockIdx.y;
+    const SelState s = st[(int64_t)t * S + c.node];
+    if (s.done) return;
+    for (int b = threadIdx.x; b < 256; b += NT) h[b] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)t * n + c.start;
+    for (int e = threadIdx.x; e < c.len; e += NT) {
+        const unsigned long long kv = ((unsigned long long)keys[base + e] << 32) | (uint32_t)perm[base + e];
+        if ((kv & s.mask) == s.prefix) atomicAdd(&h[(kv >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    uint32_t* g = ghist + ((int64_t)t * S + c.node) * 256;
+    for (int b = threadIdx.x; b < 256; b += NT)
+        if (h[b]) atomicAdd(&g[b], h[b]);
+}
+
+// One warp per (node, tree): choose the digit of this pass.
+__global__ void big_pick_kernel(int shift, int S, SelState* st, uint32_t* ghist)
+{
+    const int lane = threadIdx.x;
+    const int64_t e = (int64_t)blockIdx.y * S + blockIdx.x;
+    SelState s = st[e];
+    if (s.done) return;
+    uint32_t* h = ghist + e * 256;
+    uint32_t c[8], lsum = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) { c[b] = h[lane * 8 + b]; lsum += c[b]; h[lane * 8 + b] = 0; }
+    uint32_t incl = lsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(KNNG_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t excl = incl - lsum;
+    const uint32_t rank = (uint32_t)s.rank;
+    const bool mine = excl < rank && rank <= incl;
+    const uint32_t owner = __ffs(__ballot_sync(KNNG_FULL_MASK, mine)) - 1;
+    uint32_t digit = 0, before = 0, inbin = 0;
+    if (mine) {
+        uint32_t run = excl;
+        bool found = false;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (!found && run < rank && rank <= run + c[b]) {
+                digit = lane * 8 + b; before = run; inbin = c[b]; found = true;
+            }
+            run += c[b];
+        }
+    }
+    digit = __shfl_sync(KNNG_FULL_MASK, digit, owner);
+    before = __shfl_sync(KNNG_FULL_MASK, before, owner);
+    inbin = __shfl_sync(KNNG_FULL_MASK, inbin, owner);
+    if (lane == 0) {
+        s.prefix |= (unsigned long long)digit << shift;
+        s.mask |= 0xFFull << shift;
+        s.rank -= (int)before;
+        if ((uint32_t)s.rank == inbin || shift == 0) {
+            s.done = 1;
+            s.thr = s.prefix | (shift ? ((1ull << shift) - 1) : 0ull);
+        }
+        st[e] = s;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) big_count_kernel(int64_t n, int S, int nchunks, const Chunk* __restrict__ chunks,
+                                                       const uint32_t* __restrict__ keys,
+                                                       const int32_t* __restrict__ perm,
+                                                       const SelState* __restrict__ st, int32_t* cnt)
+{
+    __shared__ int sh[33];
+    const Chunk c = chunks[blockIdx.x];
+    const int t = blockIdx.y;
+    const unsigned long long thr = st[(int64_t)t * S + c.node].thr;
+    const int64_t base = (int64_t)t * n + c.start;
+    int v = 0;
+    for (int e = threadIdx.x; e < c.len; e += NT) {
+        const unsigned long long kv = ((unsigned long long)keys[base + e] << 32) | (uint32_t)perm[base + e];
+        v += kv <= thr;
+    }
+    int total;
+    block_excl_scan<NT>(v, sh, &total);
+    if (threadIdx.x == 0) cnt[(int64_t)t * nchunks + blockIdx.x] = total;
+}
+
+// One thread per (node, tree): exclusive scan of the node's chunk counts
+// (in place: counts in, left-destination offsets out).  A node's chunks are
+// contiguous in the level's chunk list; the first is found by bisection.
+__global__ void big_base_kernel(int S, int T, int nchunks, const Chunk* __restrict__ chunks,
+                                int32_t* cnt_to_base)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= S * T) return;
+    const int s = e % S, t = e / S;
+    int lo = 0, hi = nchunks;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (chunks[mid].node < s) lo = mid + 1; else hi = mid;
+    }
+    int run = 0;
+    int32_t* row = cnt_to_base + (int64_t)t * nchunks;
+    for (int c = lo; c < nchunks && chunks[c].node == s; ++c) {
+        const int v = row[c];
+        row[c] = run;
+        run += v;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) big_scatter_kernel(int64_t n, int S, int nchunks, const Chunk* __restrict__ chunks,
+                                                         const SplitNode* __restrict__ nodes,
+                                                         const uint32_t* __restrict__ keys,
+                                                         const int32_t* __restrict__ perm_cur,
+                                                         const SelState* __restrict__ st,
+                                                         const int32_t* __restrict__ lbase_arr,
+                                                         int32_t* perm_nxt, int32_t* pos_of, int32_t* node_of)
+{
+    __shared__ unsigned long long k64[kChunk];
+    __shared__ int sh[33];
+    const Chunk c = chunks[blockIdx.x];
+    const int t = blockIdx.y;
+    const SplitNode nd = nodes[c.node];
+    const unsigned long long thr = st[(int64_t)t * S + c.node].thr;
+    const int64_t row = (int64_t)t * n;
+    for (int e = threadIdx.x; e < c.len; e += NT)
+        k64[e] = ((unsigned long long)keys[row + c.start + e] << 32) | (uint32_t)perm_cur[row + c.start + e];
+    __syncthreads();
+    const int32_t lb = lbase_arr[(int64_t)t * nchunks + blockIdx.x];
+    const int32_t before = c.start - nd.off;
+    stable_scatter<NT>(k64, c.len, thr, nd.off + lb, nd.off + nd.size / 2 + (before - lb), nd.childL,
+                       nd.childR, perm_nxt + row, pos_of + row, node_of + row, sh);
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+static inline int grid_for(int64_t work, int per_block, int cap)
+{
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st)
+{
+    const int64_t n = x.n;
+    const int d_pad = (x.d + 3) & ~3;
+    const int S_max = std::max(P.max_nodes, 1);
+    int32_t* perm_a = ar.take<int32_t>((size_t)T * n);
+    int32_t* perm_b = ar.take<int32_t>((size_t)T * n);
+    int32_t* pos_of = ar.take<int32_t>((size_t)T * n);
+    int32_t* node_of = ar.take<int32_t>((size_t)T * n);
+    uint32_t* keys = ar.take<uint32_t>((size_t)T * n);
+    float* dirs = ar.take<float>((size_t)T * S_max * d_pad);
+    const int S_big = std::max(P.max_big_nodes, 1);
+    SelState* sel = ar.take<SelState>((size_t)T * S_big);
+    uint32_t* ghist = ar.take<uint32_t>((size_t)T * S_big * 256);
+    int32_t* cnt = ar.take<int32_t>((size_t)T * std::max(P.max_chunks, 1));
+    if (!ar.base) return cudaSuccess;  // measuring only
+
+    const int sms = num_sms();
+    const int gcap = sms * 32;
+    init_perm_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, P.levels.empty() ? -1 : 0,
+                                                                          perm_a, pos_of, node_of);
+    note_launches(1);
+    int32_t* cur = perm_a;
+    int32_t* nxt = perm_b;
+    for (size_t lvl = 0; lvl < P.levels.size(); ++lvl) {
+        const LevelPlan& L = P.levels[lvl];
+        const SplitNode* nodes = dp.nodes + L.node_base;
+        const int S = L.nnodes;
+        gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(
+            dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed);
+            note_launches(1);
+        const int pgrid = grid_for(n * 32, 256, sms * 16);
+        if (x.dtype == 1) {
+            RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
+            project_kernel<true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
+            note_launches(1);
+        } else {
+            RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
+            project_kernel<false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
+            note_launches(1);
+        }
+        // leaves of this level keep their positions: start from a copy
+        cudaMemcpyAsync(nxt, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);
+        if (L.small) {
+            constexpr int NT = 512;
+            const size_t smem = sizeof(unsigned long long) * (size_t)L.max_size;
+            split_small_kernel<NT><<<dim3(S, T), NT, smem, st>>>(n, nodes, keys, cur, nxt, pos_of, node_of);
+            note_launches(1);
+        } else {
+            constexpr int NT = 256;
+            const Chunk* chunks = dp.chunks + L.chunk_base;
+            const int NC = L.nchunks;
+            big_init_kernel<<<(S * T + 255) / 256, 256, 0, st>>>(S, T, nodes, sel);
+            note_launches(1);
+            cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * (size_t)T * S * 256, st);
+            for (int shift = 56; shift >= 0; shift -= 8) {
+                big_hist_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, shift, S, chunks, keys, cur, sel, ghist);
+                note_launches(1);
+                big_pick_kernel<<<dim3(S, T), 32, 0, st>>>(shift, S, sel, ghist);
+                note_launches(1);
+            }
+            big_count_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, S, NC, chunks, keys, cur, sel, cnt);
+            note_launches(1);
+            big_base_kernel<<<(S * T + 127) / 128, 128, 0, st>>>(S, T, NC, chunks, cnt);
+            note_launches(1);
+            big_scatter_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, S, NC, chunks, nodes, keys, cur, sel, cnt,
+                                                               nxt, pos_of, node_of);
+            note_launches(1);
+        }
+        std::swap(cur, nxt);
+    }
+    cudaMemcpyAsync(perm_out, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
+}
+
+}  // namespace knng

@@ -1,0 +1,172 @@
+// Neighbourhood propagation (Sec. 3.2 of arXiv:1307.7852), in the first-order
+// form analysed by Theorem 1: in one synchronous round every point p takes
+// the k best of its own list and of the lists of its neighbours, without p.
+//
+// One warp per point.  Candidate ids are deduplicated in a shared-memory hash
+// set (the per-point replacement of the paper's hash table of evaluated pairs,
+// Sec. 3.4 "Speedup"); ids already in p's list keep their distance, new ids
+// are scored by the canonical FP32 distance (vectorised, coalesced row loads:
+// each lane reads 16 bytes per 128-entry chunk of the row).  The k best by
+// (dist, id) are found by warp radix select and sorted by a warp bitonic sort.
+#include "knng_common.cuh"
+#include "knng_internal.h"
+
+namespace knng {
+
+struct PropLayout {
+    int H;       // hash slots (power of two)
+    int hshift;  // 32 - log2(H)
+    int cap;     // candidate capacity = k + k*k
+    size_t per_warp;
+};
+
+static PropLayout prop_layout(int k)
+{
+    PropLayout L;
+    L.cap = k + k * k;
+    int H = 64;
+    while (H < 2 * (L.cap + 1)) H <<= 1;
+    L.H = H;
+    int lg = 0;
+    while ((1 << lg) < H) ++lg;
+    L.hshift = 32 - lg;
+    L.per_warp = sizeof(int) * (size_t)H + (sizeof(int) + sizeof(float)) * (size_t)L.cap +
+                 sizeof(uint32_t) * 256 + sizeof(int) * 64;
+    L.per_warp = (L.per_warp + 15) & ~(size_t)15;
+    return L;
+}
+
+template <int E, bool kF16>
+__global__ void propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int32_t* __restrict__ order,
+                                 const int32_t* __restrict__ ids_in, const float* __restrict__ d_in,
+                                 int32_t* __restrict__ ids_out, float* __restrict__ d_out, int H,
+                                 int hshift, int cap, int per_warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned char* base = smem_raw + (size_t)w * per_warp_bytes;
+    int* tab = reinterpret_cast<int*>(base);
+    int* cid = tab + H;
+    float* cd = reinterpret_cast<float*>(cid + cap);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(cd + cap);
+    int* sel = reinterpret_cast<int*>(hist + 256);
+    const uint32_t hmask = (uint32_t)H - 1;
+
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wi = gw; wi < n; wi += nw) {
+        const int32_t p = order ? order[wi] : (int32_t)wi;
+        for (int s = lane; s < H; s += 32) tab[s] = -1;
+        __syncwarp();
+        if (lane == 0) hash_insert(tab, (uint32_t)hshift, hmask, p);
+        __syncwarp();
+        int cnt = 0;
+        // p's own list: ids keep their distances
+        for (int e0 = 0; e0 < k; e0 += 32) {
+            const int e = e0 + lane;
+            int32_t id = -1;
+            float dd = 0.f;
+            if (e < k) {
+                id = ids_in[(int64_t)p * k + e];
+                dd = d_in[(int64_t)p * k + e];
+            }
+            if (id >= n) id = -1;  // ids outside [0, n) are treated as empty slots
+            const bool ins = id >= 0 && hash_insert(tab, (uint32_t)hshift, hmask, id);
+            const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
+            if (ins) {
+                const int pos = cnt + __popc(b & lanemask_lt());
+                cid[pos] = id;
+                cd[pos] = dd;
+            }
+            cnt += __popc(b);
+        }
+        const int nknown = cnt;
+        // neighbours' lists
+        for (int e = 0; e < k; ++e) {
+            const int32_t q = ids_in[(int64_t)p * k + e];
+            if (q < 0 || q >= n) continue;
+            for (int f0 = 0; f0 < k; f0 += 32) {
+                const int f = f0 + lane;
+                const int32_t o = f < k ? ids_in[(int64_t)q * k + f] : -1;
+                const bool ins = o >= 0 && o < n && hash_insert(tab, (uint32_t)hshift, hmask, o);
+                const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
+                if (ins) cid[cnt + __popc(b & lanemask_lt())] = o;
+                cnt += __popc(b);
+            }
+        }
+        __syncwarp();
+        // score the new candidates
+        for (int c = nknown; c < cnt; ++c) {
+            const float dd = warp_canon_dist(L, p, cid[c]);
+            if (lane == 0) cd[c] = dd;
+        }
+        __syncwarp();
+        auto key = [&](int idx) -> uint64_t { return pack_key(cd[idx], (uint32_t)cid[idx]); };
+        const int want = min(k, cnt);
+        int nsel = 0;
+        if (want > 0) {
+            const uint64_t thr = warp_select_threshold(key, cnt, want, hist);
+            nsel = warp_compact_le(key, cnt, thr, sel);
+        }
+        __syncwarp();
+        uint64_t v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane * E + e;
+            v[e] = i < nsel ? key(sel[i]) : kKeyMax;
+        }
+        warp_bitonic_sort<E>(v);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane * E + e;
+            if (i < k) {
+                const bool ok = i < nsel;
+                ids_out[(int64_t)p * k + i] = ok ? (int32_t)(uint32_t)v[e] : -1;
+                d_out[(int64_t)p * k + i] = ok ? unord_key((uint32_t)(v[e] >> 32)) : __int_as_float(0x7f800000);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int E, bool kF16>
+static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
+                               const float* d_in, int32_t* ids, float* dists, cudaStream_t st)
+{
+    const PropLayout PL = prop_layout(k);
+    int warps = (int)((200 * 1024) / PL.per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = PL.per_warp * warps;
+    auto kern = propagate_kernel<E, kF16>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)num_sms() * per_sm;
+    const int64_t need = (x.n + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    RowLoader<kF16> rl{x.X, x.ld, x.d, x.vec};
+    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, x.n, k, order, ids_in, d_in, ids, dists, PL.H,
+                                                PL.hshift, PL.cap, (int)PL.per_warp);
+                                                note_launches(1);
+    return cudaGetLastError();
+}
+
+template <bool kF16>
+static cudaError_t prop_dispatch(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
+                                 const float* d_in, int32_t* ids, float* dists, cudaStream_t st)
+{
+    if (k <= 32) return launch_prop<1, kF16>(x, k, order, ids_in, d_in, ids, dists, st);
+    return launch_prop<2, kF16>(x, k, order, ids_in, d_in, ids, dists, st);
+}
+
+cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
+                          const float* d_in, int32_t* ids, float* dists, cudaStream_t st)
+{
+    if (x.dtype == 1) return prop_dispatch<true>(x, k, order, ids_in, d_in, ids, dists, st);
+    return prop_dispatch<false>(x, k, order, ids_in, d_in, ids, dists, st);
+}
+
+}  // namespace knng
