@@ -216,6 +216,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     nev = 4 + R
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(args.steps)]
+    for row in ev:  # torch creates the CUDA event on first record
+        for e_ in row:
+            e_.record(stream)
 
     def step(events=None):
         if events is not None:

@@ -87,6 +87,11 @@ const char* knng_status_string(int32_t status);
 /* Message of the last failure on h ("" if none); valid until the next call. */
 const char* knng_last_error(const knng_handle* h);
 
+/* Synchronises `stream` and reports device-side failures of earlier calls on
+ * h: KNNG_ERR_TIMEOUT if a bounded wait inside a kernel gave up (the outputs
+ * of those calls are then invalid); the flag is cleared. */
+int knng_sync(knng_handle* h, void* stream);
+
 /* ---- tree shape (host only) ------------------------------------------ */
 /* Every split halves a node of m points into floor(m/2) (left) and
  * ceil(m/2) (right) points, so the leaf layout of a tree depends on (n, g)

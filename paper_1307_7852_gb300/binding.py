@@ -58,6 +58,7 @@ SIGNATURES = {
     "knng_exact_knn": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _I32, _P, _P, _P],
     "knng_set_stage_events": [_P, _P, _I32],
     "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
+    "knng_sync": [_P, _P],
 }
 
 
@@ -313,3 +314,10 @@ def knng_launch_counter() -> int:
     if rc != KNNG_OK:
         raise KnngError(rc, "knng_launch_counter")
     return int(out.value)
+
+
+def knng_sync(h: Handle = None, stream=None, device: int = 0):
+    """Synchronise the stream and raise if a bounded device wait gave up."""
+    torch = _torch()
+    h = h or handle(device)
+    h.check(lib().knng_sync(h.ptr, _stream(torch.device("cuda", h.device), stream)), "knng_sync")

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -26,9 +27,6 @@ int num_sms()
     }
     return sms;
 }
-cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
-                             const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
-                             cudaStream_t st);
 }  // namespace knng
 
 using namespace knng;
@@ -42,6 +40,7 @@ struct knng_handle {
     size_t plan_dev_size = 0;
     DevPlan dplan;
     std::vector<cudaEvent_t> stage_ev;
+    int* dev_err = nullptr;  // set by kernels whose bounded waits gave up
     std::string err;
 };
 
@@ -180,14 +179,21 @@ int check_k(knng_handle* h, int32_t k, int32_t g)
     return KNNG_OK;
 }
 
-int leaf_stage(knng_handle* h, const XDesc& x, int T, int g, const int32_t* perm, int k, int prec,
-               int mult, int32_t* ids, float* dists, cudaStream_t st)
+// Leaf graphs of all trees.  With ar.base == nullptr only measures the
+// scratch the stage needs.
+int leaf_stage(knng_handle* h, const XDesc& x, int T, const int32_t* perm, int k, int prec, int mult,
+               int32_t* ids, float* dists, Arena& ar, cudaStream_t st)
 {
-    if (prec != KNNG_PREC_FP32)
-        return fail(h, KNNG_ERR_UNSUPPORTED, "precision %d is not available in this build", prec);
-    (void)mult;
-    (void)g;
-    cudaError_t e = run_leaf_knn_f32(x, h->plan, h->dplan, T, perm, k, k, ids, dists, st);
+    cudaError_t e;
+    const int kp = std::min(mult * k, 128);
+    if (prec == KNNG_PREC_FP32) {
+        if (!ar.base) return KNNG_OK;
+        e = run_leaf_knn_f32(x, h->plan, h->dplan, T, perm, k, kp, ids, dists, st);
+    } else if (prec == KNNG_PREC_BF16 || prec == KNNG_PREC_FP8E4M3) {
+        e = run_leaf_knn_tc(x, h->plan, h->dplan, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st);
+    } else {
+        return fail(h, KNNG_ERR_INVALID_ARG, "precision %d", prec);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "leaf k-NN");
     return KNNG_OK;
 }
@@ -223,6 +229,17 @@ int knng_create(knng_handle** out, int32_t device)
     knng_handle* h = new (std::nothrow) knng_handle();
     if (!h) return KNNG_ERR_INTERNAL;
     h->device = device;
+    {
+        DeviceGuard g(device);
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess || cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            if (p) cudaFree(p);
+            delete h;
+            return KNNG_ERR_OOM;
+        }
+        h->dev_err = static_cast<int*>(p);
+    }
     *out = h;
     return KNNG_OK;
 }
@@ -235,6 +252,7 @@ int knng_destroy(knng_handle* h)
         cudaDeviceSynchronize();
         if (h->ws) cudaFree(h->ws);
         if (h->plan_dev) cudaFree(h->plan_dev);
+        if (h->dev_err) cudaFree(h->dev_err);
     }
     delete h;
     return KNNG_OK;
@@ -298,7 +316,12 @@ int knng_leaf_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((r = ensure_plan(h, n, g, st))) return r;
-    return leaf_stage(h, x, T, g, perm, k, precision, rescore_mult, ids, dists, st);
+    Arena m;
+    if ((r = leaf_stage(h, x, T, perm, k, precision, rescore_mult, ids, dists, m, st))) return r;
+    if ((r = ensure_ws(h, m.off, st))) return r;
+    Arena a;
+    a.base = h->ws;
+    return leaf_stage(h, x, T, perm, k, precision, rescore_mult, ids, dists, a, st);
 }
 
 int knng_merge(knng_handle* h, int64_t n, int32_t T, int32_t k, const int32_t* ids_in,
@@ -372,14 +395,19 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     if ((r = ensure_plan(h, n, p->leaf_size, st))) return r;
     const int T = p->T, k = p->k;
     const size_t nk = (size_t)n * k;
-    // workspace: perm | leaf lists | propagation buffers | partition scratch
+    // workspace: perm | leaf lists | propagation buffers | max(partition, leaf scratch)
     Arena m;
     m.take<int32_t>((size_t)T * n);
     m.take<int32_t>((size_t)T * nk);
     m.take<float>((size_t)T * nk);
     for (int b = 0; b < 2; ++b) { m.take<int32_t>(nk); m.take<float>(nk); }
+    const size_t fixed = m.off;
     run_partition(x, h->plan, h->dplan, T, p->seed, nullptr, m, st);
-    if ((r = ensure_ws(h, m.off, st))) return r;
+    const size_t part_end = m.off;
+    m.off = fixed;
+    if ((r = leaf_stage(h, x, T, nullptr, k, p->precision, p->rescore_mult, nullptr, nullptr, m, st))) return r;
+    const size_t total = std::max(part_end, m.off);
+    if ((r = ensure_ws(h, total, st))) return r;
     Arena a;
     a.base = h->ws;
     int32_t* perm = a.take<int32_t>((size_t)T * n);
@@ -388,6 +416,7 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     int32_t* bi[2];
     float* bd[2];
     for (int b = 0; b < 2; ++b) { bi[b] = a.take<int32_t>(nk); bd[b] = a.take<float>(nk); }
+    const size_t fixed2 = a.off;
     const int R = p->prop_rounds;
     const bool rec = (int)h->stage_ev.size() >= 4 + R;
     auto mark = [&](int i) {
@@ -397,7 +426,8 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     cudaError_t e = run_partition(x, h->plan, h->dplan, T, p->seed, perm, a, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "partition");
     mark(1);
-    if ((r = leaf_stage(h, x, T, p->leaf_size, perm, k, p->precision, p->rescore_mult, li, ld_, st))) return r;
+    a.off = fixed2;  // the partition scratch is dead: the leaf stage reuses it
+    if ((r = leaf_stage(h, x, T, perm, k, p->precision, p->rescore_mult, li, ld_, a, st))) return r;
     mark(2);
     int32_t* mi = R == 0 ? ids : bi[0];
     float* md = R == 0 ? dists : bd[0];
@@ -436,6 +466,22 @@ int knng_exact_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int3
     return KNNG_OK;
 }
 
+int knng_sync(knng_handle* h, void* stream)
+{
+    if (!h) return KNNG_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error word");
+    if (flag) {
+        cudaMemset(h->dev_err, 0, sizeof(int));
+        return fail(h, KNNG_ERR_TIMEOUT, "a bounded device wait gave up; results of the affected calls are invalid");
+    }
+    return KNNG_OK;
+}
+
 int knng_launch_counter(uint64_t* count)
 {
     if (!count) return KNNG_ERR_INVALID_ARG;
@@ -448,7 +494,17 @@ int knng_set_stage_events(knng_handle* h, void* const* events, int32_t nevents)
     if (!h) return KNNG_ERR_INVALID_ARG;
     if (nevents < 0 || (nevents > 0 && !events)) return fail(h, KNNG_ERR_INVALID_ARG, "bad events");
     h->stage_ev.clear();
-    for (int i = 0; i < nevents; ++i) h->stage_ev.push_back(static_cast<cudaEvent_t>(events[i]));
+    DeviceGuard dg(h->device);
+    for (int i = 0; i < nevents; ++i) {
+        cudaEvent_t ev = static_cast<cudaEvent_t>(events[i]);
+        const cudaError_t e = ev ? cudaEventQuery(ev) : cudaErrorInvalidResourceHandle;
+        if (e != cudaSuccess && e != cudaErrorNotReady) {
+            cudaGetLastError();
+            h->stage_ev.clear();
+            return fail(h, KNNG_ERR_INVALID_ARG, "event %d is not a valid CUDA event", i);
+        }
+        h->stage_ev.push_back(ev);
+    }
     return KNNG_OK;
 }
 
@@ -486,9 +542,8 @@ int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int
     }
     cudaFreeAsync(dx, st);
     cudaFreeAsync(dout, st);
-    e = cudaStreamSynchronize(st);
-    if (!r && e != cudaSuccess) r = cuda_fail(h, e, "build");
-    return r;
+    const int rs = knng_sync(h, stream);
+    return r ? r : rs;
 }
 
 }  // extern "C"

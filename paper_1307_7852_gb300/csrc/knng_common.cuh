@@ -285,3 +285,53 @@ __device__ __forceinline__ bool hash_insert(int* tab, uint32_t hshift, uint32_t 
 }
 
 }  // namespace knng
+
+namespace knng {
+
+// Finishes one row of a leaf graph (collective over one warp): from the
+// candidate distances Drow[0..m) (local index j; j == self excluded) pick the
+// kp smallest (D~, j), rescore them with the canonical FP32 distance between
+// the original rows, sort by (D, id) and write the k best to oi/od (padding
+// with -1 / +inf).  lid maps local index -> point id (ascending with j).
+template <int E, bool kF16, class DFn>
+__device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m, int self,
+                                const int32_t* lid, int k, int kp, uint32_t* hist, int* cand,
+                                int32_t* oi, float* od)
+{
+    const int lane = threadIdx.x & 31;
+    auto key = [&](int j) -> uint64_t {
+        return j == self ? kKeyMax : pack_key(Drow(j), (uint32_t)j);
+    };
+    const int want = min(kp, m - 1);
+    int nsel = 0;
+    if (want > 0) {
+        const uint64_t thr = warp_select_threshold(key, m, want, hist);
+        nsel = warp_compact_le(key, m, thr, cand);
+    }
+    __syncwarp();
+    uint64_t v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = kKeyMax;
+    const int gi = lid[self];
+    for (int c = 0; c < nsel; ++c) {
+        const int gj = lid[cand[c]];
+        const float dd = warp_canon_dist(L, gi, gj);
+        const uint64_t kv = pack_key(dd, (uint32_t)gj);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (lane * E + e == c) v[e] = kv;
+    }
+    warp_bitonic_sort<E>(v);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane * E + e;
+        if (i < k) {
+            const bool ok = i < nsel;
+            oi[i] = ok ? (int32_t)(uint32_t)v[e] : -1;
+            od[i] = ok ? unord_key((uint32_t)(v[e] >> 32)) : __int_as_float(0x7f800000);
+        }
+    }
+    __syncwarp();
+}
+
+}  // namespace knng

@@ -103,9 +103,13 @@ struct XDesc {
 cudaError_t run_partition(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
                           uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st);
 
-cudaError_t run_leaf_knn(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
-                         const int32_t* perm, int k, int precision, int rescore_mult,
-                         int32_t* ids, float* dists, Arena& ar, cudaStream_t st);
+cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                             const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
+                             cudaStream_t st);
+
+cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
+                            int k, int kp, int prec, int32_t* ids, float* dists, int* err, Arena& ar,
+                            cudaStream_t st);
 
 cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
                       int32_t* ids, float* dists, cudaStream_t st);

@@ -78,7 +78,6 @@ __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, in
         for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
         if (lane == 0) sm.nrm[r] = s;
     }
-    const int want = min(kp, m - 1);
     uint32_t* hist = sm.hist + 256 * w;
     int* cand = sm.cand + kCandCap * w;
     constexpr int mp1 = m_pad + 1;
@@ -127,40 +126,9 @@ __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, in
             const int row = rb + r;
             if (row >= m) break;
             const float* Drow = sm.D + r * m_pad;
-            auto key = [&](int j) -> uint64_t {
-                return j == row ? kKeyMax : pack_key(Drow[j], (uint32_t)j);
-            };
-            int nsel = 0;
-            if (want > 0) {
-                const uint64_t thr = warp_select_threshold(key, m, want, hist);
-                nsel = warp_compact_le(key, m, thr, cand);
-            }
-            __syncwarp();
-            uint64_t v[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = kKeyMax;
             const int gi = sm.lid[row];
-            for (int c = 0; c < nsel; ++c) {
-                const int gj = sm.lid[cand[c]];
-                const float dd = warp_canon_dist(L, gi, gj);
-                const uint64_t kv = pack_key(dd, (uint32_t)gj);
-#pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (lane * E + e == c) v[e] = kv;
-            }
-            warp_bitonic_sort<E>(v);
-            int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
-            float* od = out_d + ((int64_t)t * n + gi) * k;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = lane * E + e;
-                if (i < k) {
-                    const bool ok = i < nsel;
-                    oi[i] = ok ? (int32_t)(uint32_t)v[e] : -1;
-                    od[i] = ok ? unord_key((uint32_t)(v[e] >> 32)) : __int_as_float(0x7f800000);
-                }
-            }
-            __syncwarp();
+            leaf_row_finish<E, kF16>(L, [&](int j) { return Drow[j]; }, m, row, sm.lid, k, kp, hist, cand,
+                                     out_ids + ((int64_t)t * n + gi) * k, out_d + ((int64_t)t * n + gi) * k);
         }
     }
 }

@@ -543,6 +543,13 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         if (L.small) {
             constexpr int NT = 512;
             const size_t smem = sizeof(unsigned long long) * (size_t)L.max_size;
+            static bool attr = false;
+            if (!attr) {
+                cudaError_t e = cudaFuncSetAttribute(split_small_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)(sizeof(unsigned long long) * kSmallCap));
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
             split_small_kernel<NT><<<dim3(S, T), NT, smem, st>>>(n, nodes, keys, cur, nxt, pos_of, node_of);
             note_launches(1);
         } else {
