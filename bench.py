@@ -181,7 +181,7 @@ def main():
     ap.add_argument("--data-seed", type=int, default=2013)
     ap.add_argument("--recall-sample", type=int, default=10000)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-sample", type=int, default=50000)
+    ap.add_argument("--cpu-sample", type=int, default=300000)
     ap.add_argument("--ref-sample", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")

@@ -354,24 +354,32 @@ int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int3
     const size_t nk = (size_t)n * k;
     int32_t* bi[2] = {nullptr, nullptr};
     float* bd[2] = {nullptr, nullptr};
+    unsigned long long* fl[2] = {nullptr, nullptr};
     if (rounds > 1) {
         Arena m;
-        m.take<int32_t>(nk); m.take<float>(nk); m.take<int32_t>(nk); m.take<float>(nk);
+        for (int b = 0; b < 2; ++b) { m.take<int32_t>(nk); m.take<float>(nk); m.take<unsigned long long>(n); }
         if ((r = ensure_ws(h, m.off, st))) return r;
         Arena a;
         a.base = h->ws;
-        bi[0] = a.take<int32_t>(nk); bd[0] = a.take<float>(nk);
-        bi[1] = a.take<int32_t>(nk); bd[1] = a.take<float>(nk);
+        for (int b = 0; b < 2; ++b) {
+            bi[b] = a.take<int32_t>(nk);
+            bd[b] = a.take<float>(nk);
+            fl[b] = a.take<unsigned long long>(n);
+        }
     }
     const int32_t* si = ids_in;
     const float* sd = dists_in;
+    const unsigned long long* sf = nullptr;  // the input lists count as all new
     for (int rd = 0; rd < rounds; ++rd) {
-        int32_t* oi = rd == rounds - 1 ? ids : bi[rd & 1];
-        float* od = rd == rounds - 1 ? dists : bd[rd & 1];
-        cudaError_t e = run_propagate(x, k, nullptr, si, sd, oi, od, st);
+        const bool last = rd == rounds - 1;
+        int32_t* oi = last ? ids : bi[rd & 1];
+        float* od = last ? dists : bd[rd & 1];
+        unsigned long long* of = last ? nullptr : fl[rd & 1];
+        cudaError_t e = run_propagate(x, k, nullptr, si, sd, sf, oi, od, of, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
         si = oi;
         sd = od;
+        sf = of;
     }
     return KNNG_OK;
 }
@@ -400,7 +408,7 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     m.take<int32_t>((size_t)T * n);
     m.take<int32_t>((size_t)T * nk);
     m.take<float>((size_t)T * nk);
-    for (int b = 0; b < 2; ++b) { m.take<int32_t>(nk); m.take<float>(nk); }
+    for (int b = 0; b < 2; ++b) { m.take<int32_t>(nk); m.take<float>(nk); m.take<unsigned long long>(n); }
     const size_t fixed = m.off;
     run_partition(x, h->plan, h->dplan, T, p->seed, nullptr, m, st);
     const size_t part_end = m.off;
@@ -415,7 +423,12 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     float* ld_ = a.take<float>((size_t)T * nk);
     int32_t* bi[2];
     float* bd[2];
-    for (int b = 0; b < 2; ++b) { bi[b] = a.take<int32_t>(nk); bd[b] = a.take<float>(nk); }
+    unsigned long long* fl[2];
+    for (int b = 0; b < 2; ++b) {
+        bi[b] = a.take<int32_t>(nk);
+        bd[b] = a.take<float>(nk);
+        fl[b] = a.take<unsigned long long>(n);
+    }
     const size_t fixed2 = a.off;
     const int R = p->prop_rounds;
     const bool rec = (int)h->stage_ev.size() >= 4 + R;
@@ -439,9 +452,11 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     for (int rd = 0; rd < R; ++rd) {
         const int32_t* si = bi[rd & 1];
         const float* sd = bd[rd & 1];
+        const unsigned long long* sf = rd == 0 ? nullptr : fl[rd & 1];
         int32_t* oi = rd == R - 1 ? ids : bi[(rd + 1) & 1];
         float* od = rd == R - 1 ? dists : bd[(rd + 1) & 1];
-        e = run_propagate(x, k, perm, si, sd, oi, od, st);
+        unsigned long long* of = rd == R - 1 ? nullptr : fl[(rd + 1) & 1];
+        e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
         mark(4 + rd);
     }

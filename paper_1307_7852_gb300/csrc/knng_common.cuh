@@ -335,3 +335,55 @@ __device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m
 }
 
 }  // namespace knng
+
+namespace knng {
+
+// Canonical distances from point a to up to 32 points b[0..nb) (b in shared
+// memory, read by every lane); lane c returns the distance to b[c] (lanes
+// c >= nb return an unspecified value).  Each lane first forms its partial
+// sums (entries j = 128c' + 4l + e, fmaf) for all 32 points; a recursive-
+// halving exchange then adds, for every point, the partials of lanes l and
+// l^16, then l^8, l^4, l^2, l^1 -- the same pairwise additions as the xor
+// butterfly of warp_canon_dist -- so the result is bit-identical to it, with
+// 31 shuffles per 32 distances instead of 160 and 32 row loads in flight.
+template <bool kF16>
+__device__ __forceinline__ float warp_canon_dist32(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
+{
+    const int lane = threadIdx.x & 31;
+    int bid[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) bid[c] = c < nb ? b[c] : (int)a;
+    float p[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) p[c] = 0.f;
+    for (int j = 4 * lane; j < L.d; j += 128) {
+        const float4 xa = L.load4(a, j);
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 8) {
+            float4 xb[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) xb[c] = L.load4(bid[c0 + c], j);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float t;
+                t = xa.x - xb[c].x; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+                t = xa.y - xb[c].y; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+                t = xa.z - xb[c].z; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+                t = xa.w - xb[c].w; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = hi ? p[i] : p[i + o];
+            const float keep = hi ? p[i + o] : p[i];
+            p[i] = keep + __shfl_xor_sync(KNNG_FULL_MASK, send, o);
+        }
+    }
+    return p[0];
+}
+
+}  // namespace knng

@@ -114,8 +114,12 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
 cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
                       int32_t* ids, float* dists, cudaStream_t st);
 
-cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
-                          const float* d_in, int32_t* ids, float* dists, cudaStream_t st);
+// One synchronous propagation round.  flags_in (nullable = every entry new)
+// marks, per point, the list entries that were not in the previous round's
+// list; flags_out (nullable) receives the same for the output lists.
+cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
+                          const unsigned long long* flags_in, int32_t* ids, float* dists,
+                          unsigned long long* flags_out, cudaStream_t st);
 
 cudaError_t run_exact_knn(const XDesc& x, const int32_t* queries, int nq, int k, int32_t* ids,
                           float* dists, cudaStream_t st);

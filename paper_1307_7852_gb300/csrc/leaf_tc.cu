@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) leaf_tc_kernel(const __grid_con
                 }
             }
             __syncthreads();
-            for (int rr = w; rr < G.RG; rr += 4) {
+            for (int rr = w; rr < G.RG && g0 + rr < 128; rr += 4) {
                 const int iloc = r0 + g0 + rr;
                 if (iloc >= m) break;
                 const float* drow = Dblk + (size_t)rr * ldD;
@@ -308,8 +308,9 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec)
     G.stage_bytes = G.R_load * 128;
     G.S = std::max(1, std::min(std::min(G.nK, 4), (160 * 1024) / G.stage_bytes));
     G.ldD = ((G.N_load + 31) & ~31) + 1;
-    int rg = (72 * 1024) / (G.ldD * 4) / 32 * 32;
-    G.RG = std::max(32, std::min(128, rg));
+    // rows per epilogue group: 128, 64 or 32 (a divisor of the 128-row block)
+    G.RG = 128;
+    while (G.RG > 32 && G.RG * G.ldD * 4 > 72 * 1024) G.RG >>= 1;
     G.pipe_bytes = std::max(G.S * G.stage_bytes, G.RG * G.ldD * 4);
     G.pipe_bytes = (G.pipe_bytes + 1023) & ~1023;
     G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + 4 * 256 * 4 + 4 * kTcCand * 4 + (2 * G.S + 1) * 8 + 16;

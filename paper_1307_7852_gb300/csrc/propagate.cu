@@ -2,12 +2,21 @@
 // form analysed by Theorem 1: in one synchronous round every point p takes
 // the k best of its own list and of the lists of its neighbours, without p.
 //
-// One warp per point.  Candidate ids are deduplicated in a shared-memory hash
-// set (the per-point replacement of the paper's hash table of evaluated pairs,
-// Sec. 3.4 "Speedup"); ids already in p's list keep their distance, new ids
-// are scored by the canonical FP32 distance (vectorised, coalesced row loads:
-// each lane reads 16 bytes per 128-entry chunk of the row).  The k best by
-// (dist, id) are found by warp radix select and sorted by a warp bitonic sort.
+// One warp per point.
+//  * Candidates: the k*k ids of the neighbours' lists are fetched with the
+//    lanes spread over (neighbour, slot) pairs, and deduplicated in a
+//    shared-memory hash set (the per-point replacement of the paper's hash
+//    table of evaluated pairs, Sec. 3.4 "Speedup").  Ids already in p's list
+//    keep their distance.
+//  * Skipping pairs scored before (exact): with per-entry "new" flags from
+//    the previous round, a candidate c of a neighbour q is skipped when q was
+//    already in p's previous list and c already in q's previous list.  Then c
+//    was a candidate of p in the previous round, so either c is in p's list
+//    or k listed points beat it, and it cannot enter the new list.
+//  * Scoring: 32 candidates at a time by warp_canon_dist32 (coalesced 16-byte
+//    row loads, 32 rows in flight per warp, bit-identical canonical FP32).
+//  * The k best by (dist, id): warp radix select and a warp bitonic sort; the
+//    output flags mark the entries that were not in p's input list.
 #include "knng_common.cuh"
 #include "knng_internal.h"
 
@@ -30,16 +39,18 @@ static PropLayout prop_layout(int k)
     int lg = 0;
     while ((1 << lg) < H) ++lg;
     L.hshift = 32 - lg;
+    // tab[H] | cid[cap] | cd[cap] | hist[256] | sel[64] | own[64] | ownflag (u64)
     L.per_warp = sizeof(int) * (size_t)H + (sizeof(int) + sizeof(float)) * (size_t)L.cap +
-                 sizeof(uint32_t) * 256 + sizeof(int) * 64;
+                 sizeof(uint32_t) * 256 + sizeof(int) * 64 + sizeof(int) * 64 + 16;
     L.per_warp = (L.per_warp + 15) & ~(size_t)15;
     return L;
 }
 
 template <int E, bool kF16>
-__global__ void propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int32_t* __restrict__ order,
+__global__ void __launch_bounds__(256, 2) propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int32_t* __restrict__ order,
                                  const int32_t* __restrict__ ids_in, const float* __restrict__ d_in,
-                                 int32_t* __restrict__ ids_out, float* __restrict__ d_out, int H,
+                                 const unsigned long long* __restrict__ flags_in, int32_t* __restrict__ ids_out,
+                                 float* __restrict__ d_out, unsigned long long* __restrict__ flags_out, int H,
                                  int hshift, int cap, int per_warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -50,18 +61,21 @@ __global__ void propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int3
     float* cd = reinterpret_cast<float*>(cid + cap);
     uint32_t* hist = reinterpret_cast<uint32_t*>(cd + cap);
     int* sel = reinterpret_cast<int*>(hist + 256);
+    int* own = sel + 64;
     const uint32_t hmask = (uint32_t)H - 1;
+    const int kk = k * k;
 
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t wi = gw; wi < n; wi += nw) {
         const int32_t p = order ? order[wi] : (int32_t)wi;
-        for (int s = lane; s < H; s += 32) tab[s] = -1;
+        for (int s = lane * 4; s < H; s += 128) *reinterpret_cast<int4*>(tab + s) = make_int4(-1, -1, -1, -1);
         __syncwarp();
         if (lane == 0) hash_insert(tab, (uint32_t)hshift, hmask, p);
+        const unsigned long long pf = flags_in ? flags_in[p] : ~0ull;
         __syncwarp();
-        int cnt = 0;
         // p's own list: ids keep their distances
+        int cnt = 0;
         for (int e0 = 0; e0 < k; e0 += 32) {
             const int e = e0 + lane;
             int32_t id = -1;
@@ -69,8 +83,9 @@ __global__ void propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int3
             if (e < k) {
                 id = ids_in[(int64_t)p * k + e];
                 dd = d_in[(int64_t)p * k + e];
+                if (id >= n) id = -1;  // ids outside [0, n) are treated as empty slots
+                own[e] = id;
             }
-            if (id >= n) id = -1;  // ids outside [0, n) are treated as empty slots
             const bool ins = id >= 0 && hash_insert(tab, (uint32_t)hshift, hmask, id);
             const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
             if (ins) {
@@ -81,24 +96,32 @@ __global__ void propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int3
             cnt += __popc(b);
         }
         const int nknown = cnt;
-        // neighbours' lists
-        for (int e = 0; e < k; ++e) {
-            const int32_t q = ids_in[(int64_t)p * k + e];
-            if (q < 0 || q >= n) continue;
-            for (int f0 = 0; f0 < k; f0 += 32) {
-                const int f = f0 + lane;
-                const int32_t o = f < k ? ids_in[(int64_t)q * k + f] : -1;
-                const bool ins = o >= 0 && o < n && hash_insert(tab, (uint32_t)hshift, hmask, o);
-                const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
-                if (ins) cid[cnt + __popc(b & lanemask_lt())] = o;
-                cnt += __popc(b);
+        __syncwarp();
+        // the neighbours' lists, lanes over (neighbour e, slot f)
+        for (int i0 = 0; i0 < kk; i0 += 32) {
+            const int i = i0 + lane;
+            int32_t o = -1;
+            if (i < kk) {
+                const int e = i / k, f = i - e * k;
+                const int32_t q = own[e];
+                if (q >= 0 && q != p) {
+                    const bool qnew = (pf >> e) & 1ull;
+                    const bool cnew = flags_in ? ((flags_in[q] >> f) & 1ull) : true;
+                    if (qnew || cnew) o = ids_in[(int64_t)q * k + f];
+                    if (o >= n) o = -1;
+                }
             }
+            const bool ins = o >= 0 && hash_insert(tab, (uint32_t)hshift, hmask, o);
+            const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
+            if (ins) cid[cnt + __popc(b & lanemask_lt())] = o;
+            cnt += __popc(b);
         }
         __syncwarp();
-        // score the new candidates
-        for (int c = nknown; c < cnt; ++c) {
-            const float dd = warp_canon_dist(L, p, cid[c]);
-            if (lane == 0) cd[c] = dd;
+        // score the new candidates, 32 at a time
+        for (int c0 = nknown; c0 < cnt; c0 += 32) {
+            const int nb = min(32, cnt - c0);
+            const float dd = warp_canon_dist32(L, p, cid + c0, nb);
+            if (lane < nb) cd[c0 + lane] = dd;
         }
         __syncwarp();
         auto key = [&](int idx) -> uint64_t { return pack_key(cd[idx], (uint32_t)cid[idx]); };
@@ -110,28 +133,45 @@ __global__ void propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int3
         }
         __syncwarp();
         uint64_t v[E];
+        int from[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i = lane * E + e;
             v[e] = i < nsel ? key(sel[i]) : kKeyMax;
         }
         warp_bitonic_sort<E>(v);
+        // new-entry flags: an output id is new unless it was in p's list
+        unsigned long long fl = 0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i = lane * E + e;
+            from[e] = 0;
+            if (i < nsel) {
+                const int32_t id = (int32_t)(uint32_t)v[e];
+                bool known = false;
+                for (int q = 0; q < k; ++q) known |= (own[q] == id);
+                from[e] = known ? 0 : 1;
+            }
             if (i < k) {
                 const bool ok = i < nsel;
                 ids_out[(int64_t)p * k + i] = ok ? (int32_t)(uint32_t)v[e] : -1;
                 d_out[(int64_t)p * k + i] = ok ? unord_key((uint32_t)(v[e] >> 32)) : __int_as_float(0x7f800000);
+                if (from[e]) fl |= 1ull << i;
             }
+        }
+        if (flags_out) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) fl |= __shfl_xor_sync(KNNG_FULL_MASK, fl, o);
+            if (lane == 0) flags_out[p] = fl;
         }
         __syncwarp();
     }
 }
 
 template <int E, bool kF16>
-static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
-                               const float* d_in, int32_t* ids, float* dists, cudaStream_t st)
+static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
+                               const unsigned long long* fin, int32_t* ids, float* dists, unsigned long long* fout,
+                               cudaStream_t st)
 {
     const PropLayout PL = prop_layout(k);
     int warps = (int)((200 * 1024) / PL.per_warp);
@@ -148,25 +188,27 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     const int64_t need = (x.n + warps - 1) / warps;
     if (blocks > need) blocks = need;
     RowLoader<kF16> rl{x.X, x.ld, x.d, x.vec};
-    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, x.n, k, order, ids_in, d_in, ids, dists, PL.H,
+    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
                                                 PL.hshift, PL.cap, (int)PL.per_warp);
-                                                note_launches(1);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 template <bool kF16>
 static cudaError_t prop_dispatch(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
-                                 const float* d_in, int32_t* ids, float* dists, cudaStream_t st)
+                                 const float* d_in, const unsigned long long* fin, int32_t* ids, float* dists,
+                                 unsigned long long* fout, cudaStream_t st)
 {
-    if (k <= 32) return launch_prop<1, kF16>(x, k, order, ids_in, d_in, ids, dists, st);
-    return launch_prop<2, kF16>(x, k, order, ids_in, d_in, ids, dists, st);
+    if (k <= 32) return launch_prop<1, kF16>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
+    return launch_prop<2, kF16>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
 }
 
-cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
-                          const float* d_in, int32_t* ids, float* dists, cudaStream_t st)
+cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
+                          const unsigned long long* flags_in, int32_t* ids, float* dists,
+                          unsigned long long* flags_out, cudaStream_t st)
 {
-    if (x.dtype == 1) return prop_dispatch<true>(x, k, order, ids_in, d_in, ids, dists, st);
-    return prop_dispatch<false>(x, k, order, ids_in, d_in, ids, dists, st);
+    if (x.dtype == 1) return prop_dispatch<true>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
+    return prop_dispatch<false>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
 }
 
 }  // namespace knng

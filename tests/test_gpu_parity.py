@@ -187,6 +187,19 @@ def test_propagate_integer_exact():
     assert np.all(host(qd) <= host(pd)) and np.all(host(pd) <= host(md))
 
 
+def test_propagate_rounds_skip_old_pairs():
+    # three rounds in one call: rounds 2 and 3 skip the pairs the previous
+    # round already scored; the result must equal three plain oracle rounds
+    X = synthetic.sift_like(10000, 128, centers=64, seed=1)
+    Xd, (li, ld) = _gpu_leaf_lists(X, 2, 64, 10, 9)
+    mi, md = knng().knng_merge(li, ld)
+    pi, pd = knng().knng_propagate(Xd, mi, md, 3)
+    oi = host(mi)
+    for _ in range(3):
+        oi, od = oracle.propagate(X, oi, 10)
+    assert_lists_exact(host(pi), host(pd), oi, od)
+
+
 @pytest.mark.parametrize("n,d,k", [(6000, 96, 16), (2500, 7, 40)])
 def test_propagate_real_valued(n, d, k):
     X = synthetic.gist_like(n, d, centers=16, seed=n)
