@@ -288,6 +288,71 @@ __device__ __forceinline__ bool hash_insert(int* tab, uint32_t hshift, uint32_t 
 
 namespace knng {
 
+// Canonical distances from point a to W points b[0..W) (W = 8, 16 or 32;
+// b in shared memory, entries c >= nb unused); lane l returns the distance to
+// b[l % W] (for l % W < nb).  Each lane first forms its partial sums
+// (entries j = 128c' + 4l + e, fmaf) for the W points; then, for offsets
+// o = 16, 8, 4, 2, 1, the partials of lanes l and l^o are added -- for o >= W
+// as a plain butterfly on all W values, for o < W by recursive halving (each
+// lane keeps half of its values and receives its partner's copy of them).
+// These are the pairwise additions of the xor butterfly in warp_canon_dist,
+// so the result is bit-identical to it, with far fewer shuffles and W row
+// loads in flight.
+template <int W, bool kF16>
+__device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
+{
+    const int lane = threadIdx.x & 31;
+    int bid[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) bid[c] = c < nb ? b[c] : (int)a;
+    float p[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) p[c] = 0.f;
+    for (int j = 4 * lane; j < L.d; j += 128) {
+        const float4 xa = L.load4(a, j);
+#pragma unroll
+        for (int c0 = 0; c0 < W; c0 += 8) {
+            float4 xb[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) xb[c] = L.load4(bid[c0 + c], j);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float t;
+                t = xa.x - xb[c].x; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+                t = xa.y - xb[c].y; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+                t = xa.z - xb[c].z; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+                t = xa.w - xb[c].w; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= W; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) p[c] += __shfl_xor_sync(KNNG_FULL_MASK, p[c], o);
+    }
+#pragma unroll
+    for (int o = W / 2; o >= 1; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = hi ? p[i] : p[i + o];
+            const float keep = hi ? p[i + o] : p[i];
+            p[i] = keep + __shfl_xor_sync(KNNG_FULL_MASK, send, o);
+        }
+    }
+    return p[0];
+}
+
+// Canonical distances from a to b[0..nb) (nb <= 32): lane c < nb returns the
+// distance to b[c].
+template <bool kF16>
+__device__ __forceinline__ float warp_canon_dist32(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
+{
+    if (nb > 16) return warp_canon_dist_batch<32, kF16>(L, a, b, nb);
+    if (nb > 8) return warp_canon_dist_batch<16, kF16>(L, a, b, nb);
+    return warp_canon_dist_batch<8, kF16>(L, a, b, nb);
+}
+
 // Finishes one row of a leaf graph (collective over one warp): from the
 // candidate distances Drow[0..m) (local index j; j == self excluded) pick the
 // kp smallest (D~, j), rescore them with the canonical FP32 distance between
@@ -309,18 +374,25 @@ __device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m
         nsel = warp_compact_le(key, m, thr, cand);
     }
     __syncwarp();
+    const int gi = lid[self];
+    // local -> point ids, then rescore 32 (or fewer) candidates per pass;
+    // the keys go to shared memory (the histogram area is free again)
+    for (int c = lane; c < nsel; c += 32) cand[c] = lid[cand[c]];
+    __syncwarp();
+    uint64_t* keys = reinterpret_cast<uint64_t*>(hist);  // 128 keys
+    for (int c0 = 0; c0 < nsel; c0 += 32) {
+        const int nb = min(32, nsel - c0);
+        const float dd = warp_canon_dist32(L, gi, cand + c0, nb);
+        if (lane < nb) keys[c0 + lane] = pack_key(dd, (uint32_t)cand[c0 + lane]);
+    }
+    __syncwarp();
     uint64_t v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = kKeyMax;
-    const int gi = lid[self];
-    for (int c = 0; c < nsel; ++c) {
-        const int gj = lid[cand[c]];
-        const float dd = warp_canon_dist(L, gi, gj);
-        const uint64_t kv = pack_key(dd, (uint32_t)gj);
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-            if (lane * E + e == c) v[e] = kv;
+    for (int e = 0; e < E; ++e) {
+        const int i = lane * E + e;
+        v[e] = i < nsel ? keys[i] : kKeyMax;
     }
+    __syncwarp();
     warp_bitonic_sort<E>(v);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -336,54 +408,3 @@ __device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m
 
 }  // namespace knng
 
-namespace knng {
-
-// Canonical distances from point a to up to 32 points b[0..nb) (b in shared
-// memory, read by every lane); lane c returns the distance to b[c] (lanes
-// c >= nb return an unspecified value).  Each lane first forms its partial
-// sums (entries j = 128c' + 4l + e, fmaf) for all 32 points; a recursive-
-// halving exchange then adds, for every point, the partials of lanes l and
-// l^16, then l^8, l^4, l^2, l^1 -- the same pairwise additions as the xor
-// butterfly of warp_canon_dist -- so the result is bit-identical to it, with
-// 31 shuffles per 32 distances instead of 160 and 32 row loads in flight.
-template <bool kF16>
-__device__ __forceinline__ float warp_canon_dist32(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
-{
-    const int lane = threadIdx.x & 31;
-    int bid[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) bid[c] = c < nb ? b[c] : (int)a;
-    float p[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) p[c] = 0.f;
-    for (int j = 4 * lane; j < L.d; j += 128) {
-        const float4 xa = L.load4(a, j);
-#pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 8) {
-            float4 xb[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) xb[c] = L.load4(bid[c0 + c], j);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float t;
-                t = xa.x - xb[c].x; p[c0 + c] = fmaf(t, t, p[c0 + c]);
-                t = xa.y - xb[c].y; p[c0 + c] = fmaf(t, t, p[c0 + c]);
-                t = xa.z - xb[c].z; p[c0 + c] = fmaf(t, t, p[c0 + c]);
-                t = xa.w - xb[c].w; p[c0 + c] = fmaf(t, t, p[c0 + c]);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = hi ? p[i] : p[i + o];
-            const float keep = hi ? p[i + o] : p[i];
-            p[i] = keep + __shfl_xor_sync(KNNG_FULL_MASK, send, o);
-        }
-    }
-    return p[0];
-}
-
-}  // namespace knng

@@ -31,7 +31,8 @@ namespace knng {
 
 namespace {
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;  // 8 warps: warps w and w+4 share TMEM lanes 32(w%4)..+31
+constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kTcCand = 128;
 }  // namespace
 
@@ -109,7 +110,7 @@ struct TcGeom {
 };
 
 template <int PREC, int E, bool kF16>
-__global__ void __launch_bounds__(kTcThreads, 1) leaf_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 RowLoader<kF16> L, int64_t n,
                                                                 const int32_t* __restrict__ perm,
                                                                 const int32_t* __restrict__ leaf_off,
@@ -126,8 +127,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) leaf_tc_kernel(const __grid_con
     float* qn = reinterpret_cast<float*>(lid + G.N_load);
     float* qs = qn + G.N_load;
     uint32_t* hist = reinterpret_cast<uint32_t*>(qs + G.N_load);
-    int* cand = reinterpret_cast<int*>(hist + 4 * 256);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(cand + 4 * kTcCand);
+    int* cand = reinterpret_cast<int*>(hist + kTcWarps * 256);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(cand + kTcWarps * kTcCand);
     uint64_t* full = bars;
     uint64_t* empty = bars + G.S;
     uint64_t* done = bars + 2 * G.S;
@@ -238,15 +239,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) leaf_tc_kernel(const __grid_con
     // ---- epilogue: TMEM -> distance block -> per-row selection ----------
     if (!abort_flag) {
         const int ldD = G.ldD;
+        const int quad = w & 3, half = w >> 2;
         for (int g0 = 0; g0 < 128 && r0 + g0 < m; g0 += G.RG) {
-            if (32 * w >= g0 && 32 * w < g0 + G.RG) {
-                const int lr = 32 * w + lane;
+            if (32 * quad >= g0 && 32 * quad < g0 + G.RG) {
+                const int lr = 32 * quad + lane;
                 const int il = min(r0 + lr, G.N_load - 1);
                 const float ni = qn[il], si = qs[il];
                 float* drow = Dblk + (size_t)(lr - g0) * ldD;
-                for (int c0 = 0; c0 < Nm; c0 += 32) {
+                for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
                     uint32_t r[32];
-                    tc::tmem_ld32(tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, r);
+                    tc::tmem_ld32(tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, r);
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) leaf_tc_kernel(const __grid_con
                 }
             }
             __syncthreads();
-            for (int rr = w; rr < G.RG && g0 + rr < 128; rr += 4) {
+            for (int rr = w; rr < G.RG && g0 + rr < 128; rr += kTcWarps) {
                 const int iloc = r0 + g0 + rr;
                 if (iloc >= m) break;
                 const float* drow = Dblk + (size_t)rr * ldD;
@@ -303,7 +305,7 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec)
     G.nK = dq / slice;
     G.N_load = (P.max_leaf + 15) & ~15;
     G.R_load = (P.max_leaf + 127) & ~127;
-    G.box_rows = std::min(G.R_load, 256);
+    G.box_rows = 128;  // R_load is a multiple of 128
     G.nbox = G.R_load / G.box_rows;
     G.stage_bytes = G.R_load * 128;
     G.S = std::max(1, std::min(std::min(G.nK, 4), (160 * 1024) / G.stage_bytes));
@@ -313,7 +315,7 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec)
     while (G.RG > 32 && G.RG * G.ldD * 4 > 72 * 1024) G.RG >>= 1;
     G.pipe_bytes = std::max(G.S * G.stage_bytes, G.RG * G.ldD * 4);
     G.pipe_bytes = (G.pipe_bytes + 1023) & ~1023;
-    G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + 4 * 256 * 4 + 4 * kTcCand * 4 + (2 * G.S + 1) * 8 + 16;
+    G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + kTcWarps * (256 * 4 + kTcCand * 4) + (2 * G.S + 1) * 8 + 16;
     return G;
 }
 
