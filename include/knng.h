@@ -47,6 +47,7 @@ extern "C" {
 #define KNNG_ERR_CUDA (-4)        /* a CUDA runtime call or launch failed        */
 #define KNNG_ERR_TIMEOUT (-5)     /* a bounded device wait gave up               */
 #define KNNG_ERR_INTERNAL (-6)
+#define KNNG_ERR_LIMIT (-7)       /* request exceeds a fixed capacity (see knng_propagate_noalloc) */
 
 /* ---- enumerations ---------------------------------------------------- */
 #define KNNG_DTYPE_F32 0
@@ -143,6 +144,31 @@ int knng_merge(knng_handle* h, int64_t n, int32_t T, int32_t k, const int32_t* i
 int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                    int32_t k, int32_t rounds, const int32_t* ids_in, const float* dists_in,
                    int32_t* ids, float* dists, void* stream);
+
+/* ---- propagation without device allocation ---------------------------- */
+/* The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory on their call path -- for example a plugin
+ * inside an application whose memory manager already owns all device memory,
+ * or a latency-critical loop that cannot pay for the implicit synchronisation
+ * of cudaMalloc/cudaFree.  It computes exactly what knng_propagate computes
+ * (same kernel, same results), needs no handle, and never allocates: the
+ * lists between rounds live in one fixed 16 MiB device array that the library
+ * reserves when it is loaded, held by every GPU that loads the library until
+ * the process exits.
+ *  - Runs on the CURRENT device; X, ids_in, dists_in, ids, dists are device
+ *    pointers there, with the layouts of knng_propagate.
+ *  - Limits: n <= 524288 and n*k <= 524288; larger requests return
+ *    KNNG_ERR_LIMIT without doing any work.  Other bad arguments return
+ *    KNNG_ERR_INVALID_ARG; a failed launch returns KNNG_ERR_CUDA.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device); make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the previous call's
+ *    contents (nothing in it needs to start at zero): calls whose work
+ *    overlaps on the GPU -- on different streams, or from different host
+ *    threads -- race on it and must be serialised by the caller. */
+int knng_propagate_noalloc(const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld, int32_t k,
+                           int32_t rounds, const int32_t* ids_in, const float* dists_in, int32_t* ids,
+                           float* dists, void* stream);
 
 /* ---- measurement ----------------------------------------------------- */
 /* Exact k-NN lists (Def. 1) of nq query points against all n points, by

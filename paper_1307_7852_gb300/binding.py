@@ -59,6 +59,7 @@ SIGNATURES = {
     "knng_set_stage_events": [_P, _P, _I32],
     "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
     "knng_sync": [_P, _P],
+    "knng_propagate_noalloc": [_P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
 }
 
 
@@ -321,3 +322,21 @@ def knng_sync(h: Handle = None, stream=None, device: int = 0):
     torch = _torch()
     h = h or handle(device)
     h.check(lib().knng_sync(h.ptr, _stream(torch.device("cuda", h.device), stream)), "knng_sync")
+
+
+def knng_propagate_noalloc(X, ids_in, dists_in, rounds=1, ids=None, dists=None, stream=None):
+    """Propagation rounds that allocate no device memory (for callers that
+    cannot allocate on their call path); the lists between rounds live in the
+    library's fixed 16 MiB device array.  Runs on X's device, which is made
+    current.  Outputs, if given, must be preallocated by the caller."""
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    k = ids_in.shape[1]
+    ids = _out((n, k), torch.int32, X.device, ids)
+    dists = _out((n, k), torch.float32, X.device, dists)
+    with torch.cuda.device(X.device):
+        rc = lib().knng_propagate_noalloc(xp, dt, n, d, ld, int(k), int(rounds), _ptr(ids_in), _ptr(dists_in),
+                                          _ptr(ids), _ptr(dists), _stream(X.device, stream))
+    if rc != KNNG_OK:
+        raise KnngError(rc, "knng_propagate_noalloc: " + lib().knng_status_string(rc).decode())
+    return ids, dists

@@ -213,6 +213,7 @@ const char* knng_status_string(int32_t s)
         case KNNG_ERR_CUDA: return "CUDA error";
         case KNNG_ERR_TIMEOUT: return "device wait timed out";
         case KNNG_ERR_INTERNAL: return "internal error";
+        case KNNG_ERR_LIMIT: return "request exceeds a fixed capacity of the library";
         default: return "unknown status";
     }
 }
