@@ -35,6 +35,8 @@ WORKLOADS = {
     # name: generator args and method parameters
     "sift1m": dict(gen="sift_like", n=1_000_000, d=128, centers=1024, k=20, T=8, g=256, R=2,
                    desc="1M x 128 SIFT-like integer mixture (1,024 centres, std 20), k=20, T=8, g=256, R=2"),
+    "sift400k": dict(gen="sift_like", n=400_000, d=128, centers=410, k=20, T=8, g=256, R=2,
+                     desc="400k x 128 SIFT-like integer mixture (410 centres), k=20, T=8, g=256, R=2 (profiling size)"),
     "sift10k": dict(gen="sift_like", n=10_000, d=128, centers=64, k=10, T=4, g=64, R=1,
                     desc="10k x 128 SIFT-like integer mixture (64 centres), k=10, T=4, g=64, R=1"),
     "gist1m": dict(gen="gist_like", n=1_000_000, d=960, centers=256, k=10, T=8, g=512, R=1,
@@ -176,7 +178,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sift1m")
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16")
     ap.add_argument("--seed", type=int, default=12345)
     ap.add_argument("--data-seed", type=int, default=2013)
     ap.add_argument("--recall-sample", type=int, default=10000)

@@ -152,7 +152,7 @@ int check_x(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, 
     if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16) return fail(h, KNNG_ERR_INVALID_ARG, "dtype %d", dtype);
     if (n < 2 || n >= (int64_t)1 << 31) return fail(h, KNNG_ERR_INVALID_ARG, "n = %lld out of [2, 2^31)", (long long)n);
     if (d < 1 || d > 4096) return fail(h, KNNG_ERR_INVALID_ARG, "d = %d out of [1, 4096]", d);
-    if (ld < d) return fail(h, KNNG_ERR_INVALID_ARG, "ld = %lld < d", (long long)ld);
+    if (ld < d || ld >= (int64_t)1 << 31) return fail(h, KNNG_ERR_INVALID_ARG, "ld = %lld out of [d, 2^31)", (long long)ld);
     const size_t es = dtype == KNNG_DTYPE_F16 ? 2 : 4;
     const size_t align = dtype == KNNG_DTYPE_F16 ? 8 : 16;
     x.X = X;

@@ -72,11 +72,17 @@ struct RowLoader {
     int d;
     bool vec;  // rows 16-byte (F32) / 8-byte (F16) aligned and ld multiple of 4
 
+    // element offset of row i (ids < 2^31, ld < 2^31: one 32x32->64 multiply)
+    __device__ __forceinline__ uint64_t row_off(int64_t i) const
+    {
+        return (uint64_t)(uint32_t)i * (uint32_t)ld;
+    }
+
     __device__ __forceinline__ float4 load4(int64_t i, int j) const
     {
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
         if (kF16) {
-            const __half* row = static_cast<const __half*>(X) + i * ld;
+            const __half* row = static_cast<const __half*>(X) + row_off(i);
             if (vec && j + 3 < d) {
                 const uint2 u = __ldg(reinterpret_cast<const uint2*>(row + j));
                 const __half2 a = *reinterpret_cast<const __half2*>(&u.x);
@@ -90,7 +96,7 @@ struct RowLoader {
                 if (j + 3 < d) r.w = __half2float(row[j + 3]);
             }
         } else {
-            const float* row = static_cast<const float*>(X) + i * ld;
+            const float* row = static_cast<const float*>(X) + row_off(i);
             if (vec && j + 3 < d) {
                 r = __ldg(reinterpret_cast<const float4*>(row + j));
             } else {
@@ -102,10 +108,24 @@ struct RowLoader {
         }
         return r;
     }
+    // entries j..j+3 of row i when rows are vector-aligned and j + 3 < d
+    __device__ __forceinline__ float4 load4v(int64_t i, int j) const
+    {
+        if (kF16) {
+            const uint2 u = __ldg(reinterpret_cast<const uint2*>(static_cast<const __half*>(X) + row_off(i) + j));
+            const float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+            const float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+            return make_float4(fa.x, fa.y, fb.x, fb.y);
+        }
+        return __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(X) + row_off(i) + j));
+    }
+    // every load of a row is a full vector load (aligned rows, d % 4 == 0)
+    __device__ __forceinline__ bool all_vec() const { return vec && (d & 3) == 0; }
+
     __device__ __forceinline__ float load1(int64_t i, int j) const
     {
-        if (kF16) return __half2float(static_cast<const __half*>(X)[i * ld + j]);
-        return __ldg(static_cast<const float*>(X) + i * ld + j);
+        if (kF16) return __half2float(static_cast<const __half*>(X)[row_off(i) + j]);
+        return __ldg(static_cast<const float*>(X) + row_off(i) + j);
     }
 };
 
@@ -189,66 +209,87 @@ __device__ __forceinline__ uint32_t lanemask_lt()
 // ---------------------------------------------------------------------------
 // Warp radix select.  Among cnt unique 64-bit keys key(idx), idx in [0, cnt),
 // returns the threshold K such that exactly min(want, cnt) keys are <= K
-// (want >= 1).  8-bit digits from the most significant end; a pass stops the
-// search as soon as every key that matches the prefix must be taken.  hist:
-// 256 words of shared memory private to the warp.  Collective: all 32 lanes.
+// (want >= 1).  The bits that all keys share (from their minimum and
+// maximum) are skipped; the rest is resolved 8 bits per pass from the most
+// significant end, and a pass ends the search as soon as every key that
+// matches the prefix must be taken.  hist: 256 words of shared memory private
+// to the warp; lane l owns bins l, l+32, ..., l+224 (conflict-free).
+// Collective: all 32 lanes.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t lowmask64(int b)
+{
+    return b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+}
+
 template <class KeyFn>
 __device__ uint64_t warp_select_threshold(const KeyFn& key, int cnt, int want, uint32_t* hist)
 {
     if (want >= cnt) return kKeyMax;
     const int lane = threadIdx.x & 31;
-    uint64_t prefix = 0, mask = 0;
-    int rank = want;
-    for (int shift = 56;; shift -= 8) {
+    uint64_t mn = kKeyMax, mx = 0;
+    for (int idx = lane; idx < cnt; idx += 32) {
+        const uint64_t kv = key(idx);
+        mn = kv < mn ? kv : mn;
+        mx = kv > mx ? kv : mx;
+    }
 #pragma unroll
-        for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
+    for (int o = 16; o >= 1; o >>= 1) {
+        const uint64_t a = __shfl_xor_sync(KNNG_FULL_MASK, mn, o);
+        const uint64_t b = __shfl_xor_sync(KNNG_FULL_MASK, mx, o);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+    }
+    int hi = 64 - __clzll((long long)(mn ^ mx));  // bits [hi, 64) are common (cnt >= 2)
+    uint64_t mask = ~lowmask64(hi);
+    uint64_t prefix = mn & mask;
+    int rank = want;
+    while (true) {
+        const int lo = hi > 8 ? hi - 8 : 0;
+        const uint32_t dmask = (uint32_t)lowmask64(hi - lo);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) hist[b * 32 + lane] = 0;
         __syncwarp();
         for (int idx = lane; idx < cnt; idx += 32) {
             const uint64_t kv = key(idx);
-            if ((kv & mask) == prefix) atomicAdd(&hist[(kv >> shift) & 0xFF], 1u);
+            if ((kv & mask) == prefix) atomicAdd(&hist[(uint32_t)(kv >> lo) & dmask], 1u);
         }
         __syncwarp();
         uint32_t c[8];
-        uint32_t lsum = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) c[b] = hist[b * 32 + lane];
+        // the 32-bin chunk in which the rank falls, then the bin inside it
+        uint32_t run = 0, before_chunk = 0, mine = 0;
+        int chunk = 0;
+        bool found = false;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            c[b] = hist[lane * 8 + b];
-            lsum += c[b];
+            const uint32_t tot = __reduce_add_sync(KNNG_FULL_MASK, c[b]);
+            if (!found && run < (uint32_t)rank && (uint32_t)rank <= run + tot) {
+                found = true;
+                chunk = b;
+                before_chunk = run;
+                mine = c[b];
+            }
+            run += tot;
         }
-        uint32_t incl = lsum;
+        uint32_t incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(KNNG_FULL_MASK, incl, o);
             if (lane >= o) incl += t;
         }
-        const uint32_t excl = incl - lsum;
-        const bool mine = excl < (uint32_t)rank && (uint32_t)rank <= incl;
-        const uint32_t owner = __ffs(__ballot_sync(KNNG_FULL_MASK, mine)) - 1;
-        uint32_t digit = 0, before = 0, inbin = 0;
-        if (mine) {
-            uint32_t run = excl;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                if (run < (uint32_t)rank && (uint32_t)rank <= run + c[b] && inbin == 0) {
-                    digit = lane * 8 + b;
-                    before = run;
-                    inbin = c[b];
-                }
-                run += c[b];
-            }
-        }
-        digit = __shfl_sync(KNNG_FULL_MASK, digit, owner);
-        before = __shfl_sync(KNNG_FULL_MASK, before, owner);
-        inbin = __shfl_sync(KNNG_FULL_MASK, inbin, owner);
-        prefix |= (uint64_t)digit << shift;
-        mask |= (uint64_t)0xFF << shift;
+        const uint32_t excl = incl - mine;
+        const bool own = before_chunk + excl < (uint32_t)rank && (uint32_t)rank <= before_chunk + incl;
+        const int owner = __ffs(__ballot_sync(KNNG_FULL_MASK, own)) - 1;
+        const uint32_t digit = (uint32_t)(chunk * 32 + owner);
+        const uint32_t before = before_chunk + __shfl_sync(KNNG_FULL_MASK, excl, owner);
+        const uint32_t inbin = __shfl_sync(KNNG_FULL_MASK, mine, owner);
+        prefix |= (uint64_t)digit << lo;
+        mask |= (uint64_t)dmask << lo;
         rank -= (int)before;
         __syncwarp();
-        if ((uint32_t)rank == inbin || shift == 0) {
-            const uint64_t low = shift ? ((1ull << shift) - 1) : 0ull;
-            return prefix | low;
-        }
+        if ((uint32_t)rank == inbin || lo == 0) return prefix | lowmask64(lo);
+        hi = lo;
     }
 }
 
@@ -290,14 +331,14 @@ namespace knng {
 
 // Canonical distances from point a to W points b[0..W) (W = 8, 16 or 32;
 // b in shared memory, entries c >= nb unused); lane l returns the distance to
-// b[l % W] (for l % W < nb).  Each lane first forms its partial sums
-// (entries j = 128c' + 4l + e, fmaf) for the W points; then, for offsets
-// o = 16, 8, 4, 2, 1, the partials of lanes l and l^o are added -- for o >= W
-// as a plain butterfly on all W values, for o < W by recursive halving (each
-// lane keeps half of its values and receives its partner's copy of them).
-// These are the pairwise additions of the xor butterfly in warp_canon_dist,
-// so the result is bit-identical to it, with far fewer shuffles and W row
-// loads in flight.
+// b[l % W] (for l % W < nb).  Rows must be vector-aligned with d % 4 == 0.
+// Each lane first forms its partial sums (entries j = 128c' + 4l + e, fmaf)
+// for the W points; then, for offsets o = 16, 8, 4, 2, 1, the partials of
+// lanes l and l^o are added -- for o >= W as a plain butterfly on all W
+// values, for o < W by recursive halving (each lane keeps half of its values
+// and receives its partner's copy of them).  These are the pairwise additions
+// of the xor butterfly in warp_canon_dist, so the result is bit-identical to
+// it, with far fewer shuffles and W row loads in flight.
 template <int W, bool kF16>
 __device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
 {
@@ -309,12 +350,12 @@ __device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kF16>& L,
 #pragma unroll
     for (int c = 0; c < W; ++c) p[c] = 0.f;
     for (int j = 4 * lane; j < L.d; j += 128) {
-        const float4 xa = L.load4(a, j);
+        const float4 xa = L.load4v(a, j);
 #pragma unroll
         for (int c0 = 0; c0 < W; c0 += 8) {
             float4 xb[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) xb[c] = L.load4(bid[c0 + c], j);
+            for (int c = 0; c < 8; ++c) xb[c] = L.load4v(bid[c0 + c], j);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 float t;
@@ -343,14 +384,20 @@ __device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kF16>& L,
     return p[0];
 }
 
-// Canonical distances from a to b[0..nb) (nb <= 32): lane c < nb returns the
-// distance to b[c].
+// Canonical distances from a to b[0..nb) (nb <= 16): lane c < nb returns the
+// distance to b[c].  Vector-aligned rows take the batched path; other rows
+// one distance at a time.
 template <bool kF16>
-__device__ __forceinline__ float warp_canon_dist32(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
+__device__ __forceinline__ float warp_canon_dist16(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
 {
-    if (nb > 16) return warp_canon_dist_batch<32, kF16>(L, a, b, nb);
-    if (nb > 8) return warp_canon_dist_batch<16, kF16>(L, a, b, nb);
-    return warp_canon_dist_batch<8, kF16>(L, a, b, nb);
+    if (L.all_vec()) return warp_canon_dist_batch<16, kF16>(L, a, b, nb);
+    const int lane = threadIdx.x & 31;
+    float mine = 0.f;
+    for (int c = 0; c < nb; ++c) {
+        const float dd = warp_canon_dist(L, a, b[c]);
+        if (lane == c) mine = dd;
+    }
+    return mine;
 }
 
 // Finishes one row of a leaf graph (collective over one warp): from the
@@ -358,10 +405,14 @@ __device__ __forceinline__ float warp_canon_dist32(const RowLoader<kF16>& L, int
 // kp smallest (D~, j), rescore them with the canonical FP32 distance between
 // the original rows, sort by (D, id) and write the k best to oi/od (padding
 // with -1 / +inf).  lid maps local index -> point id (ascending with j).
+//
+// With rescore == false the candidate distances are taken as final: the
+// caller certifies that Drow(j) already equals the canonical distance (see
+// the exactness test of the tensor-core path), and kp should be k.
 template <int E, bool kF16, class DFn>
 __device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m, int self,
                                 const int32_t* lid, int k, int kp, uint32_t* hist, int* cand,
-                                int32_t* oi, float* od)
+                                int32_t* oi, float* od, bool rescore = true)
 {
     const int lane = threadIdx.x & 31;
     auto key = [&](int j) -> uint64_t {
@@ -375,15 +426,18 @@ __device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m
     }
     __syncwarp();
     const int gi = lid[self];
-    // local -> point ids, then rescore 32 (or fewer) candidates per pass;
-    // the keys go to shared memory (the histogram area is free again)
-    for (int c = lane; c < nsel; c += 32) cand[c] = lid[cand[c]];
-    __syncwarp();
-    uint64_t* keys = reinterpret_cast<uint64_t*>(hist);  // 128 keys
-    for (int c0 = 0; c0 < nsel; c0 += 32) {
-        const int nb = min(32, nsel - c0);
-        const float dd = warp_canon_dist32(L, gi, cand + c0, nb);
-        if (lane < nb) keys[c0 + lane] = pack_key(dd, (uint32_t)cand[c0 + lane]);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(hist);  // 128 keys (the histogram area is free again)
+    if (rescore) {
+        // local -> point ids, then rescore 32 (or fewer) candidates per pass
+        for (int c = lane; c < nsel; c += 32) cand[c] = lid[cand[c]];
+        __syncwarp();
+        for (int c0 = 0; c0 < nsel; c0 += 16) {
+            const int nb = min(16, nsel - c0);
+            const float dd = warp_canon_dist16(L, gi, cand + c0, nb);
+            if (lane < nb) keys[c0 + lane] = pack_key(dd, (uint32_t)cand[c0 + lane]);
+        }
+    } else {
+        for (int c = lane; c < nsel; c += 32) keys[c] = pack_key(Drow(cand[c]), (uint32_t)lid[cand[c]]);
     }
     __syncwarp();
     uint64_t v[E];

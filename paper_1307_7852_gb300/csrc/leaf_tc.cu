@@ -39,11 +39,17 @@ constexpr int kTcCand = 128;
 // ---------------------------------------------------------------------------
 // 1. leaf-order gather and quantisation
 // ---------------------------------------------------------------------------
+//     For bfloat16 every row also gets an exactness bit: set when all its
+//     entries are integers of magnitude <= 256 and its squared norm is below
+//     2^23.  Between two such rows every bfloat16 value, product and partial
+//     sum of the Gram is an integer below 2^24, exact in FP32, so the
+//     candidate distance |x|^2 + |y|^2 - 2 x.y equals the true squared
+//     distance, which is also what the canonical FP32 distance returns.
 template <int PREC, bool kF16>
 __global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kF16> L, int64_t rows,
                                                            const int32_t* __restrict__ perm, int dq,
                                                            void* __restrict__ out, float* __restrict__ nrm,
-                                                           float* __restrict__ scl)
+                                                           float* __restrict__ scl, uint8_t* __restrict__ exact)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -51,10 +57,13 @@ __global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kF16> L, in
     for (int64_t r = gw; r < rows; r += nw) {
         const int32_t id = perm[r];
         float s = 0.f;
+        bool ex = true;
         if (PREC == 1) {
             __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + r * dq;
             for (int j = 4 * lane; j < dq; j += 128) {
                 const float4 v = j < L.d ? L.load4(id, j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ex &= v.x == rintf(v.x) && v.y == rintf(v.y) && v.z == rintf(v.z) && v.w == rintf(v.w);
+                ex &= fabsf(v.x) <= 256.f && fabsf(v.y) <= 256.f && fabsf(v.z) <= 256.f && fabsf(v.w) <= 256.f;
                 __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
                 __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
                 const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
@@ -88,7 +97,11 @@ __global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kF16> L, in
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
-        if (lane == 0) nrm[r] = s;
+        ex = __all_sync(KNNG_FULL_MASK, ex);
+        if (lane == 0) {
+            nrm[r] = s;
+            exact[r] = (PREC == 1 && ex && s < 8388608.0f) ? 1 : 0;
+        }
     }
 }
 
@@ -115,7 +128,8 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                                                                 const int32_t* __restrict__ perm,
                                                                 const int32_t* __restrict__ leaf_off,
                                                                 int nleaves, const float* __restrict__ qnrm,
-                                                                const float* __restrict__ qscl, int k, int kp,
+                                                                const float* __restrict__ qscl,
+                                                                const uint8_t* __restrict__ qexact, int k, int kp,
                                                                 TcGeom G, int32_t* __restrict__ out_ids,
                                                                 float* __restrict__ out_d, int* err)
 {
@@ -163,14 +177,17 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
         tc::tmem_relinquish();
     }
     const int64_t rowbase = (int64_t)t * n + off;
+    bool ex = PREC == 1;
     for (int j = tid; j < G.N_load; j += kTcThreads) {
         const bool v = j < m;
         lid[j] = v ? perm[rowbase + j] : 0;
         qn[j] = v ? qnrm[rowbase + j] : 0.f;
         qs[j] = (PREC == 2 && v) ? qscl[rowbase + j] : 1.f;
+        if (v) ex = ex && qexact[rowbase + j];
     }
     tc::fence_before_sync();
-    __syncthreads();
+    // the whole leaf is exact: candidate distances are final, no rescoring
+    const bool exact_leaf = __syncthreads_and(ex) != 0;
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
@@ -267,9 +284,9 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 if (iloc >= m) break;
                 const float* drow = Dblk + (size_t)rr * ldD;
                 const int gi = lid[iloc];
-                leaf_row_finish<E, kF16>(L, [&](int j) { return drow[j]; }, m, iloc, lid, k, kp, hist + 256 * w,
-                                         cand + kTcCand * w, out_ids + ((int64_t)t * n + gi) * k,
-                                         out_d + ((int64_t)t * n + gi) * k);
+                leaf_row_finish<E, kF16>(L, [&](int j) { return drow[j]; }, m, iloc, lid, k, exact_leaf ? k : kp,
+                                         hist + 256 * w, cand + kTcCand * w, out_ids + ((int64_t)t * n + gi) * k,
+                                         out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
             }
             __syncthreads();
         }
@@ -321,7 +338,7 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec)
 
 template <int PREC, int E, bool kF16>
 static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
-                             const int32_t* perm, const float* qn, const float* qs, int k, int kp,
+                             const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
                              const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
 {
     auto kern = leaf_tc_kernel<PREC, E, kF16>;
@@ -330,7 +347,7 @@ static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreeP
     RowLoader<kF16> rl{x.X, x.ld, x.d, x.vec};
     const int nleaves = (int)P.leaf_off.size() - 1;
     const int RB = (P.max_leaf + 127) / 128;
-    kern<<<dim3(nleaves * RB, T), kTcThreads, G.smem, st>>>(map, rl, x.n, perm, dp.leaf_off, nleaves, qn, qs, k, kp,
+    kern<<<dim3(nleaves * RB, T), kTcThreads, G.smem, st>>>(map, rl, x.n, perm, dp.leaf_off, nleaves, qn, qs, qx, k, kp,
                                                             G, ids, dists, err);
     note_launches(1);
     return cudaGetLastError();
@@ -338,12 +355,12 @@ static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreeP
 
 template <int PREC, bool kF16>
 static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
-                               const int32_t* perm, const float* qn, const float* qs, int k, int kp,
+                               const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
                                const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
 {
-    if (kp <= 32) return launch_tc<PREC, 1, kF16>(map, x, P, dp, T, perm, qn, qs, k, kp, G, ids, dists, err, st);
-    if (kp <= 64) return launch_tc<PREC, 2, kF16>(map, x, P, dp, T, perm, qn, qs, k, kp, G, ids, dists, err, st);
-    return launch_tc<PREC, 4, kF16>(map, x, P, dp, T, perm, qn, qs, k, kp, G, ids, dists, err, st);
+    if (kp <= 32) return launch_tc<PREC, 1, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    if (kp <= 64) return launch_tc<PREC, 2, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    return launch_tc<PREC, 4, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
 }
 
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
@@ -357,6 +374,7 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     uint8_t* Xq = ar.take<uint8_t>((size_t)rows * dq * elem);
     float* qn = ar.take<float>((size_t)rows);
     float* qs = ar.take<float>((size_t)rows);
+    uint8_t* qx = ar.take<uint8_t>((size_t)rows);
     if (!ar.base) return cudaSuccess;
     if (kp > kTcCand) kp = kTcCand;
     const TcGeom G = tc_geometry(P, x.d, prec);
@@ -365,12 +383,12 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);
     if (x.dtype == 1) {
         RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
-        if (prec == 1) gather_quant_kernel<1, true><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs);
-        else gather_quant_kernel<2, true><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs);
+        if (prec == 1) gather_quant_kernel<1, true><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
+        else gather_quant_kernel<2, true><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
     } else {
         RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
-        if (prec == 1) gather_quant_kernel<1, false><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs);
-        else gather_quant_kernel<2, false><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs);
+        if (prec == 1) gather_quant_kernel<1, false><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
+        else gather_quant_kernel<2, false><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
     }
     note_launches(1);
 
@@ -387,11 +405,11 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
     if (x.dtype == 1) {
-        if (prec == 1) return dispatch_tc<1, true>(map, x, P, dp, T, perm, qn, qs, k, kp, G, ids, dists, err, st);
-        return dispatch_tc<2, true>(map, x, P, dp, T, perm, qn, qs, k, kp, G, ids, dists, err, st);
+        if (prec == 1) return dispatch_tc<1, true>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+        return dispatch_tc<2, true>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
     }
-    if (prec == 1) return dispatch_tc<1, false>(map, x, P, dp, T, perm, qn, qs, k, kp, G, ids, dists, err, st);
-    return dispatch_tc<2, false>(map, x, P, dp, T, perm, qn, qs, k, kp, G, ids, dists, err, st);
+    if (prec == 1) return dispatch_tc<1, false>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    return dispatch_tc<2, false>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
 }
 
 }  // namespace knng

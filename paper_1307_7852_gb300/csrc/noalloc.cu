@@ -61,7 +61,7 @@ extern "C" int knng_propagate_noalloc(const void* X, int32_t dtype, int64_t n, i
 {
     if (!X || !ids_in || !dists_in || !ids || !dists) return KNNG_ERR_INVALID_ARG;
     if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16) return KNNG_ERR_INVALID_ARG;
-    if (n < 2 || d < 1 || d > 4096 || ld < d || k < 1 || k > kMaxK) return KNNG_ERR_INVALID_ARG;
+    if (n < 2 || d < 1 || d > 4096 || ld < d || ld >= (int64_t)1 << 31 || k < 1 || k > kMaxK) return KNNG_ERR_INVALID_ARG;
     if (rounds < 1 || rounds > 16) return KNNG_ERR_INVALID_ARG;
     if (n > kNoAllocMaxPoints || n * (int64_t)k > kNoAllocMaxEntries) return KNNG_ERR_LIMIT;
     int dev = 0;

@@ -13,12 +13,18 @@
 //    already in p's previous list and c already in q's previous list.  Then c
 //    was a candidate of p in the previous round, so either c is in p's list
 //    or k listed points beat it, and it cannot enter the new list.
-//  * Scoring: 32 candidates at a time by warp_canon_dist32 (coalesced 16-byte
-//    row loads, 32 rows in flight per warp, bit-identical canonical FP32).
+//  * Scoring: 16 candidates at a time by warp_canon_dist16 (coalesced 16-byte
+//    row loads, 16 rows in flight per warp, bit-identical canonical FP32).
 //  * The k best by (dist, id): warp radix select and a warp bitonic sort; the
 //    output flags mark the entries that were not in p's input list.
 #include "knng_common.cuh"
 #include "knng_internal.h"
+
+// Blocks of 256 threads the register budget is sized for (2: 128 registers,
+// no spills; 3: 80 registers with small spills, 24 resident warps).
+#ifndef KNNG_PROP_MINBLOCKS
+#define KNNG_PROP_MINBLOCKS 2
+#endif
 
 namespace knng {
 
@@ -39,15 +45,16 @@ static PropLayout prop_layout(int k)
     int lg = 0;
     while ((1 << lg) < H) ++lg;
     L.hshift = 32 - lg;
-    // tab[H] | cid[cap] | cd[cap] | hist[256] | sel[64] | own[64] | ownflag (u64)
+    // tab[H] | cid[cap] | cd[cap] | hist[256] | sel[64] | own[64] | own_fl[64] (u64)
+    L.cap = (L.cap + 1) & ~1;  // keeps own_fl 8-byte aligned
     L.per_warp = sizeof(int) * (size_t)H + (sizeof(int) + sizeof(float)) * (size_t)L.cap +
-                 sizeof(uint32_t) * 256 + sizeof(int) * 64 + sizeof(int) * 64 + 16;
+                 sizeof(uint32_t) * 256 + sizeof(int) * 64 + sizeof(int) * 64 + sizeof(unsigned long long) * 64;
     L.per_warp = (L.per_warp + 15) & ~(size_t)15;
     return L;
 }
 
 template <int E, bool kF16>
-__global__ void __launch_bounds__(256, 2) propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int32_t* __restrict__ order,
+__global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int32_t* __restrict__ order,
                                  const int32_t* __restrict__ ids_in, const float* __restrict__ d_in,
                                  const unsigned long long* __restrict__ flags_in, int32_t* __restrict__ ids_out,
                                  float* __restrict__ d_out, unsigned long long* __restrict__ flags_out, int H,
@@ -62,6 +69,7 @@ __global__ void __launch_bounds__(256, 2) propagate_kernel(RowLoader<kF16> L, in
     uint32_t* hist = reinterpret_cast<uint32_t*>(cd + cap);
     int* sel = reinterpret_cast<int*>(hist + 256);
     int* own = sel + 64;
+    unsigned long long* own_fl = reinterpret_cast<unsigned long long*>(own + 64);
     const uint32_t hmask = (uint32_t)H - 1;
     const int kk = k * k;
 
@@ -96,17 +104,24 @@ __global__ void __launch_bounds__(256, 2) propagate_kernel(RowLoader<kF16> L, in
             cnt += __popc(b);
         }
         const int nknown = cnt;
+        // flags of the neighbours' lists (entries of a list that are new)
+        if (flags_in)
+            for (int e = lane; e < k; e += 32) {
+                const int32_t q = own[e];
+                own_fl[e] = q >= 0 ? flags_in[q] : 0ull;
+            }
         __syncwarp();
-        // the neighbours' lists, lanes over (neighbour e, slot f)
+        // the neighbours' lists, lanes over (neighbour e, slot f) with
+        // i = e*k + f = lane + 32*step, advanced without division
+        int e = lane / k, f = lane - (lane / k) * k;
+        const int de = 32 / k, df = 32 - (32 / k) * k;
         for (int i0 = 0; i0 < kk; i0 += 32) {
-            const int i = i0 + lane;
             int32_t o = -1;
-            if (i < kk) {
-                const int e = i / k, f = i - e * k;
+            if (i0 + lane < kk) {
                 const int32_t q = own[e];
                 if (q >= 0 && q != p) {
                     const bool qnew = (pf >> e) & 1ull;
-                    const bool cnew = flags_in ? ((flags_in[q] >> f) & 1ull) : true;
+                    const bool cnew = flags_in ? ((own_fl[e] >> f) & 1ull) : true;
                     if (qnew || cnew) o = ids_in[(int64_t)q * k + f];
                     if (o >= n) o = -1;
                 }
@@ -115,12 +130,15 @@ __global__ void __launch_bounds__(256, 2) propagate_kernel(RowLoader<kF16> L, in
             const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
             if (ins) cid[cnt + __popc(b & lanemask_lt())] = o;
             cnt += __popc(b);
+            e += de;
+            f += df;
+            if (f >= k) { f -= k; ++e; }
         }
         __syncwarp();
         // score the new candidates, 32 at a time
-        for (int c0 = nknown; c0 < cnt; c0 += 32) {
-            const int nb = min(32, cnt - c0);
-            const float dd = warp_canon_dist32(L, p, cid + c0, nb);
+        for (int c0 = nknown; c0 < cnt; c0 += 16) {
+            const int nb = min(16, cnt - c0);
+            const float dd = warp_canon_dist16(L, p, cid + c0, nb);
             if (lane < nb) cd[c0 + lane] = dd;
         }
         __syncwarp();
