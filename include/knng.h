@@ -113,6 +113,31 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
 int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d,
                     int64_t ld, const knng_params* p, int32_t* ids, float* dists, void* stream);
 
+/* ---- many independent point sets ----------------------------------------- */
+/* One independent point set of a batch: X (device, row-major, rows of ld
+ * elements) and its outputs ids/dists (device [n][k]). */
+typedef struct knng_dataset {
+    const void* X;
+    int32_t dtype; /* KNNG_DTYPE_* */
+    int32_t d;
+    int64_t n;
+    int64_t ld;
+    int32_t* ids;
+    float* dists;
+} knng_dataset;
+
+/* Builds the graphs of nsets independent point sets with the same
+ * parameters (Sec. 3 applied to each set).  Every set gets exactly the graph
+ * knng_build would produce for it alone.  Sets of equal (d, dtype) are
+ * processed together: their trees form one forest whose roots are the sets,
+ * so each stage is one launch for the whole group.  The first call with a
+ * given batch (pointers, sizes, parameters) records the whole batch once as a
+ * CUDA graph; later identical calls replay it with a single graph launch.
+ * The first call synchronises `stream` (table upload); make it outside any
+ * stream capture.  1 <= nsets <= 65536; per set the limits of knng_build. */
+int knng_build_batched(knng_handle* h, int32_t nsets, const knng_dataset* sets, const knng_params* p,
+                       void* stream);
+
 /* ---- stages ---------------------------------------------------------- */
 /* Random divisions (Sec. 3.1; split rule of the appendix after Lemma 1).
  * perm: device int32 [T][n].  Row t lists the point ids of tree t leaf by

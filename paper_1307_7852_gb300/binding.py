@@ -33,6 +33,12 @@ class KnngError(RuntimeError):
         self.code = code
 
 
+class knng_dataset(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("ids", ctypes.c_void_p),
+                ("dists", ctypes.c_void_p)]
+
+
 class knng_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("T", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("prop_rounds", ctypes.c_int32), ("seed", ctypes.c_uint64),
@@ -59,6 +65,7 @@ SIGNATURES = {
     "knng_set_stage_events": [_P, _P, _I32],
     "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
     "knng_sync": [_P, _P],
+    "knng_build_batched": [_P, _I32, _P, ctypes.POINTER(knng_params), _P],
     "knng_propagate_noalloc": [_P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
 }
 
@@ -340,3 +347,27 @@ def knng_propagate_noalloc(X, ids_in, dists_in, rounds=1, ids=None, dists=None, 
     if rc != KNNG_OK:
         raise KnngError(rc, "knng_propagate_noalloc: " + lib().knng_status_string(rc).decode())
     return ids, dists
+
+
+def knng_build_batched(Xs, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
+                       outs=None, stream=None, h: Handle = None):
+    """Graphs of many independent point sets (CUDA tensors) in one recorded
+    launch; returns a list of (ids, dists) per set."""
+    torch = _torch()
+    if not Xs:
+        raise ValueError("no point sets")
+    dev = Xs[0].device
+    h = h or handle(dev.index or 0)
+    arr = (knng_dataset * len(Xs))()
+    res = []
+    for i, X in enumerate(Xs):
+        xp, dt, n, d, ld = _xdesc(X)
+        oi, od = (outs[i] if outs is not None else (None, None))
+        oi = _out((n, k), torch.int32, dev, oi)
+        od = _out((n, k), torch.float32, dev, od)
+        arr[i] = knng_dataset(xp.value, dt, d, n, ld, oi.data_ptr(), od.data_ptr())
+        res.append((oi, od))
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    h.check(lib().knng_build_batched(h.ptr, len(Xs), arr, ctypes.byref(p), _stream(dev, stream)),
+            "knng_build_batched")
+    return res

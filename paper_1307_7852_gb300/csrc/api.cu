@@ -31,6 +31,28 @@ int num_sms()
 
 using namespace knng;
 
+// A recorded batched build (knng_build_batched): the batch it was recorded
+// for, its device tables and the instantiated CUDA graph.
+struct BatchGroup {
+    int dtype = 0, d = 0;
+    int64_t n = 0, ld = 0;
+    std::vector<int> members;
+    TreePlan plan;
+    DevPlan dp;
+    const BatchSet* dev_sets = nullptr;
+};
+struct BatchCache {
+    std::vector<uint64_t> sig;
+    std::vector<BatchGroup> groups;
+    char* tables = nullptr;
+    size_t tables_size = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int kernels = 0;  // kernel nodes of the graph
+};
+
 struct knng_handle {
     int device = 0;
     char* ws = nullptr;
@@ -41,6 +63,7 @@ struct knng_handle {
     DevPlan dplan;
     std::vector<cudaEvent_t> stage_ev;
     int* dev_err = nullptr;  // set by kernels whose bounded waits gave up
+    BatchCache batch;
     std::string err;
 };
 
@@ -181,20 +204,99 @@ int check_k(knng_handle* h, int32_t k, int32_t g)
 
 // Leaf graphs of all trees.  With ar.base == nullptr only measures the
 // scratch the stage needs.
-int leaf_stage(knng_handle* h, const XDesc& x, int T, const int32_t* perm, int k, int prec, int mult,
-               int32_t* ids, float* dists, Arena& ar, cudaStream_t st)
+int leaf_stage(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc& x, int T, const int32_t* perm,
+               int k, int prec, int mult, int32_t* ids, float* dists, Arena& ar, cudaStream_t st)
 {
     cudaError_t e;
     const int kp = std::min(mult * k, 128);
     if (prec == KNNG_PREC_FP32) {
         if (!ar.base) return KNNG_OK;
-        e = run_leaf_knn_f32(x, h->plan, h->dplan, T, perm, k, kp, ids, dists, st);
+        e = run_leaf_knn_f32(x, P, dp, T, perm, k, kp, ids, dists, st);
     } else if (prec == KNNG_PREC_BF16 || prec == KNNG_PREC_FP8E4M3) {
-        e = run_leaf_knn_tc(x, h->plan, h->dplan, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st);
+        e = run_leaf_knn_tc(x, P, dp, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st);
     } else {
         return fail(h, KNNG_ERR_INVALID_ARG, "precision %d", prec);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "leaf k-NN");
+    return KNNG_OK;
+}
+
+int check_params(knng_handle* h, const knng_params* p, int64_t n)
+{
+    if (!p) return fail(h, KNNG_ERR_INVALID_ARG, "params is NULL");
+    int r;
+    if ((r = check_tree(h, p->T, p->leaf_size))) return r;
+    if ((r = check_k(h, p->k, n > p->leaf_size ? p->leaf_size : -1))) return r;
+    if (p->prop_rounds < 0 || p->prop_rounds > 16) return fail(h, KNNG_ERR_INVALID_ARG, "prop_rounds %d", p->prop_rounds);
+    if (p->rescore_mult < 1 || p->rescore_mult > 4) return fail(h, KNNG_ERR_INVALID_ARG, "rescore_mult %d", p->rescore_mult);
+    if (p->partitioner != KNNG_PART_RANDOM) return fail(h, KNNG_ERR_UNSUPPORTED, "partitioner %d", p->partitioner);
+    if (p->reserved != 0) return fail(h, KNNG_ERR_INVALID_ARG, "reserved must be 0");
+    return KNNG_OK;
+}
+
+// The whole method over one point set (or one forest of sets): divisions,
+// leaf graphs, merge, propagation rounds.  Carves its buffers from ar; with
+// ar.base == nullptr it only measures them.
+int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc& x, const knng_params& p,
+                   int32_t* ids, float* dists, Arena& a, cudaStream_t st, bool events)
+{
+    const int64_t n = x.n;
+    const int T = p.T, k = p.k, R = p.prop_rounds;
+    const size_t nk = (size_t)n * k;
+    // perm | leaf lists | propagation buffers | max(partition, leaf scratch)
+    int32_t* perm = a.take<int32_t>((size_t)T * n);
+    int32_t* li = a.take<int32_t>((size_t)T * nk);
+    float* ld_ = a.take<float>((size_t)T * nk);
+    int32_t* bi[2];
+    float* bd[2];
+    unsigned long long* fl[2];
+    for (int b = 0; b < 2; ++b) {
+        bi[b] = a.take<int32_t>(nk);
+        bd[b] = a.take<float>(nk);
+        fl[b] = a.take<unsigned long long>(n);
+    }
+    const size_t fixed = a.off;
+    int r;
+    if (!a.base) {
+        run_partition(x, P, dp, T, p.seed, nullptr, a, st);
+        const size_t part_end = a.off;
+        a.off = fixed;
+        if ((r = leaf_stage(h, P, dp, x, T, nullptr, k, p.precision, p.rescore_mult, nullptr, nullptr, a, st)))
+            return r;
+        a.off = std::max(part_end, a.off);
+        return KNNG_OK;
+    }
+    const bool rec = events && (int)h->stage_ev.size() >= 4 + R;
+    auto mark = [&](int i) {
+        if (rec) cudaEventRecord(h->stage_ev[i], st);
+    };
+    mark(0);
+    cudaError_t e = run_partition(x, P, dp, T, p.seed, perm, a, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "partition");
+    mark(1);
+    const size_t part_end = a.off;
+    a.off = fixed;  // the partition scratch is dead: the leaf stage reuses it
+    if ((r = leaf_stage(h, P, dp, x, T, perm, k, p.precision, p.rescore_mult, li, ld_, a, st))) return r;
+    a.off = std::max(part_end, a.off);
+    mark(2);
+    int32_t* mi = R == 0 ? ids : bi[0];
+    float* md = R == 0 ? dists : bd[0];
+    e = run_merge(n, T, k, li, ld_, mi, md, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "merge");
+    mark(3);
+    // propagation visits points in the leaf order of tree 0: neighbouring
+    // points run together, so candidate rows are shared through L2.
+    for (int rd = 0; rd < R; ++rd) {
+        const int32_t* si = bi[rd & 1];
+        const float* sd = bd[rd & 1];
+        const unsigned long long* sf = rd == 0 ? nullptr : fl[rd & 1];
+        int32_t* oi = rd == R - 1 ? ids : bi[(rd + 1) & 1];
+        float* od = rd == R - 1 ? dists : bd[(rd + 1) & 1];
+        unsigned long long* of = rd == R - 1 ? nullptr : fl[(rd + 1) & 1];
+        e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
+        mark(4 + rd);
+    }
     return KNNG_OK;
 }
 
@@ -254,6 +356,13 @@ int knng_destroy(knng_handle* h)
         if (h->ws) cudaFree(h->ws);
         if (h->plan_dev) cudaFree(h->plan_dev);
         if (h->dev_err) cudaFree(h->dev_err);
+        BatchCache& B = h->batch;
+        if (B.exec) cudaGraphExecDestroy(B.exec);
+        if (B.graph) cudaGraphDestroy(B.graph);
+        if (B.tables) cudaFree(B.tables);
+        if (B.cap) cudaStreamDestroy(B.cap);
+        if (B.ev_in) cudaEventDestroy(B.ev_in);
+        if (B.ev_out) cudaEventDestroy(B.ev_out);
     }
     delete h;
     return KNNG_OK;
@@ -318,11 +427,11 @@ int knng_leaf_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((r = ensure_plan(h, n, g, st))) return r;
     Arena m;
-    if ((r = leaf_stage(h, x, T, perm, k, precision, rescore_mult, ids, dists, m, st))) return r;
+    if ((r = leaf_stage(h, h->plan, h->dplan, x, T, perm, k, precision, rescore_mult, ids, dists, m, st))) return r;
     if ((r = ensure_ws(h, m.off, st))) return r;
     Arena a;
     a.base = h->ws;
-    return leaf_stage(h, x, T, perm, k, precision, rescore_mult, ids, dists, a, st);
+    return leaf_stage(h, h->plan, h->dplan, x, T, perm, k, precision, rescore_mult, ids, dists, a, st);
 }
 
 int knng_merge(knng_handle* h, int64_t n, int32_t T, int32_t k, const int32_t* ids_in,
@@ -391,77 +500,17 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     XDesc x;
     int r = check_x(h, X, dtype, n, d, ld, x);
     if (r) return r;
-    if (!p) return fail(h, KNNG_ERR_INVALID_ARG, "params is NULL");
-    if ((r = check_tree(h, p->T, p->leaf_size))) return r;
-    if ((r = check_k(h, p->k, n > p->leaf_size ? p->leaf_size : -1))) return r;
-    if (p->prop_rounds < 0 || p->prop_rounds > 16) return fail(h, KNNG_ERR_INVALID_ARG, "prop_rounds %d", p->prop_rounds);
-    if (p->rescore_mult < 1 || p->rescore_mult > 4) return fail(h, KNNG_ERR_INVALID_ARG, "rescore_mult %d", p->rescore_mult);
-    if (p->partitioner != KNNG_PART_RANDOM) return fail(h, KNNG_ERR_UNSUPPORTED, "partitioner %d", p->partitioner);
-    if (p->reserved != 0) return fail(h, KNNG_ERR_INVALID_ARG, "reserved must be 0");
+    if ((r = check_params(h, p, n))) return r;
     if (!ids || !dists) return fail(h, KNNG_ERR_INVALID_ARG, "NULL output");
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((r = ensure_plan(h, n, p->leaf_size, st))) return r;
-    const int T = p->T, k = p->k;
-    const size_t nk = (size_t)n * k;
-    // workspace: perm | leaf lists | propagation buffers | max(partition, leaf scratch)
     Arena m;
-    m.take<int32_t>((size_t)T * n);
-    m.take<int32_t>((size_t)T * nk);
-    m.take<float>((size_t)T * nk);
-    for (int b = 0; b < 2; ++b) { m.take<int32_t>(nk); m.take<float>(nk); m.take<unsigned long long>(n); }
-    const size_t fixed = m.off;
-    run_partition(x, h->plan, h->dplan, T, p->seed, nullptr, m, st);
-    const size_t part_end = m.off;
-    m.off = fixed;
-    if ((r = leaf_stage(h, x, T, nullptr, k, p->precision, p->rescore_mult, nullptr, nullptr, m, st))) return r;
-    const size_t total = std::max(part_end, m.off);
-    if ((r = ensure_ws(h, total, st))) return r;
+    if ((r = build_pipeline(h, h->plan, h->dplan, x, *p, ids, dists, m, st, true))) return r;
+    if ((r = ensure_ws(h, m.off, st))) return r;
     Arena a;
     a.base = h->ws;
-    int32_t* perm = a.take<int32_t>((size_t)T * n);
-    int32_t* li = a.take<int32_t>((size_t)T * nk);
-    float* ld_ = a.take<float>((size_t)T * nk);
-    int32_t* bi[2];
-    float* bd[2];
-    unsigned long long* fl[2];
-    for (int b = 0; b < 2; ++b) {
-        bi[b] = a.take<int32_t>(nk);
-        bd[b] = a.take<float>(nk);
-        fl[b] = a.take<unsigned long long>(n);
-    }
-    const size_t fixed2 = a.off;
-    const int R = p->prop_rounds;
-    const bool rec = (int)h->stage_ev.size() >= 4 + R;
-    auto mark = [&](int i) {
-        if (rec) cudaEventRecord(h->stage_ev[i], st);
-    };
-    mark(0);
-    cudaError_t e = run_partition(x, h->plan, h->dplan, T, p->seed, perm, a, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "partition");
-    mark(1);
-    a.off = fixed2;  // the partition scratch is dead: the leaf stage reuses it
-    if ((r = leaf_stage(h, x, T, perm, k, p->precision, p->rescore_mult, li, ld_, a, st))) return r;
-    mark(2);
-    int32_t* mi = R == 0 ? ids : bi[0];
-    float* md = R == 0 ? dists : bd[0];
-    e = run_merge(n, T, k, li, ld_, mi, md, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "merge");
-    mark(3);
-    // propagation visits points in the leaf order of tree 0: neighbouring
-    // points run together, so candidate rows are shared through L2.
-    for (int rd = 0; rd < R; ++rd) {
-        const int32_t* si = bi[rd & 1];
-        const float* sd = bd[rd & 1];
-        const unsigned long long* sf = rd == 0 ? nullptr : fl[rd & 1];
-        int32_t* oi = rd == R - 1 ? ids : bi[(rd + 1) & 1];
-        float* od = rd == R - 1 ? dists : bd[(rd + 1) & 1];
-        unsigned long long* of = rd == R - 1 ? nullptr : fl[(rd + 1) & 1];
-        e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st);
-        if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
-        mark(4 + rd);
-    }
-    return KNNG_OK;
+    return build_pipeline(h, h->plan, h->dplan, x, *p, ids, dists, a, st, true);
 }
 
 int knng_exact_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
@@ -521,6 +570,180 @@ int knng_set_stage_events(knng_handle* h, void* const* events, int32_t nevents)
         }
         h->stage_ev.push_back(ev);
     }
+    return KNNG_OK;
+}
+
+int knng_build_batched(knng_handle* h, int32_t nsets, const knng_dataset* sets, const knng_params* p, void* stream)
+{
+    if (!h) return KNNG_ERR_INVALID_ARG;
+    if (nsets < 1 || nsets > 65536 || !sets) return fail(h, KNNG_ERR_INVALID_ARG, "nsets = %d", nsets);
+    if (!p) return fail(h, KNNG_ERR_INVALID_ARG, "params is NULL");
+    int r;
+    for (int i = 0; i < nsets; ++i) {
+        XDesc x;
+        const knng_dataset& D = sets[i];
+        if ((r = check_x(h, D.X, D.dtype, D.n, D.d, D.ld, x))) return r;
+        if ((r = check_params(h, p, D.n))) return r;
+        if (!D.ids || !D.dists) return fail(h, KNNG_ERR_INVALID_ARG, "set %d: NULL output", i);
+    }
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BatchCache& B = h->batch;
+    std::vector<uint64_t> sig;
+    sig.push_back((uint64_t)nsets);
+    const uint64_t* pw = reinterpret_cast<const uint64_t*>(p);
+    for (size_t i = 0; i < sizeof(knng_params) / 8; ++i) sig.push_back(pw[i]);
+    for (int i = 0; i < nsets; ++i) {
+        const knng_dataset& D = sets[i];
+        sig.push_back((uint64_t)(uintptr_t)D.X);
+        sig.push_back(((uint64_t)(uint32_t)D.dtype << 32) | (uint32_t)D.d);
+        sig.push_back((uint64_t)D.n);
+        sig.push_back((uint64_t)D.ld);
+        sig.push_back((uint64_t)(uintptr_t)D.ids);
+        sig.push_back((uint64_t)(uintptr_t)D.dists);
+    }
+    if (!B.cap) {
+        if (cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B.ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, KNNG_ERR_CUDA, "batch stream / events");
+        }
+    }
+    if (!B.exec || sig != B.sig) {
+        // ---- record the batch: groups of equal (dtype, d) form one forest
+        if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+        if (B.graph) { cudaGraphDestroy(B.graph); B.graph = nullptr; }
+        B.sig.clear();
+        B.groups.clear();
+        for (int i = 0; i < nsets; ++i) {
+            BatchGroup* g = nullptr;
+            for (BatchGroup& q : B.groups)
+                if (q.dtype == sets[i].dtype && q.d == sets[i].d) g = &q;
+            if (!g) {
+                B.groups.emplace_back();
+                g = &B.groups.back();
+                g->dtype = sets[i].dtype;
+                g->d = sets[i].d;
+                g->ld = (sets[i].d + 3) & ~3;
+            }
+            g->members.push_back(i);
+        }
+        // plans and tables (one device buffer for all groups)
+        std::vector<char> host;
+        auto put = [&](const void* src, size_t bytes) {
+            size_t o = (host.size() + 255) & ~(size_t)255;
+            host.resize(o + bytes);
+            if (bytes) memcpy(host.data() + o, src, bytes);
+            return o;
+        };
+        std::vector<size_t> offs;
+        for (BatchGroup& g : B.groups) {
+            std::vector<int64_t> roots;
+            std::vector<BatchSet> bs;
+            int64_t off = 0;
+            for (int i : g.members) {
+                roots.push_back(sets[i].n);
+                bs.push_back(BatchSet{off, sets[i].n, sets[i].ids, sets[i].dists});
+                off += sets[i].n;
+            }
+            g.n = off;
+            if (g.n >= (int64_t)1 << 31) return fail(h, KNNG_ERR_UNSUPPORTED, "a group of sets exceeds 2^31 points");
+            make_forest_plan(roots, p->leaf_size, g.plan);
+            offs.push_back(put(g.plan.nodes.data(), sizeof(SplitNode) * g.plan.nodes.size()));
+            offs.push_back(put(g.plan.chunks.data(), sizeof(Chunk) * g.plan.chunks.size()));
+            offs.push_back(put(g.plan.leaf_off.data(), sizeof(int32_t) * g.plan.leaf_off.size()));
+            offs.push_back(put(bs.data(), sizeof(BatchSet) * bs.size()));
+        }
+        if (host.size() > B.tables_size) {
+            cudaStreamSynchronize(st);
+            if (B.tables) cudaFree(B.tables);
+            B.tables = nullptr;
+            B.tables_size = 0;
+            void* q = nullptr;
+            if (cudaMalloc(&q, host.size()) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, KNNG_ERR_OOM, "batch tables");
+            }
+            B.tables = static_cast<char*>(q);
+            B.tables_size = host.size();
+        } else {
+            cudaStreamSynchronize(st);
+        }
+        if (cudaMemcpy(B.tables, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cuda_fail(h, cudaGetLastError(), "batch table upload");
+        for (size_t gi = 0; gi < B.groups.size(); ++gi) {
+            BatchGroup& g = B.groups[gi];
+            g.dp.nodes = reinterpret_cast<const SplitNode*>(B.tables + offs[4 * gi + 0]);
+            g.dp.chunks = reinterpret_cast<const Chunk*>(B.tables + offs[4 * gi + 1]);
+            g.dp.leaf_off = reinterpret_cast<const int32_t*>(B.tables + offs[4 * gi + 2]);
+            g.dev_sets = reinterpret_cast<const BatchSet*>(B.tables + offs[4 * gi + 3]);
+        }
+        // workspace: the largest group (groups run one after another)
+        size_t need = 0;
+        for (BatchGroup& g : B.groups) {
+            Arena m;
+            const size_t es = g.dtype == KNNG_DTYPE_F16 ? 2 : 4;
+            m.take<char>((size_t)g.n * g.ld * es);
+            m.take<int32_t>((size_t)g.n * p->k);
+            m.take<float>((size_t)g.n * p->k);
+            XDesc x{nullptr, g.dtype, g.n, g.d, g.ld, true};
+            if ((r = build_pipeline(h, g.plan, g.dp, x, *p, nullptr, nullptr, m, st, false))) return r;
+            need = std::max(need, m.off);
+        }
+        if ((r = ensure_ws(h, need, st))) return r;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "batch setup");
+        // record every group's pipeline into one graph
+        if (cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return cuda_fail(h, cudaGetLastError(), "begin capture");
+        int rr = KNNG_OK;
+        const unsigned long long c0 = launch_count();
+        for (BatchGroup& g : B.groups) {
+            Arena a;
+            a.base = h->ws;
+            const size_t es = g.dtype == KNNG_DTYPE_F16 ? 2 : 4;
+            char* xc = a.take<char>((size_t)g.n * g.ld * es);
+            int32_t* gi = a.take<int32_t>((size_t)g.n * p->k);
+            float* gd = a.take<float>((size_t)g.n * p->k);
+            int64_t off = 0;
+            for (int i : g.members) {
+                const knng_dataset& D = sets[i];
+                cudaMemcpy2DAsync(xc + (size_t)off * g.ld * es, (size_t)g.ld * es, D.X, (size_t)D.ld * es,
+                                  (size_t)D.d * es, (size_t)D.n, cudaMemcpyDeviceToDevice, B.cap);
+                off += D.n;
+            }
+            XDesc x{xc, g.dtype, g.n, g.d, g.ld, true};
+            if ((rr = build_pipeline(h, g.plan, g.dp, x, *p, gi, gd, a, B.cap, false))) break;
+            if (run_scatter_batch(g.n, p->k, g.dev_sets, (int)g.members.size(), gi, gd, B.cap) != cudaSuccess) {
+                rr = cuda_fail(h, cudaGetLastError(), "batch scatter");
+                break;
+            }
+        }
+        // kernels recorded into the graph run on replay, not now
+        B.kernels = (int)(launch_count() - c0);
+        note_launches(-B.kernels);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(B.cap, &graph);
+        if (rr) {
+            if (graph) cudaGraphDestroy(graph);
+            return rr;
+        }
+        if (ec != cudaSuccess || !graph) return cuda_fail(h, ec, "end capture");
+        if (cudaGraphInstantiate(&B.exec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_fail(h, cudaGetLastError(), "graph instantiate");
+        }
+        B.graph = graph;
+        B.sig = sig;
+    }
+    // ---- one graph launch, ordered after and before the caller's stream
+    cudaError_t e = cudaEventRecord(B.ev_in, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B.cap, B.ev_in, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(B.exec, B.cap);
+    note_launches(B.kernels);
+    if (e == cudaSuccess) e = cudaEventRecord(B.ev_out, B.cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B.ev_out, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
     return KNNG_OK;
 }
 

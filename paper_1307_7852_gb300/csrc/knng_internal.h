@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -43,19 +44,25 @@ constexpr int kMaxLeaf = 512;      // largest leaf size g
 constexpr int kMaxK = 64;
 constexpr int kMaxT = 32;
 
+// The split nodes of one level: the nbig nodes larger than kSmallCap come
+// first (split by the multi-block path), the others after them (one block
+// each).
 struct LevelPlan {
     int64_t node_base;   // offset of this level's SplitNode array in the plan table
     int32_t nnodes;
-    int32_t max_size;
-    bool small;          // every split node <= kSmallCap
-    int64_t chunk_base;  // offset of this level's Chunk array (large levels)
+    int32_t nbig;
+    int32_t max_small;   // largest node split by one block (0 if none)
+    int64_t chunk_base;  // offset of this level's Chunk array (big nodes)
     int32_t nchunks;
 };
 
-// Shape of every tree over n points with leaf size g (shared by all trees).
+// Shape of every tree over n points with leaf size g (shared by all trees),
+// or of a forest: one tree per root segment (independent point sets stored
+// back to back), with node numbers local to each tree.
 struct TreePlan {
     int64_t n = -1;
     int g = -1;
+    std::vector<int64_t> roots;    // root sizes (one root for a single set)
     std::vector<LevelPlan> levels;
     std::vector<SplitNode> nodes;  // all levels, concatenated
     std::vector<Chunk> chunks;     // large levels, concatenated
@@ -67,6 +74,7 @@ struct TreePlan {
 };
 
 void make_tree_plan(int64_t n, int g, TreePlan& plan);
+void make_forest_plan(const std::vector<int64_t>& roots, int g, TreePlan& plan);
 
 // Device copy of a TreePlan.
 struct DevPlan {
@@ -123,6 +131,16 @@ cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int
 
 cudaError_t run_exact_knn(const XDesc& x, const int32_t* queries, int nq, int k, int32_t* ids,
                           float* dists, cudaStream_t st);
+
+// One set of a batched build, as seen by the output scatter.
+struct BatchSet {
+    int64_t off;  // first global point id of the set
+    int64_t n;
+    int32_t* ids;
+    float* dists;
+};
+cudaError_t run_scatter_batch(int64_t ng, int k, const BatchSet* sets, int nsets, const int32_t* gi,
+                              const float* gd, cudaStream_t st);
 
 int num_sms();
 

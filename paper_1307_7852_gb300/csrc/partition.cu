@@ -27,10 +27,13 @@ namespace knng {
 // Host: the tree shape.  Sizes at a level are floor/ceil halves, so the
 // shape depends on (n, g) only and is shared by all trees.
 // ---------------------------------------------------------------------------
-void make_tree_plan(int64_t n, int g, TreePlan& P)
+void make_forest_plan(const std::vector<int64_t>& roots, int g, TreePlan& P)
 {
+    int64_t n = 0;
+    for (int64_t r : roots) n += r;
     P.n = n;
     P.g = g;
+    P.roots = roots;
     P.levels.clear();
     P.nodes.clear();
     P.chunks.clear();
@@ -40,50 +43,74 @@ void make_tree_plan(int64_t n, int g, TreePlan& P)
     P.max_big_nodes = 0;
     P.max_leaf = 0;
 
-    struct Tmp { uint32_t v; int64_t off, size; };
+    struct Tmp {
+        uint32_t v;
+        int64_t off, size;
+        int parent;  // index in the previous level's (sorted) list
+        int side;    // 0 left, 1 right
+    };
     std::vector<Tmp> cur;
     std::vector<std::pair<int64_t, int64_t>> leaves;  // (off, size)
-    if (n > g) cur.push_back({0u, 0, n});
-    else leaves.push_back({0, n});
+    int64_t off = 0;
+    for (int64_t r : roots) {
+        if (r > g) cur.push_back({0u, off, r, -1, 0});
+        else if (r > 0) leaves.push_back({off, r});
+        off += r;
+    }
     while (!cur.empty()) {
+        // big nodes first, then small ones, each group in offset order
+        std::stable_sort(cur.begin(), cur.end(), [](const Tmp& a, const Tmp& b) {
+            return (a.size > kSmallCap) > (b.size > kSmallCap);
+        });
+        // link the parents of the previous level to these positions
+        if (!P.levels.empty()) {
+            const LevelPlan& prev = P.levels.back();
+            for (size_t i = 0; i < cur.size(); ++i) {
+                SplitNode& pn = P.nodes[prev.node_base + cur[i].parent];
+                if (cur[i].side == 0) pn.childL = (int32_t)i;
+                else pn.childR = (int32_t)i;
+            }
+        }
         LevelPlan L;
         L.node_base = (int64_t)P.nodes.size();
         L.nnodes = (int32_t)cur.size();
-        L.max_size = 0;
+        L.nbig = 0;
+        L.max_small = 0;
         std::vector<Tmp> nxt;
-        for (const Tmp& t : cur) {
+        for (size_t i = 0; i < cur.size(); ++i) {
+            const Tmp& t = cur[i];
             SplitNode s{};
             s.v = t.v;
             s.off = (int32_t)t.off;
             s.size = (int32_t)t.size;
+            s.childL = -1;
+            s.childR = -1;
             const int64_t ml = t.size / 2, mr = t.size - ml;
-            if (ml > g) { s.childL = (int32_t)nxt.size(); nxt.push_back({2 * t.v, t.off, ml}); }
-            else { s.childL = -1; leaves.push_back({t.off, ml}); }
-            if (mr > g) { s.childR = (int32_t)nxt.size(); nxt.push_back({2 * t.v + 1, t.off + ml, mr}); }
-            else { s.childR = -1; leaves.push_back({t.off + ml, mr}); }
+            if (ml > g) nxt.push_back({2 * t.v, t.off, ml, (int)i, 0});
+            else leaves.push_back({t.off, ml});
+            if (mr > g) nxt.push_back({2 * t.v + 1, t.off + ml, mr, (int)i, 1});
+            else leaves.push_back({t.off + ml, mr});
             P.nodes.push_back(s);
-            if (t.size > L.max_size) L.max_size = (int32_t)t.size;
+            if (t.size > kSmallCap) ++L.nbig;
+            else L.max_small = std::max<int32_t>(L.max_small, (int32_t)t.size);
         }
-        L.small = L.max_size <= kSmallCap;
         L.chunk_base = (int64_t)P.chunks.size();
         L.nchunks = 0;
-        if (!L.small) {
-            for (int32_t s = 0; s < L.nnodes; ++s) {
-                const SplitNode& sn = P.nodes[L.node_base + s];
-                const int32_t first = L.nchunks;
-                for (int64_t a = 0; a < sn.size; a += kChunk) {
-                    Chunk c;
-                    c.node = s;
-                    c.start = (int32_t)(sn.off + a);
-                    c.len = (int32_t)std::min<int64_t>(kChunk, sn.size - a);
-                    c.first = first;
-                    P.chunks.push_back(c);
-                    ++L.nchunks;
-                }
+        for (int32_t s = 0; s < L.nbig; ++s) {
+            const SplitNode& sn = P.nodes[L.node_base + s];
+            const int32_t first = L.nchunks;
+            for (int64_t a = 0; a < sn.size; a += kChunk) {
+                Chunk c;
+                c.node = s;
+                c.start = (int32_t)(sn.off + a);
+                c.len = (int32_t)std::min<int64_t>(kChunk, sn.size - a);
+                c.first = first;
+                P.chunks.push_back(c);
+                ++L.nchunks;
             }
         }
         P.max_nodes = std::max(P.max_nodes, L.nnodes);
-        if (!L.small) P.max_big_nodes = std::max(P.max_big_nodes, L.nnodes);
+        P.max_big_nodes = std::max(P.max_big_nodes, L.nbig);
         P.max_chunks = std::max(P.max_chunks, L.nchunks);
         P.levels.push_back(L);
         cur.swap(nxt);
@@ -94,6 +121,11 @@ void make_tree_plan(int64_t n, int g, TreePlan& P)
         P.max_leaf = std::max<int32_t>(P.max_leaf, (int32_t)l.second);
     }
     P.leaf_off.push_back((int32_t)n);
+}
+
+void make_tree_plan(int64_t n, int g, TreePlan& P)
+{
+    make_forest_plan(std::vector<int64_t>{n}, g, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -110,6 +142,15 @@ __global__ void init_perm_kernel(int64_t n, int T, int first_node, int32_t* perm
         pos_of[e] = i;
         node_of[e] = first_node;
     }
+}
+
+// Points of the root node s of level 0 start in node s (other points are in
+// roots that are already leaves and keep node -1).
+__global__ void init_root_nodes_kernel(int64_t n, const SplitNode* __restrict__ nodes, int32_t* node_of)
+{
+    const SplitNode nd = nodes[blockIdx.x];
+    int32_t* row = node_of + (int64_t)blockIdx.y * n;
+    for (int e = threadIdx.x; e < nd.size; e += blockDim.x) row[nd.off + e] = (int32_t)blockIdx.x;
 }
 
 // dirs[t][s][0..d_pad): direction of split node s of this level in tree t.
@@ -516,9 +557,12 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
 
     const int sms = num_sms();
     const int gcap = sms * 32;
-    init_perm_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, P.levels.empty() ? -1 : 0,
-                                                                          perm_a, pos_of, node_of);
+    init_perm_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, -1, perm_a, pos_of, node_of);
     note_launches(1);
+    if (!P.levels.empty()) {
+        init_root_nodes_kernel<<<dim3(P.levels[0].nnodes, T), 256, 0, st>>>(n, dp.nodes, node_of);
+        note_launches(1);
+    }
     int32_t* cur = perm_a;
     int32_t* nxt = perm_b;
     for (size_t lvl = 0; lvl < P.levels.size(); ++lvl) {
@@ -540,9 +584,9 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         }
         // leaves of this level keep their positions: start from a copy
         cudaMemcpyAsync(nxt, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);
-        if (L.small) {
+        if (L.nbig < S) {
             constexpr int NT = 512;
-            const size_t smem = sizeof(unsigned long long) * (size_t)L.max_size;
+            const size_t smem = sizeof(unsigned long long) * (size_t)L.max_small;
             static bool attr = false;
             if (!attr) {
                 cudaError_t e = cudaFuncSetAttribute(split_small_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -550,27 +594,30 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
                 if (e != cudaSuccess) return e;
                 attr = true;
             }
-            split_small_kernel<NT><<<dim3(S, T), NT, smem, st>>>(n, nodes, keys, cur, nxt, pos_of, node_of);
+            split_small_kernel<NT><<<dim3(S - L.nbig, T), NT, smem, st>>>(n, nodes + L.nbig, keys, cur, nxt, pos_of,
+                                                                         node_of);
             note_launches(1);
-        } else {
+        }
+        if (L.nbig > 0) {
             constexpr int NT = 256;
+            const int SB = L.nbig;
             const Chunk* chunks = dp.chunks + L.chunk_base;
             const int NC = L.nchunks;
-            big_init_kernel<<<(S * T + 255) / 256, 256, 0, st>>>(S, T, nodes, sel);
+            big_init_kernel<<<(SB * T + 255) / 256, 256, 0, st>>>(SB, T, nodes, sel);
             note_launches(1);
-            cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * (size_t)T * S * 256, st);
+            cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * (size_t)T * SB * 256, st);
             for (int shift = 56; shift >= 0; shift -= 8) {
-                big_hist_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, shift, S, chunks, keys, cur, sel, ghist);
+                big_hist_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, shift, SB, chunks, keys, cur, sel, ghist);
                 note_launches(1);
-                big_pick_kernel<<<dim3(S, T), 32, 0, st>>>(shift, S, sel, ghist);
+                big_pick_kernel<<<dim3(SB, T), 32, 0, st>>>(shift, SB, sel, ghist);
                 note_launches(1);
             }
-            big_count_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, S, NC, chunks, keys, cur, sel, cnt);
+            big_count_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, SB, NC, chunks, keys, cur, sel, cnt);
             note_launches(1);
-            big_base_kernel<<<(S * T + 127) / 128, 128, 0, st>>>(S, T, NC, chunks, cnt);
+            big_base_kernel<<<(SB * T + 127) / 128, 128, 0, st>>>(SB, T, NC, chunks, cnt);
             note_launches(1);
-            big_scatter_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, S, NC, chunks, nodes, keys, cur, sel, cnt,
-                                                               nxt, pos_of, node_of);
+            big_scatter_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, SB, NC, chunks, nodes, keys, cur, sel, cnt, nxt,
+                                                               pos_of, node_of);
             note_launches(1);
         }
         std::swap(cur, nxt);
