@@ -156,6 +156,13 @@ def run_batched(args):
     outs = [(torch.empty((X.shape[0], k), dtype=torch.int32, device=dev),
              torch.empty((X.shape[0], k), dtype=torch.float32, device=dev)) for X in Xs]
     stream = torch.cuda.current_stream(dev)
+    # tile shapes of the tensor-core leaf kernel from the autotuner, one per
+    # dimension (tuned on the largest set of that dimension)
+    tiles = {}
+    if prec != 0:
+        for dd in sorted(set(int(X.shape[1]) for X in Xs)):
+            big = max((X for X in Xs if X.shape[1] == dd), key=lambda X: X.shape[0])
+            tiles[dd] = knng.knng_autotune(big, k, T, g, args.seed, precision=prec, h=h)
 
     def batched():
         knng.knng_build_batched(Xs, k, T, g, R, args.seed, prec, 2, outs=outs, h=h)
@@ -195,6 +202,8 @@ def run_batched(args):
                      "ms_per_step": res["separate"]["ms_per_step"],
                      "launches_per_step": res["separate"]["launches_per_step"]},
         "speedup_vs_separate": res["separate"]["ms_per_step"] / res["batched"]["ms_per_step"],
+        "autotuned_tiles": {str(dd): {"stages": t[0], "rows_per_group": t[1], "leaf_ms": t[2]}
+                            for dd, t in tiles.items()},
         "clocks": res["batched"]["clocks"],
     }
     print(json.dumps(line), flush=True)

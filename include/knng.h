@@ -138,6 +138,21 @@ typedef struct knng_dataset {
 int knng_build_batched(knng_handle* h, int32_t nsets, const knng_dataset* sets, const knng_params* p,
                        void* stream);
 
+/* ---- tile autotuning (tensor-core leaf kernel) --------------------------- */
+/* Times the tensor-core leaf kernel (p->precision BF16 or FP8E4M3) on X with
+ * every valid tile choice -- pipeline stages and epilogue row-group height --
+ * and keeps the fastest in h for this problem shape (precision, padded row
+ * length, widest leaf).  Later builds and batched builds on h of the same
+ * shape use it; results do not depend on the choice, only speed.  Optional
+ * outputs (may be NULL): the chosen stages, rows per group and its mean time
+ * per leaf stage in ms.  Synchronises `stream`. */
+int knng_autotune(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                  const knng_params* p, int32_t* stages, int32_t* rows_per_group, float* best_ms,
+                  void* stream);
+/* Writes / reads the tile choices of h as a text file (one shape per line). */
+int knng_tune_save(knng_handle* h, const char* path);
+int knng_tune_load(knng_handle* h, const char* path);
+
 /* ---- stages ---------------------------------------------------------- */
 /* Random divisions (Sec. 3.1; split rule of the appendix after Lemma 1).
  * perm: device int32 [T][n].  Row t lists the point ids of tree t leaf by

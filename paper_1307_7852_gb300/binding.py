@@ -65,6 +65,9 @@ SIGNATURES = {
     "knng_set_stage_events": [_P, _P, _I32],
     "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
     "knng_sync": [_P, _P],
+    "knng_autotune": [_P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P, _P],
+    "knng_tune_save": [_P, ctypes.c_char_p],
+    "knng_tune_load": [_P, ctypes.c_char_p],
     "knng_build_batched": [_P, _I32, _P, ctypes.POINTER(knng_params), _P],
     "knng_propagate_noalloc": [_P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
 }
@@ -371,3 +374,24 @@ def knng_build_batched(Xs, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP
     h.check(lib().knng_build_batched(h.ptr, len(Xs), arr, ctypes.byref(p), _stream(dev, stream)),
             "knng_build_batched")
     return res
+
+
+def knng_autotune(X, k, T, leaf_size, seed, precision=PREC_BF16, rescore_mult=2, prop_rounds=0,
+                  stream=None, h: Handle = None):
+    """Tunes the tensor-core leaf tiles for X's shape on handle h; returns
+    (stages, rows_per_group, ms)."""
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    S, RG, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    h.check(lib().knng_autotune(h.ptr, xp, dt, n, d, ld, ctypes.byref(p), ctypes.byref(S), ctypes.byref(RG),
+                                ctypes.byref(ms), _stream(X.device, stream)), "knng_autotune")
+    return S.value, RG.value, ms.value
+
+
+def knng_tune_save(path: str, h: Handle):
+    h.check(lib().knng_tune_save(h.ptr, os.fsencode(path)), "knng_tune_save")
+
+
+def knng_tune_load(path: str, h: Handle):
+    h.check(lib().knng_tune_load(h.ptr, os.fsencode(path)), "knng_tune_load")

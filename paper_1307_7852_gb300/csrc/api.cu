@@ -64,6 +64,7 @@ struct knng_handle {
     std::vector<cudaEvent_t> stage_ev;
     int* dev_err = nullptr;  // set by kernels whose bounded waits gave up
     BatchCache batch;
+    std::map<TcKey, TcTile> tune;  // tile choices found by knng_autotune
     std::string err;
 };
 
@@ -213,7 +214,9 @@ int leaf_stage(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc
         if (!ar.base) return KNNG_OK;
         e = run_leaf_knn_f32(x, P, dp, T, perm, k, kp, ids, dists, st);
     } else if (prec == KNNG_PREC_BF16 || prec == KNNG_PREC_FP8E4M3) {
-        e = run_leaf_knn_tc(x, P, dp, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st);
+        const auto it = h->tune.find(tc_key(P, x.d, prec));
+        const TcTile* tile = it == h->tune.end() ? nullptr : &it->second;
+        e = run_leaf_knn_tc(x, P, dp, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st, tile);
     } else {
         return fail(h, KNNG_ERR_INVALID_ARG, "precision %d", prec);
     }
@@ -744,6 +747,109 @@ int knng_build_batched(knng_handle* h, int32_t nsets, const knng_dataset* sets, 
     if (e == cudaSuccess) e = cudaEventRecord(B.ev_out, B.cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B.ev_out, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    return KNNG_OK;
+}
+
+int knng_autotune(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                  const knng_params* p, int32_t* stages, int32_t* rows_per_group, float* best_ms, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    if ((r = check_params(h, p, n))) return r;
+    if (p->precision != KNNG_PREC_BF16 && p->precision != KNNG_PREC_FP8E4M3)
+        return fail(h, KNNG_ERR_UNSUPPORTED, "tiles are tuned for the tensor-core precisions only");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((r = ensure_plan(h, n, p->leaf_size, st))) return r;
+    const int T = p->T, k = p->k;
+    const size_t nk = (size_t)n * k;
+    const int kp = std::min(p->rescore_mult * k, 128);
+    // perm | lists | max(partition, leaf scratch)
+    Arena m;
+    m.take<int32_t>((size_t)T * n);
+    m.take<int32_t>((size_t)T * nk);
+    m.take<float>((size_t)T * nk);
+    const size_t fixed = m.off;
+    run_partition(x, h->plan, h->dplan, T, p->seed, nullptr, m, st);
+    const size_t pe = m.off;
+    m.off = fixed;
+    run_leaf_knn_tc(x, h->plan, h->dplan, T, nullptr, k, kp, p->precision, nullptr, nullptr, nullptr, m, st);
+    if ((r = ensure_ws(h, std::max(pe, m.off), st))) return r;
+    Arena a;
+    a.base = h->ws;
+    int32_t* perm = a.take<int32_t>((size_t)T * n);
+    int32_t* li = a.take<int32_t>((size_t)T * nk);
+    float* ldd = a.take<float>((size_t)T * nk);
+    cudaError_t e = run_partition(x, h->plan, h->dplan, T, p->seed, perm, a, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "partition");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    TcTile best_t{};
+    for (const TcTile& t : tc_candidates(h->plan, d, p->precision)) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            a.off = fixed;
+            cudaEventRecord(e0, st);
+            e = run_leaf_knn_tc(x, h->plan, h->dplan, T, perm, k, kp, p->precision, li, ldd, h->dev_err, a, st, &t);
+            cudaEventRecord(e1, st);
+            if (e != cudaSuccess) break;
+            cudaEventSynchronize(e1);
+            float one = 0.f;
+            cudaEventElapsedTime(&one, e0, e1);
+            if (rep > 0) ms += one;  // the first run warms up
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (ms < best) {
+            best = ms;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_t.S == 0) return fail(h, KNNG_ERR_INTERNAL, "no tile configuration ran");
+    h->tune[tc_key(h->plan, d, p->precision)] = best_t;
+    if (stages) *stages = best_t.S;
+    if (rows_per_group) *rows_per_group = best_t.RG;
+    if (best_ms) *best_ms = best / 3.f;
+    return knng_sync(h, stream);
+}
+
+int knng_tune_save(knng_handle* h, const char* path)
+{
+    if (!h || !path) return KNNG_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "w");
+    if (!f) return fail(h, KNNG_ERR_INVALID_ARG, "cannot write %s", path);
+    fprintf(f, "# knng tensor-core leaf tiles: precision row_bytes n_load stages rows_per_group\n");
+    for (const auto& kv : h->tune)
+        fprintf(f, "%d %d %d %d %d\n", kv.first.prec, kv.first.row_bytes, kv.first.n_load, kv.second.S, kv.second.RG);
+    fclose(f);
+    return KNNG_OK;
+}
+
+int knng_tune_load(knng_handle* h, const char* path)
+{
+    if (!h || !path) return KNNG_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "r");
+    if (!f) return fail(h, KNNG_ERR_INVALID_ARG, "cannot read %s", path);
+    char line[256];
+    int added = 0;
+    while (fgets(line, sizeof line, f)) {
+        if (line[0] == '#') continue;
+        TcKey key{};
+        TcTile t{};
+        if (sscanf(line, "%d %d %d %d %d", &key.prec, &key.row_bytes, &key.n_load, &t.S, &t.RG) == 5 && t.S >= 1 &&
+            t.S <= 4 && (t.RG == 32 || t.RG == 64 || t.RG == 128)) {
+            h->tune[key] = t;
+            ++added;
+        }
+    }
+    fclose(f);
     return KNNG_OK;
 }
 

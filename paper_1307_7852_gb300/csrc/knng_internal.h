@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -115,9 +116,30 @@ cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& d
                              const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
                              cudaStream_t st);
 
+// Tile choices of the tensor-core leaf kernel for one problem shape:
+// pipeline stages S and epilogue row-group height RG (32, 64 or 128).
+struct TcTile {
+    int S = 0;
+    int RG = 0;
+};
+// Shape key of the tensor-core leaf kernel: precision, padded row bytes and
+// the widest leaf (MMA N) -- the quantities its geometry depends on.
+struct TcKey {
+    int prec, row_bytes, n_load;
+    bool operator<(const TcKey& o) const
+    {
+        if (prec != o.prec) return prec < o.prec;
+        if (row_bytes != o.row_bytes) return row_bytes < o.row_bytes;
+        return n_load < o.n_load;
+    }
+};
+TcKey tc_key(const TreePlan& P, int d, int prec);
+// Candidate tiles for a shape (valid for its shared-memory budget).
+std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec);
+
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
                             int k, int kp, int prec, int32_t* ids, float* dists, int* err, Arena& ar,
-                            cudaStream_t st);
+                            cudaStream_t st, const TcTile* tile = nullptr);
 
 cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
                       int32_t* ids, float* dists, cudaStream_t st);

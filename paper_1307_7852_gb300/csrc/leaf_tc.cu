@@ -313,7 +313,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-static TcGeom tc_geometry(const TreePlan& P, int d, int prec)
+static TcGeom tc_geometry(const TreePlan& P, int d, int prec, const TcTile* tile)
 {
     TcGeom G{};
     const int elem = prec == 1 ? 2 : 1;
@@ -325,15 +325,42 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec)
     G.box_rows = 128;  // R_load is a multiple of 128
     G.nbox = G.R_load / G.box_rows;
     G.stage_bytes = G.R_load * 128;
-    G.S = std::max(1, std::min(std::min(G.nK, 4), (160 * 1024) / G.stage_bytes));
     G.ldD = ((G.N_load + 31) & ~31) + 1;
-    // rows per epilogue group: 128, 64 or 32 (a divisor of the 128-row block)
-    G.RG = 128;
-    while (G.RG > 32 && G.RG * G.ldD * 4 > 72 * 1024) G.RG >>= 1;
+    const int s_max = std::max(1, std::min(std::min(G.nK, 4), (160 * 1024) / G.stage_bytes));
+    if (tile && tile->S >= 1 && tile->RG >= 32) {
+        G.S = std::min(tile->S, s_max);
+        G.RG = tile->RG;
+    } else {
+        // default: deepest pipeline that fits; rows per epilogue group: 128,
+        // 64 or 32 (a divisor of the 128-row block) within 72 KB
+        G.S = s_max;
+        G.RG = 128;
+        while (G.RG > 32 && G.RG * G.ldD * 4 > 72 * 1024) G.RG >>= 1;
+    }
     G.pipe_bytes = std::max(G.S * G.stage_bytes, G.RG * G.ldD * 4);
     G.pipe_bytes = (G.pipe_bytes + 1023) & ~1023;
     G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + kTcWarps * (256 * 4 + kTcCand * 4) + (2 * G.S + 1) * 8 + 16;
     return G;
+}
+
+TcKey tc_key(const TreePlan& P, int d, int prec)
+{
+    const int elem = prec == 1 ? 2 : 1;
+    const int slice = 128 / elem;
+    return TcKey{prec, (d + slice - 1) / slice * 128, (P.max_leaf + 15) & ~15};
+}
+
+std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec)
+{
+    std::vector<TcTile> out;
+    const TcGeom base = tc_geometry(P, d, prec, nullptr);
+    const int s_max = std::max(1, std::min(std::min(base.nK, 4), (160 * 1024) / base.stage_bytes));
+    for (int S = 1; S <= s_max; ++S)
+        for (int RG = 32; RG <= 128; RG <<= 1) {
+            TcTile t{S, RG};
+            if (tc_geometry(P, d, prec, &t).smem <= 220 * 1024) out.push_back(t);
+        }
+    return out;
 }
 
 template <int PREC, int E, bool kF16>
@@ -365,7 +392,7 @@ static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const Tre
 
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
                             int k, int kp, int prec, int32_t* ids, float* dists, int* err, Arena& ar,
-                            cudaStream_t st)
+                            cudaStream_t st, const TcTile* tile)
 {
     const int elem = prec == 1 ? 2 : 1;
     const int slice = 128 / elem;
@@ -377,7 +404,7 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     uint8_t* qx = ar.take<uint8_t>((size_t)rows);
     if (!ar.base) return cudaSuccess;
     if (kp > kTcCand) kp = kTcCand;
-    const TcGeom G = tc_geometry(P, x.d, prec);
+    const TcGeom G = tc_geometry(P, x.d, prec, tile);
     if (G.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
 
     const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);

@@ -48,3 +48,26 @@ def test_batched_replay_sees_new_contents():
     ref = knng.knng_build(Xs[2], k, T, g, R, seed)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(got[2][0].cpu().numpy(), ref[0].cpu().numpy())
+
+
+def test_autotune_keeps_results_and_round_trips(tmp_path):
+    import paper_1307_7852_gb300 as knng
+    X = torch.from_numpy(synthetic.gist_like(6000, 96, centers=8, seed=9)).cuda()
+    h = knng.Handle(0)
+    k, T, g, R, seed = 10, 2, 128, 1, 4
+    before = knng.knng_build(X, k, T, g, R, seed, 1, h=h)
+    S, RG, ms = knng.knng_autotune(X, k, T, g, seed, precision=1, h=h)
+    assert 1 <= S <= 4 and RG in (32, 64, 128) and ms > 0
+    after = knng.knng_build(X, k, T, g, R, seed, 1, h=h)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(before[0].cpu().numpy(), after[0].cpu().numpy())
+    np.testing.assert_array_equal(before[1].cpu().numpy(), after[1].cpu().numpy())
+    path = str(tmp_path / "tiles.txt")
+    knng.knng_tune_save(path, h)
+    lines = [l.split() for l in open(path) if not l.startswith("#")]
+    assert [int(v) for v in lines[0][3:5]] == [S, RG]
+    h2 = knng.Handle(0)
+    knng.knng_tune_load(path, h2)
+    again = knng.knng_build(X, k, T, g, R, seed, 1, h=h2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(before[0].cpu().numpy(), again[0].cpu().numpy())
