@@ -1,0 +1,100 @@
+"""FP64 oracle of the learned partitioner's network and training loss.
+
+TEST INFRASTRUCTURE (see oracle/__init__.py): the plain NumPy statement of
+what the CUDA training kernels compute, used to check their gradients.
+
+The paper has no learned partitioner; this is the reading used by the
+library (listed in the design doc).  Network (FP32 weights on the GPU):
+
+    A = X W1^T + b1          (N x H)
+    Hh = GELU(A)             GELU(a) = a/2 (1 + erf(a / sqrt 2))
+    Z = Hh W2^T + b2         (N x C)
+
+Loss on a batch of B graph edges (i_b, j_b): rows 0..B-1 of X are the first
+endpoints, rows B..2B-1 the second ones (N = 2B).  With the batch mean mu_c
+and variance V_c of every output c over the N rows,
+
+    L_pair = sum_c  mean_b (Z[b,c] - Z[B+b,c])^2 / (V_c + eps)
+    S      = (Z - mu) / sqrt(V + eps),    K = S^T S / N
+    L_dec  = sum_{c != c'} K[c,c']^2
+    L      = L_pair + lam * L_dec
+
+Neighbours should fall on the same side of a median split: each output
+should vary little along graph edges relative to its spread (L_pair), and
+the outputs should carry different information (L_dec).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SQRT2 = math.sqrt(2.0)
+INV_SQRT_2PI = 1.0 / math.sqrt(2.0 * math.pi)
+
+
+def _erf(x):
+    return np.vectorize(math.erf, otypes=[np.float64])(x)
+
+
+def gelu(a):
+    return 0.5 * a * (1.0 + _erf(a / SQRT2))
+
+
+def gelu_grad(a):
+    return 0.5 * (1.0 + _erf(a / SQRT2)) + a * INV_SQRT_2PI * np.exp(-0.5 * a * a)
+
+
+def forward(X, W1, b1, W2, b2):
+    X = np.asarray(X, dtype=np.float64)
+    A = X @ np.asarray(W1, np.float64).T + np.asarray(b1, np.float64)
+    Hh = gelu(A)
+    Z = Hh @ np.asarray(W2, np.float64).T + np.asarray(b2, np.float64)
+    return A, Hh, Z
+
+
+def loss_from_z(Z, lam, eps):
+    """Loss and dL/dZ (both FP64) for the pair batch Z (2B x C)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    N, C = Z.shape
+    B = N // 2
+    mu = Z.mean(axis=0)
+    Zc = Z - mu
+    V = (Zc * Zc).mean(axis=0)
+    D = Z[:B] - Z[B:]
+    P = (D * D).mean(axis=0)
+    L_pair = float(np.sum(P / (V + eps)))
+    sig = np.sqrt(V + eps)
+    S = Zc / sig
+    K = S.T @ S / N
+    off = K - np.diag(np.diag(K))
+    L_dec = float(np.sum(off * off))
+    L = L_pair + lam * L_dec
+    # gradient
+    dZ = np.zeros_like(Z)
+    dP = 1.0 / (V + eps)                      # dL/dP_c
+    dV = -P / (V + eps) ** 2                  # dL/dV_c (pair term)
+    dZ[:B] += dP * (2.0 / B) * D
+    dZ[B:] -= dP * (2.0 / B) * D
+    dZ += dV * (2.0 / N) * Zc
+    G = 2.0 * off * lam                       # dL/dK (symmetric, zero diagonal)
+    dS = (2.0 / N) * S @ G                    # K = S^T S / N
+    # through S = (Z - mu) / sqrt(V + eps), per column
+    m1 = dS.mean(axis=0)
+    m2 = (dS * S).mean(axis=0)
+    dZ += (dS - m1 - S * m2) / sig
+    return L, dZ
+
+
+def loss_and_grads(X, W1, b1, W2, b2, lam=0.05, eps=1e-4):
+    """Loss and gradients with respect to (W1, b1, W2, b2), FP64."""
+    X = np.asarray(X, dtype=np.float64)
+    A, Hh, Z = forward(X, W1, b1, W2, b2)
+    L, dZ = loss_from_z(Z, lam, eps)
+    dW2 = dZ.T @ Hh
+    db2 = dZ.sum(axis=0)
+    dH = dZ @ np.asarray(W2, np.float64)
+    dA = dH * gelu_grad(A)
+    dW1 = dA.T @ X
+    db1 = dA.sum(axis=0)
+    return L, (dW1, db1, dW2, db2)
