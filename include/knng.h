@@ -60,7 +60,7 @@ extern "C" {
 #define KNNG_PREC_BF16 1
 #define KNNG_PREC_FP8E4M3 2
 
-#define KNNG_PART_RANDOM 0
+#define KNNG_PART_RANDOM 0  /* Philox random directions (the only value knng_build takes) */
 
 /* ---- parameters ------------------------------------------------------ */
 typedef struct knng_params {
@@ -184,6 +184,48 @@ int knng_merge(knng_handle* h, int64_t n, int32_t T, int32_t k, const int32_t* i
 int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                    int32_t k, int32_t rounds, const int32_t* ids_in, const float* dists_in,
                    int32_t* ids, float* dists, void* stream);
+
+/* ---- learned partitioner ----------------------------------------------- */
+/* The paper splits along random principal directions (Sec. 3.4) or random
+ * projections (appendix after Lemma 1).  As an alternative the library can
+ * split along learned features: a network z = W2 GELU(W1 x + b1) + b2 with
+ * z in R^C (C = 16 or 32), where level l < C of tree t splits every node at
+ * the median of feature pi_t(l) (pi_t a Philox permutation of the features,
+ * a function of (seed, t)); deeper levels use random directions.  The network
+ * is trained on edges of k-NN graphs built by the method itself, so that
+ * neighbours stay on the same side of those medians and fewer trees reach
+ * the same recall.  Parameters are FP32 (packed W1[H][d] | b1[H] | W2[C][H] |
+ * b2[C]); inference is BF16 on the tensor cores (d <= 128). */
+typedef struct knng_mlp knng_mlp;
+
+/* A network d_in -> hidden -> d_out on `device`, weights N(0, 1/fan_in)
+ * from `seed`, biases 0.  d_in 1..1024, hidden 16..256 (multiple of 16),
+ * d_out 16 or 32. */
+int knng_mlp_create(int32_t device, int32_t d_in, int32_t hidden, int32_t d_out, uint64_t seed, knng_mlp** out);
+int knng_mlp_destroy(knng_mlp* m);
+int knng_mlp_param_count(const knng_mlp* m, int64_t* count);
+/* Copies the packed parameters to / from HOST memory. */
+int knng_mlp_get_params(const knng_mlp* m, float* host);
+int knng_mlp_set_params(knng_mlp* m, const float* host);
+/* Loss and packed gradient (device, param_count floats) of one batch of B
+ * edges: Xpairs is device FP32 [2B][d_in], rows b and B+b the two endpoints
+ * of edge b.  *loss is written on the host; synchronises `stream`. */
+int knng_mlp_loss_grad(knng_mlp* m, const float* Xpairs, int32_t B, float* loss, float* grad, void* stream);
+/* `steps` Adam steps (lr, betas 0.9/0.999) on batches of batch_edges edges
+ * drawn (Philox, from `seed`) from the graph ids[n][k] over X (device).
+ * *last_loss (host, may be NULL) gets the loss of the last step. */
+int knng_mlp_train(knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld, const int32_t* ids,
+                   int32_t k, int32_t steps, int32_t batch_edges, float lr, uint64_t seed, float* last_loss,
+                   void* stream);
+/* Binary file with a header and the packed FP32 parameters. */
+int knng_mlp_save(const knng_mlp* m, const char* path);
+int knng_mlp_load(knng_mlp* m, const char* path);
+/* Features of every point: Z (device, FP32 [n][d_out]), BF16 inference. */
+int knng_mlp_forward(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                     float* Z, void* stream);
+/* knng_build with learned splits (the network's d_in must equal d). */
+int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                       const knng_params* p, int32_t* ids, float* dists, void* stream);
 
 /* ---- propagation without device allocation ---------------------------- */
 /* The paper has no counterpart: this entry point exists for callers that

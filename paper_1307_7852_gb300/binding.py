@@ -68,6 +68,18 @@ SIGNATURES = {
     "knng_autotune": [_P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P, _P],
     "knng_tune_save": [_P, ctypes.c_char_p],
     "knng_tune_load": [_P, ctypes.c_char_p],
+    "knng_mlp_create": [_I32, _I32, _I32, _I32, _U64, ctypes.POINTER(ctypes.c_void_p)],
+    "knng_mlp_destroy": [_P],
+    "knng_mlp_param_count": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "knng_mlp_get_params": [_P, _P],
+    "knng_mlp_set_params": [_P, _P],
+    "knng_mlp_loss_grad": [_P, _P, _I32, ctypes.POINTER(ctypes.c_float), _P, _P],
+    "knng_mlp_train": [_P, _P, _I32, _I64, _I32, _I64, _P, _I32, _I32, _I32, ctypes.c_float, _U64,
+                       ctypes.POINTER(ctypes.c_float), _P],
+    "knng_mlp_save": [_P, ctypes.c_char_p],
+    "knng_mlp_load": [_P, ctypes.c_char_p],
+    "knng_mlp_forward": [_P, _P, _P, _I32, _I64, _I32, _I64, _P, _P],
+    "knng_build_learned": [_P, _P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P],
     "knng_build_batched": [_P, _I32, _P, ctypes.POINTER(knng_params), _P],
     "knng_propagate_noalloc": [_P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
 }
@@ -395,3 +407,103 @@ def knng_tune_save(path: str, h: Handle):
 
 def knng_tune_load(path: str, h: Handle):
     h.check(lib().knng_tune_load(h.ptr, os.fsencode(path)), "knng_tune_load")
+
+
+class Mlp:
+    """The learned partitioner's split-feature network (knng_mlp)."""
+
+    def __init__(self, d_in, hidden=256, d_out=16, seed=0, device=0):
+        p = ctypes.c_void_p()
+        rc = lib().knng_mlp_create(int(device), int(d_in), int(hidden), int(d_out), int(seed), ctypes.byref(p))
+        if rc != KNNG_OK:
+            raise KnngError(rc, "knng_mlp_create: " + lib().knng_status_string(rc).decode())
+        self._p, self.d_in, self.hidden, self.d_out, self.device = p, d_in, hidden, d_out, device
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def _chk(self, rc, what):
+        if rc != KNNG_OK:
+            raise KnngError(rc, what + ": " + lib().knng_status_string(rc).decode())
+
+    def param_count(self) -> int:
+        c = ctypes.c_int64()
+        self._chk(lib().knng_mlp_param_count(self._p, ctypes.byref(c)), "knng_mlp_param_count")
+        return int(c.value)
+
+    def get_params(self):
+        """(W1, b1, W2, b2) as float32 numpy arrays."""
+        buf = np.empty(self.param_count(), dtype=np.float32)
+        self._chk(lib().knng_mlp_get_params(self._p, ctypes.c_void_p(buf.ctypes.data)), "knng_mlp_get_params")
+        H, d, C = self.hidden, self.d_in, self.d_out
+        o = 0
+        W1 = buf[o:o + H * d].reshape(H, d); o += H * d
+        b1 = buf[o:o + H]; o += H
+        W2 = buf[o:o + C * H].reshape(C, H); o += C * H
+        b2 = buf[o:o + C]
+        return W1, b1, W2, b2
+
+    def set_params(self, W1, b1, W2, b2):
+        buf = np.concatenate([np.ravel(W1), np.ravel(b1), np.ravel(W2), np.ravel(b2)]).astype(np.float32)
+        assert buf.size == self.param_count()
+        self._chk(lib().knng_mlp_set_params(self._p, ctypes.c_void_p(buf.ctypes.data)), "knng_mlp_set_params")
+
+    def loss_grad(self, Xpairs, stream=None):
+        """Loss and packed gradient of a batch (CUDA float32 [2B, d_in])."""
+        torch = _torch()
+        B = Xpairs.shape[0] // 2
+        g = torch.empty(self.param_count(), dtype=torch.float32, device=Xpairs.device)
+        loss = ctypes.c_float()
+        self._chk(lib().knng_mlp_loss_grad(self._p, _ptr(Xpairs), int(B), ctypes.byref(loss), _ptr(g),
+                                           _stream(Xpairs.device, stream)), "knng_mlp_loss_grad")
+        return float(loss.value), g
+
+    def train(self, X, ids, steps, batch_edges=4096, lr=1e-3, seed=0, stream=None) -> float:
+        xp, dt, n, d, ld = _xdesc(X)
+        k = ids.shape[1]
+        loss = ctypes.c_float()
+        self._chk(lib().knng_mlp_train(self._p, xp, dt, n, d, ld, _ptr(ids), int(k), int(steps), int(batch_edges),
+                                       float(lr), int(seed), ctypes.byref(loss), _stream(X.device, stream)),
+                  "knng_mlp_train")
+        return float(loss.value)
+
+    def save(self, path):
+        self._chk(lib().knng_mlp_save(self._p, os.fsencode(path)), "knng_mlp_save")
+
+    def load(self, path):
+        self._chk(lib().knng_mlp_load(self._p, os.fsencode(path)), "knng_mlp_load")
+
+    def close(self):
+        if getattr(self, "_p", None):
+            lib().knng_mlp_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def knng_mlp_forward(mlp: Mlp, X, Z=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    Z = _out((n, mlp.d_out), torch.float32, X.device, Z)
+    h.check(lib().knng_mlp_forward(h.ptr, mlp.ptr, xp, dt, n, d, ld, _ptr(Z), _stream(X.device, stream)),
+            "knng_mlp_forward")
+    return Z
+
+
+def knng_build_learned(mlp: Mlp, X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
+                       ids=None, dists=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    ids = _out((n, k), torch.int32, X.device, ids)
+    dists = _out((n, k), torch.float32, X.device, dists)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    h.check(lib().knng_build_learned(h.ptr, mlp.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
+                                     _stream(X.device, stream)), "knng_build_learned")
+    return ids, dists

@@ -241,7 +241,8 @@ int check_params(knng_handle* h, const knng_params* p, int64_t n)
 // leaf graphs, merge, propagation rounds.  Carves its buffers from ar; with
 // ar.base == nullptr it only measures them.
 int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc& x, const knng_params& p,
-                   int32_t* ids, float* dists, Arena& a, cudaStream_t st, bool events)
+                   int32_t* ids, float* dists, Arena& a, cudaStream_t st, bool events,
+                   const LearnedFeat* lf = nullptr)
 {
     const int64_t n = x.n;
     const int T = p.T, k = p.k, R = p.prop_rounds;
@@ -274,7 +275,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         if (rec) cudaEventRecord(h->stage_ev[i], st);
     };
     mark(0);
-    cudaError_t e = run_partition(x, P, dp, T, p.seed, perm, a, st);
+    cudaError_t e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf);
     if (e != cudaSuccess) return cuda_fail(h, e, "partition");
     mark(1);
     const size_t part_end = a.off;
@@ -851,6 +852,58 @@ int knng_tune_load(knng_handle* h, const char* path)
     }
     fclose(f);
     return KNNG_OK;
+}
+
+int knng_mlp_forward(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                     float* Z, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    MlpModel* M = mlp_model(m);
+    if (!M || !Z) return fail(h, KNNG_ERR_INVALID_ARG, "NULL network or output");
+    if (M->d != d) return fail(h, KNNG_ERR_INVALID_ARG, "network input %d != d %d", M->d, d);
+    if (d > 128) return fail(h, KNNG_ERR_UNSUPPORTED, "tensor-core inference supports d <= 128");
+    DeviceGuard dg(h->device);
+    const cudaError_t e = run_mlp_forward(*M, x, Z, h->dev_err, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "network inference");
+    return KNNG_OK;
+}
+
+int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                       const knng_params* p, int32_t* ids, float* dists, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    if (!p) return fail(h, KNNG_ERR_INVALID_ARG, "params is NULL");
+    knng_params q = *p;
+    q.partitioner = KNNG_PART_RANDOM;  // the random directions serve the levels past the features
+    if ((r = check_params(h, &q, n))) return r;
+    MlpModel* M = mlp_model(m);
+    if (!M || !ids || !dists) return fail(h, KNNG_ERR_INVALID_ARG, "NULL network or output");
+    if (M->d != d) return fail(h, KNNG_ERR_INVALID_ARG, "network input %d != d %d", M->d, d);
+    if (d > 128) return fail(h, KNNG_ERR_UNSUPPORTED, "tensor-core inference supports d <= 128");
+    if (q.T > 32) return fail(h, KNNG_ERR_INVALID_ARG, "T");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((r = ensure_plan(h, n, q.leaf_size, st))) return r;
+    LearnedFeat lf;
+    lf.C = M->C;
+    learned_feature_order(q.seed, q.T, M->C, lf);
+    Arena m0;
+    m0.take<float>((size_t)n * M->C);
+    if ((r = build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, m0, st, true, &lf))) return r;
+    if ((r = ensure_ws(h, m0.off, st))) return r;
+    Arena a;
+    a.base = h->ws;
+    float* Z = a.take<float>((size_t)n * M->C);
+    lf.Z = Z;
+    const bool rec = (int)h->stage_ev.size() >= 5 + q.prop_rounds;
+    if (rec) cudaEventRecord(h->stage_ev[4 + q.prop_rounds], st);  // start of inference
+    cudaError_t e = run_mlp_forward(*M, x, Z, h->dev_err, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "network inference");
+    return build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, a, st, true, &lf);
 }
 
 int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,

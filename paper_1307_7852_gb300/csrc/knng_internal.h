@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/knng.h"
+
 #include <algorithm>
 #include <map>
 #include <string>
@@ -108,9 +110,20 @@ struct XDesc {
     bool vec;
 };
 
+// Learned split features: Z[n][C] (FP32) and, per tree t, the feature used
+// at level l < C (feat[t][l], a permutation of 0..C-1).
+struct LearnedFeat {
+    const float* Z = nullptr;
+    int C = 0;
+    int feat[32][32] = {};
+};
+// Per-tree feature order from Philox (Fisher-Yates), a function of (seed, t).
+void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf);
+
 // ---- stages (each carves its scratch from the arena) -------------------
 cudaError_t run_partition(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
-                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st);
+                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st,
+                          const LearnedFeat* lf = nullptr);
 
 cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                              const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
@@ -163,6 +176,37 @@ struct BatchSet {
 };
 cudaError_t run_scatter_batch(int64_t ng, int k, const BatchSet* sets, int nsets, const int32_t* gi,
                               const float* gd, cudaStream_t st);
+
+// Split-feature network of the learned partitioner (parameters packed as
+// W1[H][d] | b1[H] | W2[C][H] | b2[C], FP32, on the device).
+struct MlpModel {
+    int device = 0;
+    int d = 0, H = 0, C = 0;
+    int64_t count = 0;       // packed parameters: W1 | b1 | W2 | b2
+    float* w = nullptr;      // device, packed
+    float* g = nullptr;      // gradient
+    float* am = nullptr;     // Adam moments
+    float* av = nullptr;
+    int64_t adam_t = 0;
+    // training buffers (grown on demand)
+    int cap_rows = 0;
+    float* Xb = nullptr;
+    float* A = nullptr;
+    float* Hh = nullptr;
+    float* Z = nullptr;
+    float* dZ = nullptr;
+    float* loss = nullptr;
+    // BF16 inference images (swizzled operand layouts), rebuilt when stale
+    void* img = nullptr;
+    bool img_stale = true;
+    float* W1() const { return w; }
+    float* b1() const { return w + (int64_t)H * d; }
+    float* W2() const { return b1() + H; }
+    float* b2() const { return W2() + (int64_t)C * H; }
+};
+MlpModel* mlp_model(knng_mlp* o);
+// z = W2 GELU(W1 x + b1) + b2 for every point, BF16 on the tensor cores.
+cudaError_t run_mlp_forward(MlpModel& M, const XDesc& x, float* Z, int* err, cudaStream_t st);
 
 int num_sms();
 

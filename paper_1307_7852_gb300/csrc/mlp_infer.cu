@@ -1,0 +1,235 @@
+// Learned partitioner: BF16 inference of the split-feature network on the
+// tensor cores (z = W2 GELU(W1 x + b1) + b2 for every point).
+//
+// Persistent CTAs of 4 warps.  The weights, packed once per update into the
+// 128-byte swizzled K-major layout, stay in shared memory.  Per tile of 128
+// points: the rows are converted to bfloat16 into a swizzled operand tile;
+// one thread issues tcgen05.mma for H = X W1^T into TMEM (FP32); the warps
+// read their TMEM lanes back, apply bias and GELU, and write bfloat16 H into
+// the second operand tile; a second MMA gives Z = H W2^T; bias added, Z
+// stored in FP32.  Waits on the MMA barriers are bounded.
+#include <cuda_bf16.h>
+
+#include "../../include/knng.h"
+#include "knng_common.cuh"
+#include "knng_internal.h"
+#include "tc_ptx.cuh"
+
+namespace knng {
+
+namespace {
+constexpr long long kWait = 2000000000LL;
+}
+
+// W [rows][K] FP32 -> swizzled bfloat16 image with Kpad columns (zeros past K).
+__global__ void pack_sw128_kernel(const float* __restrict__ W, int rows, int K, int Kpad, uint8_t* __restrict__ img)
+{
+    const int total = rows * Kpad;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int r = e / Kpad, k = e % Kpad;
+        const float v = k < K ? W[(int64_t)r * K + k] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(img + tc::sw128_bf16_offset(r, k, rows)) = __float2bfloat16_rn(v);
+    }
+}
+
+__device__ __forceinline__ float gelu_inf(float a)
+{
+    return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f));
+}
+
+template <bool kF16, int C>
+__global__ void __launch_bounds__(128, 1) mlp_infer_kernel(RowLoader<kF16> L, int64_t n, const uint8_t* __restrict__ img,
+                                                           int K1pad, int H, const float* __restrict__ b1,
+                                                           const float* __restrict__ b2, float* __restrict__ Z,
+                                                           int* err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int w1b = H * K1pad * 2, w2b = C * H * 2, a1b = 128 * K1pad * 2, a2b = 128 * H * 2;
+    uint8_t* W1s = base;
+    uint8_t* W2s = W1s + w1b;
+    uint8_t* A1 = W2s + ((w2b + 1023) & ~1023);
+    uint8_t* A2 = A1 + a1b;
+    float* sb1 = reinterpret_cast<float*>(A2 + a2b);
+    float* sb2 = sb1 + H;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sb2 + C + (C & 1));
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+    // weights and biases into shared memory
+    {
+        const int4* src = reinterpret_cast<const int4*>(img);
+        int4* dst = reinterpret_cast<int4*>(W1s);
+        for (int e = tid; e < w1b / 16; e += 128) dst[e] = src[e];
+        src = reinterpret_cast<const int4*>(img + w1b);
+        dst = reinterpret_cast<int4*>(W2s);
+        for (int e = tid; e < w2b / 16; e += 128) dst[e] = src[e];
+        for (int e = tid; e < H; e += 128) sb1[e] = b1[e];
+        for (int e = tid; e < C; e += 128) sb2[e] = b2[e];
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::fence_mbar_init();
+        abort_flag = 0;
+    }
+    if (w == 0) {
+        tc::tmem_alloc(tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const uint32_t id1 = tc::make_idesc(1u, 128, (uint32_t)H), id2 = tc::make_idesc(1u, 128, (uint32_t)C);
+    const int64_t ntiles = (n + 127) / 128;
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x, phase ^= 1u) {
+        const int64_t r0 = tile * 128;
+        // rows -> bfloat16 operand tile
+        const int c8n = K1pad / 8;
+        for (int idx = tid; idx < 128 * c8n; idx += 128) {
+            const int r = idx / c8n, c8 = idx % c8n, j = c8 * 8;
+            const int64_t row = r0 + r;
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
+            if (row < n && j < L.d) {
+                u = L.load4(row, j);
+                v = L.load4(row, j + 4);
+            }
+            __nv_bfloat162 q0 = __floats2bfloat162_rn(u.x, u.y), q1 = __floats2bfloat162_rn(u.z, u.w);
+            __nv_bfloat162 q2 = __floats2bfloat162_rn(v.x, v.y), q3 = __floats2bfloat162_rn(v.z, v.w);
+            uint4 pk;
+            pk.x = *reinterpret_cast<uint32_t*>(&q0);
+            pk.y = *reinterpret_cast<uint32_t*>(&q1);
+            pk.z = *reinterpret_cast<uint32_t*>(&q2);
+            pk.w = *reinterpret_cast<uint32_t*>(&q3);
+            *reinterpret_cast<uint4*>(A1 + tc::sw128_bf16_offset(r, j, 128)) = pk;
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(A1), sw = tc::smem_u32(W1s);
+            for (int s = 0; s < K1pad / 64; ++s)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_f16(tbase, tc::sw128_desc(sa + s * 128 * 128 + kk * 32),
+                                tc::sw128_desc(sw + s * H * 128 + kk * 32), id1, (s | kk) ? 1u : 0u);
+            tc::mma_commit(&bars[0]);
+        }
+        if (!tc::mbar_wait(&bars[0], phase, kWait)) { abort_flag = 1; atomicExch(err, 1); }
+        tc::fence_after_sync();
+        // bias + GELU -> bfloat16 second operand
+        {
+            const int row = 32 * w + lane;
+            for (int c0 = 0; c0 < H; c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 32; e += 8) {
+                    uint4 pk;
+                    uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float h0 = gelu_inf(__uint_as_float(r[e + 2 * q]) + sb1[c0 + e + 2 * q]);
+                        const float h1 = gelu_inf(__uint_as_float(r[e + 2 * q + 1]) + sb1[c0 + e + 2 * q + 1]);
+                        __nv_bfloat162 hb = __floats2bfloat162_rn(h0, h1);
+                        pw[q] = *reinterpret_cast<uint32_t*>(&hb);
+                    }
+                    *reinterpret_cast<uint4*>(A2 + tc::sw128_bf16_offset(row, c0 + e, 128)) = pk;
+                }
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0 && !abort_flag) {
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(A2), sw = tc::smem_u32(W2s);
+            for (int s = 0; s < H / 64; ++s)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_f16(tbase + 256, tc::sw128_desc(sa + s * 128 * 128 + kk * 32),
+                                tc::sw128_desc(sw + s * C * 128 + kk * 32), id2, (s | kk) ? 1u : 0u);
+            tc::mma_commit(&bars[1]);
+        }
+        __syncthreads();
+        if (!abort_flag) {
+            if (!tc::mbar_wait(&bars[1], phase, kWait)) { abort_flag = 1; atomicExch(err, 1); }
+        }
+        tc::fence_after_sync();
+        if (!abort_flag) {
+            const int64_t row = r0 + 32 * w + lane;
+            if (C == 16) {
+                uint32_t r[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * w) << 16) + 256u, r);
+                tc::tmem_ld_wait();
+                if (row < n)
+#pragma unroll
+                    for (int c = 0; c < 16; c += 4)
+                        *reinterpret_cast<float4*>(Z + row * C + c) =
+                            make_float4(__uint_as_float(r[c]) + sb2[c], __uint_as_float(r[c + 1]) + sb2[c + 1],
+                                        __uint_as_float(r[c + 2]) + sb2[c + 2], __uint_as_float(r[c + 3]) + sb2[c + 3]);
+            } else {
+                uint32_t r[32];
+                tc::tmem_ld32(tbase + ((uint32_t)(32 * w) << 16) + 256u, r);
+                tc::tmem_ld_wait();
+                if (row < n)
+#pragma unroll
+                    for (int c = 0; c < 32; c += 4)
+                        *reinterpret_cast<float4*>(Z + row * C + c) =
+                            make_float4(__uint_as_float(r[c]) + sb2[c], __uint_as_float(r[c + 1]) + sb2[c + 1],
+                                        __uint_as_float(r[c + 2]) + sb2[c + 2], __uint_as_float(r[c + 3]) + sb2[c + 3]);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+cudaError_t run_mlp_forward(MlpModel& M, const XDesc& x, float* Z, int* err, cudaStream_t st)
+{
+    if (x.d != M.d || M.d > 128 || M.H > 256 || (M.C != 16 && M.C != 32)) return cudaErrorInvalidValue;
+    const int K1pad = (M.d + 63) / 64 * 64;
+    const size_t w1b = (size_t)M.H * K1pad * 2, w2b = (size_t)M.C * M.H * 2;
+    if (!M.img) {
+        if (cudaMalloc(&M.img, w1b + w2b) != cudaSuccess) return cudaErrorMemoryAllocation;
+        M.img_stale = true;
+    }
+    if (M.img_stale) {
+        uint8_t* img = static_cast<uint8_t*>(M.img);
+        pack_sw128_kernel<<<64, 256, 0, st>>>(M.W1(), M.H, M.d, K1pad, img);
+        pack_sw128_kernel<<<16, 256, 0, st>>>(M.W2(), M.C, M.H, M.H, img + w1b);
+        note_launches(2);
+        M.img_stale = false;
+    }
+    const size_t smem = 1024 + w1b + ((w2b + 1023) & ~(size_t)1023) + (size_t)128 * K1pad * 2 + (size_t)128 * M.H * 2 +
+                        sizeof(float) * (M.H + M.C + 2) + 64;
+    const int64_t tiles = (x.n + 127) / 128;
+    const int grid = (int)std::min<int64_t>(tiles, num_sms());
+    cudaError_t e;
+#define KNNG_MLP_LAUNCH(F16, CC)                                                                                     \
+    {                                                                                                                \
+        auto kern = mlp_infer_kernel<F16, CC>;                                                                       \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+        if (e != cudaSuccess) return e;                                                                              \
+        RowLoader<F16> rl{x.X, x.ld, x.d, x.vec};                                                                    \
+        kern<<<grid, 128, smem, st>>>(rl, x.n, static_cast<const uint8_t*>(M.img), K1pad, M.H, M.b1(), M.b2(), Z, err); \
+    }
+    if (x.dtype == 1) {
+        if (M.C == 16) KNNG_MLP_LAUNCH(true, 16) else KNNG_MLP_LAUNCH(true, 32)
+    } else {
+        if (M.C == 16) KNNG_MLP_LAUNCH(false, 16) else KNNG_MLP_LAUNCH(false, 32)
+    }
+#undef KNNG_MLP_LAUNCH
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace knng

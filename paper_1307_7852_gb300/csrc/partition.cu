@@ -176,6 +176,40 @@ __global__ void gen_dirs_kernel(float* dirs, int T, int S, int d, int d_pad,
     }
 }
 
+// Learned splits: the key of a point at this level is its feature
+// feat[t] (an output of the split-feature network).
+struct FeatOfTree {
+    int f[32];
+};
+__global__ void project_feature_kernel(int64_t n, int T, const float* __restrict__ Z, int C, FeatOfTree ft,
+                                       const int32_t* __restrict__ node_of, const int32_t* __restrict__ pos_of,
+                                       uint32_t* __restrict__ keys)
+{
+    const int64_t total = (int64_t)T * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (node_of[e] < 0) continue;
+        const int t = (int)(e / n);
+        const int64_t i = e - (int64_t)t * n;
+        keys[(int64_t)t * n + pos_of[e]] = ord_key(Z[i * C + ft.f[t]]);
+    }
+}
+
+void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf)
+{
+    const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+    for (int t = 0; t < T && t < 32; ++t) {
+        for (int c = 0; c < C; ++c) lf.feat[t][c] = c;
+        for (int i = C - 1; i > 0; --i) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0x4C524E44u, (uint32_t)i, 0u), key);
+            const int j = (int)(w.x % (uint32_t)(i + 1));
+            const int tmp = lf.feat[t][i];
+            lf.feat[t][i] = lf.feat[t][j];
+            lf.feat[t][j] = tmp;
+        }
+    }
+}
+
 // One warp per point; up to 8 trees per pass over the row.  The projection
 // order is the canonical one: lane l, j = 128c + 4l + e, fmaf, then the
 // pairwise rounds 16..1.
@@ -538,7 +572,7 @@ static inline int grid_for(int64_t work, int per_block, int cap)
 }
 
 cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
-                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st)
+                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st, const LearnedFeat* lf)
 {
     const int64_t n = x.n;
     const int d_pad = (x.d + 3) & ~3;
@@ -569,17 +603,24 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         const LevelPlan& L = P.levels[lvl];
         const SplitNode* nodes = dp.nodes + L.node_base;
         const int S = L.nnodes;
-        gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(
-            dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed);
-            note_launches(1);
-        const int pgrid = grid_for(n * 32, 256, sms * 16);
-        if (x.dtype == 1) {
-            RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
-            project_kernel<true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
+        if (lf && lf->Z && (int)lvl < lf->C) {
+            FeatOfTree ft{};
+            for (int t = 0; t < T && t < 32; ++t) ft.f[t] = lf->feat[t][lvl];
+            project_feature_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, lf->Z, lf->C, ft, node_of,
+                                                                                      pos_of, keys);
             note_launches(1);
         } else {
-            RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
-            project_kernel<false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
+            gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(
+                dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed);
+            note_launches(1);
+            const int pgrid = grid_for(n * 32, 256, sms * 16);
+            if (x.dtype == 1) {
+                RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
+                project_kernel<true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
+            } else {
+                RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
+                project_kernel<false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
+            }
             note_launches(1);
         }
         // leaves of this level keep their positions: start from a copy

@@ -169,3 +169,33 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
 
 }  // namespace tc
 }  // namespace knng
+
+namespace knng {
+namespace tc {
+// 16 consecutive FP32 columns of the warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+// Makes generic-proxy shared-memory writes visible to the tensor core.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Byte offset of element (row, k) of a K-major bfloat16 operand in the
+// 128-byte swizzled layout: K in slices of 64 elements, each slice a block
+// of rows x 128 bytes, 16-byte chunk index XORed with (row mod 8).
+__host__ __device__ __forceinline__ uint32_t sw128_bf16_offset(int row, int k, int rows)
+{
+    const int slice = k >> 6, kk = k & 63;
+    const int chunk = kk >> 3, within = kk & 7;
+    return (uint32_t)(slice * rows * 128 + row * 128 + ((chunk ^ (row & 7)) << 4) + within * 2);
+}
+}  // namespace tc
+}  // namespace knng
