@@ -210,6 +210,88 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------------- learned splits
+def run_learned(args):
+    """10M x 96 FP16 points (4,096-centre normalised mixture, std 0.05), k=20,
+    leaf size 256, 1 round.  The split-feature network (96 -> 256 -> 16) is
+    trained on the k-NN graph the method builds for a 1M-point subsample;
+    then learned splits with T=4 are timed against random directions with T=8
+    (and T=4), recall against exact brute force on a sample."""
+    import torch
+    import paper_1307_7852_gb300 as knng
+    from paper_1307_7852_gb300 import synthetic
+    n = args.learned_n
+    X = synthetic.sphere_f16(n, 96, centers=4096, std=0.05, seed=args.data_seed)
+    dev = torch.device("cuda", 0)
+    Xd = torch.from_numpy(X).to(dev)
+    k, g, R = 20, 256, 1
+    prec = PRECISIONS[args.precision]
+    h = knng.Handle(0)
+    stream = torch.cuda.current_stream(dev)
+    # training graph: random directions, T=8, on a 1M subsample
+    nsub = min(n, 1_000_000)
+    sub = Xd[:nsub]
+    t0 = time.perf_counter()
+    gi, _ = knng.knng_build(sub, k, 8, g, 1, args.seed + 7, prec, 2, h=h)
+    net = knng.Mlp(96, 256, 16, seed=args.seed)
+    loss0 = net.train(sub, gi, 1, batch_edges=4096, lr=2e-3, seed=1)
+    loss = net.train(sub, gi, args.train_steps, batch_edges=4096, lr=2e-3, seed=2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    ids = torch.empty((n, k), dtype=torch.int32, device=dev)
+    dists = torch.empty((n, k), dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            a.record(stream)
+            for _ in range(args.steps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps, clk.summary()
+
+    q = synthetic.sample_ids(n, args.recall_sample, args.seed + 1)
+    qd = torch.from_numpy(q).to(dev)
+    ei, _ = knng.knng_exact_knn(Xd, qd, k, h=h)
+    e_ids = ei.cpu().numpy()
+
+    def recall():
+        got = ids[qd.long()].cpu().numpy()
+        return float(np.mean([len(set(got[r]) & set(e_ids[r])) / k for r in range(len(q))]))
+
+    res = {}
+    l0 = knng.knng_launch_counter()
+    ms, clk = timed(lambda: knng.knng_build_learned(net, Xd, k, 4, g, R, args.seed, prec, 2, ids=ids, dists=dists,
+                                                    h=h))
+    launches = (knng.knng_launch_counter() - l0) // (args.steps + args.warmup)
+    res["learned_T4"] = {"ms_per_step": ms, "recall": recall()}
+    for T in (8, 4):
+        ms_r, _ = timed(lambda: knng.knng_build(Xd, k, T, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h))
+        res[f"random_T{T}"] = {"ms_per_step": ms_r, "recall": recall()}
+    for v in res.values():
+        v["points_per_s"] = n / (v["ms_per_step"] / 1e3)
+    line = {
+        "metric": "points/sec to build the k-NN graph with learned splits (T=4) vs random (T=8)",
+        "value": res["learned_T4"]["points_per_s"], "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["learned_T4"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[args.precision], "data": "synthetic",
+        "config": {"workload": "learned10m", "n": n, "d": 96, "input": "f16", "k": k, "leaf_size": g, "rounds": R,
+                   "precision": args.precision, "network": "96-256-16 GELU, FP32 weights, BF16 inference",
+                   "train": {"subsample": nsub, "graph": "random T=8 R=1", "steps": args.train_steps,
+                             "batch_edges": 4096, "loss_first": loss0, "loss_last": loss, "seconds": train_s}},
+        "gpu_launches": int(launches * args.steps),
+        "results": res, "recall_sample": int(len(q)), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args, w, rank):
     if rank != 0:
@@ -249,7 +331,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched256"], default="sift1m")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched256", "learned10m"], default="sift1m")
+    ap.add_argument("--learned-n", type=int, default=10_000_000)
+    ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--batch-sets", type=int, default=256)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16")
     ap.add_argument("--seed", type=int, default=12345)
@@ -263,12 +347,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed builds only (for profiler runs)")
     args = ap.parse_args()
-    if args.workload == "batched256":
+    if args.workload in ("batched256", "learned10m"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the whole method "
                               "on the sift1m workload only"}))
             return 0
-        return run_batched(args)
+        return run_batched(args) if args.workload == "batched256" else run_learned(args)
     w = WORKLOADS[args.workload]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -188,10 +188,13 @@ int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int3
 /* ---- learned partitioner ----------------------------------------------- */
 /* The paper splits along random principal directions (Sec. 3.4) or random
  * projections (appendix after Lemma 1).  As an alternative the library can
- * split along learned features: a network z = W2 GELU(W1 x + b1) + b2 with
- * z in R^C (C = 16 or 32), where level l < C of tree t splits every node at
- * the median of feature pi_t(l) (pi_t a Philox permutation of the features,
- * a function of (seed, t)); deeper levels use random directions.  The network
+ * split along learned features: a network z = tanh(W2 GELU(W1 x + b1) + b2)
+ * with z in (-1, 1)^C (C = 16 or 32), where level l < C of tree t splits
+ * every node at the median of feature pi_t(l) (pi_t a Philox permutation of
+ * the features, a function of (seed, t)) -- unless that feature has become
+ * flat inside the node (range within the node below 2% of its range over all
+ * points), in which case, as on deeper levels, the node splits along its
+ * random direction.  The network
  * is trained on edges of k-NN graphs built by the method itself, so that
  * neighbours stay on the same side of those medians and fewer trees reach
  * the same recall.  Parameters are FP32 (packed W1[H][d] | b1[H] | W2[C][H] |

@@ -8,7 +8,11 @@ library (listed in the design doc).  Network (FP32 weights on the GPU):
 
     A = X W1^T + b1          (N x H)
     Hh = GELU(A)             GELU(a) = a/2 (1 + erf(a / sqrt 2))
-    Z = Hh W2^T + b2         (N x C)
+    Z = tanh(Hh W2^T + b2)   (N x C)
+
+The outputs are bounded so that no output can lower the loss by inflating
+its spread with a few outliers (tanh is monotone, so splits at a median are
+unaffected by it).
 
 Loss on a batch of B graph edges (i_b, j_b): rows 0..B-1 of X are the first
 endpoints, rows B..2B-1 the second ones (N = 2B).  With the batch mean mu_c
@@ -17,11 +21,14 @@ and variance V_c of every output c over the N rows,
     L_pair = sum_c  mean_b (Z[b,c] - Z[B+b,c])^2 / (V_c + eps)
     S      = (Z - mu) / sqrt(V + eps),    K = S^T S / N
     L_dec  = sum_{c != c'} K[c,c']^2
-    L      = L_pair + lam * L_dec
+    L_spr  = sum_c (1 - V_c)^2
+    L      = L_pair + lam * L_dec + mu_s * L_spr
 
 Neighbours should fall on the same side of a median split: each output
-should vary little along graph edges relative to its spread (L_pair), and
-the outputs should carry different information (L_dec).
+should vary little along graph edges relative to its spread (L_pair), the
+outputs should carry different information (L_dec), and no output may
+collapse to a constant (L_spr: with outputs in (-1, 1) the spread is largest
+for balanced +-1 values).
 """
 from __future__ import annotations
 
@@ -49,11 +56,11 @@ def forward(X, W1, b1, W2, b2):
     X = np.asarray(X, dtype=np.float64)
     A = X @ np.asarray(W1, np.float64).T + np.asarray(b1, np.float64)
     Hh = gelu(A)
-    Z = Hh @ np.asarray(W2, np.float64).T + np.asarray(b2, np.float64)
+    Z = np.tanh(Hh @ np.asarray(W2, np.float64).T + np.asarray(b2, np.float64))
     return A, Hh, Z
 
 
-def loss_from_z(Z, lam, eps):
+def loss_from_z(Z, lam, eps, mu_s=1.0):
     """Loss and dL/dZ (both FP64) for the pair batch Z (2B x C)."""
     Z = np.asarray(Z, dtype=np.float64)
     N, C = Z.shape
@@ -69,11 +76,12 @@ def loss_from_z(Z, lam, eps):
     K = S.T @ S / N
     off = K - np.diag(np.diag(K))
     L_dec = float(np.sum(off * off))
-    L = L_pair + lam * L_dec
+    L_spr = float(np.sum((1.0 - V) ** 2))
+    L = L_pair + lam * L_dec + mu_s * L_spr
     # gradient
     dZ = np.zeros_like(Z)
     dP = 1.0 / (V + eps)                      # dL/dP_c
-    dV = -P / (V + eps) ** 2                  # dL/dV_c (pair term)
+    dV = -P / (V + eps) ** 2 - 2.0 * mu_s * (1.0 - V)   # dL/dV_c (pair and spread terms)
     dZ[:B] += dP * (2.0 / B) * D
     dZ[B:] -= dP * (2.0 / B) * D
     dZ += dV * (2.0 / N) * Zc
@@ -86,11 +94,12 @@ def loss_from_z(Z, lam, eps):
     return L, dZ
 
 
-def loss_and_grads(X, W1, b1, W2, b2, lam=0.05, eps=1e-4):
+def loss_and_grads(X, W1, b1, W2, b2, lam=0.05, eps=1e-4, mu_s=1.0):
     """Loss and gradients with respect to (W1, b1, W2, b2), FP64."""
     X = np.asarray(X, dtype=np.float64)
     A, Hh, Z = forward(X, W1, b1, W2, b2)
-    L, dZ = loss_from_z(Z, lam, eps)
+    L, dZ = loss_from_z(Z, lam, eps, mu_s)
+    dZ = dZ * (1.0 - Z * Z)   # through the output tanh
     dW2 = dZ.T @ Hh
     db2 = dZ.sum(axis=0)
     dH = dZ @ np.asarray(W2, np.float64)

@@ -262,7 +262,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
     const size_t fixed = a.off;
     int r;
     if (!a.base) {
-        run_partition(x, P, dp, T, p.seed, nullptr, a, st);
+        run_partition(x, P, dp, T, p.seed, nullptr, a, st, lf);
         const size_t part_end = a.off;
         a.off = fixed;
         if ((r = leaf_stage(h, P, dp, x, T, nullptr, k, p.precision, p.rescore_mult, nullptr, nullptr, a, st)))
@@ -893,15 +893,21 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     learned_feature_order(q.seed, q.T, M->C, lf);
     Arena m0;
     m0.take<float>((size_t)n * M->C);
+    m0.take<uint32_t>(2 * (size_t)M->C);
+    m0.take<float>((size_t)M->C);
     if ((r = build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, m0, st, true, &lf))) return r;
     if ((r = ensure_ws(h, m0.off, st))) return r;
     Arena a;
     a.base = h->ws;
     float* Z = a.take<float>((size_t)n * M->C);
+    uint32_t* mm = a.take<uint32_t>(2 * (size_t)M->C);
+    float* frange = a.take<float>((size_t)M->C);
     lf.Z = Z;
+    lf.frange = frange;
     const bool rec = (int)h->stage_ev.size() >= 5 + q.prop_rounds;
     if (rec) cudaEventRecord(h->stage_ev[4 + q.prop_rounds], st);  // start of inference
     cudaError_t e = run_mlp_forward(*M, x, Z, h->dev_err, st);
+    if (e == cudaSuccess) e = run_feature_range(Z, n, M->C, mm, frange, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "network inference");
     return build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, a, st, true, &lf);
 }

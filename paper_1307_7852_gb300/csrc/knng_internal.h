@@ -112,11 +112,18 @@ struct XDesc {
 
 // Learned split features: Z[n][C] (FP32) and, per tree t, the feature used
 // at level l < C (feat[t][l], a permutation of 0..C-1).
+// A node splits along its learned feature only while that feature still
+// varies inside the node: range within the node > tau x range over all
+// points; otherwise (a feature that has saturated into a constant there) it
+// splits along its random direction.
 struct LearnedFeat {
     const float* Z = nullptr;
     int C = 0;
     int feat[32][32] = {};
+    float tau = 0.02f;
+    const float* frange = nullptr;  // device [C]: max - min of each feature over all points
 };
+cudaError_t run_feature_range(const float* Z, int64_t n, int C, uint32_t* scratch2C, float* frange, cudaStream_t st);
 // Per-tree feature order from Philox (Fisher-Yates), a function of (seed, t).
 void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf);
 

@@ -2,13 +2,16 @@
 //
 // The paper splits along random principal directions (Sec. 3.4) or random
 // projections (appendix after Lemma 1); this library can also split along
-// learned features: a network x -> z in R^C (d -> H -> C, GELU), where level
+// learned features: a network x -> z in (-1, 1)^C (d -> H -> C, GELU, output
+// tanh), where level
 // l of tree t splits every node at the median of feature pi_t(l).  The
 // network is trained on edges (i, j) of k-NN graphs built by the method
 // itself, to keep neighbours on the same side of those medians:
 //
 //   L = sum_c mean_b (z_c(i_b) - z_c(j_b))^2 / (V_c + eps)
-//       + lam * sum_{c != c'} corr(z_c, z_c')^2        (batch statistics)
+//       + lam * sum_{c != c'} corr(z_c, z_c')^2 + mu * sum_c (1 - V_c)^2
+// (batch statistics; the last term stops an output from collapsing to a
+// constant, which would zero the first two)
 //
 // All training arithmetic is FP32 in the kernels below: batch sampling
 // (Philox), forward and backward GEMMs (tiled SIMT), the loss and its
@@ -29,7 +32,7 @@ namespace knng {
 // Tiled FP32 GEMM: C[M][N] (+)= sum_k A(m, k) B(k, n) with A(m, k) = TA ?
 // A[k*lda + m] : A[m*lda + k] and B(k, n) = TB ? B[n*ldb + k] : B[k*ldb + n].
 // Epilogue: EPI 0 plain store, 1 = + bias[n], store pre-activation to aux and
-// GELU to C, 2 = + bias[n].
+// GELU to C, 2 = + bias[n], 3 = tanh(. + bias[n]).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float gelu_f(float a)
 {
@@ -90,6 +93,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
                 v = gelu_f(v);
             } else if (EPI == 2) {
                 v += bias[n];
+            } else if (EPI == 3) {
+                v = tanhf(v + bias[n]);
             }
             C[(int64_t)m * ldc + n] = v;
         }
@@ -141,7 +146,7 @@ __global__ void sample_batch_kernel(RowLoader<kF16> L, int64_t n, const int32_t*
 constexpr int kLossThreads = 1024;
 
 __global__ void __launch_bounds__(kLossThreads) loss_kernel(const float* __restrict__ Z, int N, int C, float lam,
-                                                            float eps, float* __restrict__ dZ,
+                                                            float eps, float mus, float* __restrict__ dZ,
                                                             float* __restrict__ loss)
 {
     extern __shared__ float sh[];
@@ -206,7 +211,9 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const float* __restr
         for (int a = 0; a < C; ++a)
             for (int bb = 0; bb < C; ++bb)
                 if (a != bb) Ld += Kc[a * C + bb] * Kc[a * C + bb];
-        *loss = L + lam * Ld;
+        float Ls = 0.f;
+        for (int a = 0; a < C; ++a) Ls += (1.f - var[a]) * (1.f - var[a]);
+        *loss = L + lam * Ld + mus * Ls;
     }
     // dS = (2/N) S G with G = 2 lam offdiag(K); then the column means
     float d1 = 0.f, d2 = 0.f;
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const float* __restr
         const float ve = var[c] + eps;
         const float sig = sqrtf(ve);
         const float zc = Z[(int64_t)r * C + c] - mu[c];
-        float g = -P[c] / (ve * ve) * (2.f / N) * zc;
+        float g = (-P[c] / (ve * ve) - 2.f * mus * (1.f - var[c])) * (2.f / N) * zc;
         const int rb = r < B ? r : r - B;
         const float dd = Z[(int64_t)rb * C + c] - Z[(int64_t)(rb + B) * C + c];
         g += (r < B ? 1.f : -1.f) * (1.f / ve) * (2.f / B) * dd;
@@ -246,6 +253,13 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const float* __restr
         g += (ds - m1[c] - sc * m2[c]) / sig;
         dZ[(int64_t)r * C + c] = g;
     }
+}
+
+// through the output tanh: dZpre = dZ (1 - Z^2)
+__global__ void tanh_back_kernel(int64_t count, const float* __restrict__ Z, float* __restrict__ dZ)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        dZ[e] *= 1.f - Z[e] * Z[e];
 }
 
 // dA = dH * GELU'(A)
@@ -282,7 +296,7 @@ __global__ void adam_kernel(int count, float* __restrict__ w, const float* __res
 // ---------------------------------------------------------------------------
 // Model object
 // ---------------------------------------------------------------------------
-constexpr float kLam = 0.05f, kEps = 1e-4f;
+constexpr float kLam = 0.05f, kEps = 1e-4f, kSpread = 1.0f;
 
 static int ensure_rows(MlpModel* M, int rows)
 {
@@ -311,10 +325,11 @@ static cudaError_t loss_grad(MlpModel* M, const float* Xb, int B, cudaStream_t s
 {
     const int N = 2 * B, d = M->d, H = M->H, C = M->C;
     gemm<false, true, 1>(N, H, d, Xb, d, M->W1(), d, M->Hh, H, M->b1(), M->A, st);
-    gemm<false, true, 2>(N, C, H, M->Hh, H, M->W2(), H, M->Z, C, M->b2(), nullptr, st);
+    gemm<false, true, 3>(N, C, H, M->Hh, H, M->W2(), H, M->Z, C, M->b2(), nullptr, st);
     const size_t lsm = sizeof(float) * (6 * C + C * C + kLossThreads);
-    loss_kernel<<<1, kLossThreads, lsm, st>>>(M->Z, N, C, kLam, kEps, M->dZ, M->loss);
-    note_launches(1);
+    loss_kernel<<<1, kLossThreads, lsm, st>>>(M->Z, N, C, kLam, kEps, kSpread, M->dZ, M->loss);
+    tanh_back_kernel<<<(N * C + 255) / 256, 256, 0, st>>>((int64_t)N * C, M->Z, M->dZ);
+    note_launches(2);
     float* gW1 = M->g;
     float* gb1 = gW1 + (int64_t)H * d;
     float* gW2 = gb1 + H;

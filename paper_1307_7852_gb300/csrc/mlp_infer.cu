@@ -1,5 +1,5 @@
 // Learned partitioner: BF16 inference of the split-feature network on the
-// tensor cores (z = W2 GELU(W1 x + b1) + b2 for every point).
+// tensor cores (z = tanh(W2 GELU(W1 x + b1) + b2) for every point).
 //
 // Persistent CTAs of 4 warps.  The weights, packed once per update into the
 // 128-byte swizzled K-major layout, stay in shared memory.  Per tile of 128
@@ -7,7 +7,7 @@
 // one thread issues tcgen05.mma for H = X W1^T into TMEM (FP32); the warps
 // read their TMEM lanes back, apply bias and GELU, and write bfloat16 H into
 // the second operand tile; a second MMA gives Z = H W2^T; bias added, Z
-// stored in FP32.  Waits on the MMA barriers are bounded.
+// tanh applied, stored in FP32.  Waits on the MMA barriers are bounded.
 #include <cuda_bf16.h>
 
 #include "../../include/knng.h"
@@ -171,8 +171,8 @@ __global__ void __launch_bounds__(128, 1) mlp_infer_kernel(RowLoader<kF16> L, in
 #pragma unroll
                     for (int c = 0; c < 16; c += 4)
                         *reinterpret_cast<float4*>(Z + row * C + c) =
-                            make_float4(__uint_as_float(r[c]) + sb2[c], __uint_as_float(r[c + 1]) + sb2[c + 1],
-                                        __uint_as_float(r[c + 2]) + sb2[c + 2], __uint_as_float(r[c + 3]) + sb2[c + 3]);
+                            make_float4(tanhf(__uint_as_float(r[c]) + sb2[c]), tanhf(__uint_as_float(r[c + 1]) + sb2[c + 1]),
+                                        tanhf(__uint_as_float(r[c + 2]) + sb2[c + 2]), tanhf(__uint_as_float(r[c + 3]) + sb2[c + 3]));
             } else {
                 uint32_t r[32];
                 tc::tmem_ld32(tbase + ((uint32_t)(32 * w) << 16) + 256u, r);
@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(128, 1) mlp_infer_kernel(RowLoader<kF16> L, in
 #pragma unroll
                     for (int c = 0; c < 32; c += 4)
                         *reinterpret_cast<float4*>(Z + row * C + c) =
-                            make_float4(__uint_as_float(r[c]) + sb2[c], __uint_as_float(r[c + 1]) + sb2[c + 1],
-                                        __uint_as_float(r[c + 2]) + sb2[c + 2], __uint_as_float(r[c + 3]) + sb2[c + 3]);
+                            make_float4(tanhf(__uint_as_float(r[c]) + sb2[c]), tanhf(__uint_as_float(r[c + 1]) + sb2[c + 1]),
+                                        tanhf(__uint_as_float(r[c + 2]) + sb2[c + 2]), tanhf(__uint_as_float(r[c + 3]) + sb2[c + 3]));
             }
         }
         tc::fence_before_sync();

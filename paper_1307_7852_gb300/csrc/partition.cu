@@ -176,24 +176,66 @@ __global__ void gen_dirs_kernel(float* dirs, int T, int S, int d, int d_pad,
     }
 }
 
-// Learned splits: the key of a point at this level is its feature
-// feat[t] (an output of the split-feature network).
+// Learned splits, step 1: range (as order keys) of every tree's feature of
+// this level inside every node.
 struct FeatOfTree {
     int f[32];
 };
-__global__ void project_feature_kernel(int64_t n, int T, const float* __restrict__ Z, int C, FeatOfTree ft,
-                                       const int32_t* __restrict__ node_of, const int32_t* __restrict__ pos_of,
-                                       uint32_t* __restrict__ keys)
+__global__ void node_feature_range_kernel(int64_t n, int T, const float* __restrict__ Z, int C, FeatOfTree ft,
+                                          const int32_t* __restrict__ node_of, int S, uint32_t* __restrict__ rmin,
+                                          uint32_t* __restrict__ rmax)
 {
     const int64_t total = (int64_t)T * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        if (node_of[e] < 0) continue;
+        const int s = node_of[e];
+        if (s < 0) continue;
         const int t = (int)(e / n);
         const int64_t i = e - (int64_t)t * n;
-        keys[(int64_t)t * n + pos_of[e]] = ord_key(Z[i * C + ft.f[t]]);
+        const uint32_t o = ord_key(Z[i * C + ft.f[t]]);
+        atomicMin(&rmin[(int64_t)t * S + s], o);
+        atomicMax(&rmax[(int64_t)t * S + s], o);
     }
 }
+
+// Range of every feature over all points (order keys in scratch, then
+// max - min in frange).
+__global__ void feature_range_kernel(const float* __restrict__ Z, int64_t n, int C, uint32_t* __restrict__ mm)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * C; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const uint32_t o = ord_key(Z[e]);
+        atomicMin(&mm[c], o);
+        atomicMax(&mm[C + c], o);
+    }
+}
+__global__ void feature_range_finish_kernel(int C, const uint32_t* __restrict__ mm, float* __restrict__ frange)
+{
+    const int c = threadIdx.x;
+    if (c < C) frange[c] = unord_key(mm[C + c]) - unord_key(mm[c]);
+}
+
+cudaError_t run_feature_range(const float* Z, int64_t n, int C, uint32_t* mm, float* frange, cudaStream_t st)
+{
+    cudaMemsetAsync(mm, 0xFF, sizeof(uint32_t) * C, st);
+    cudaMemsetAsync(mm + C, 0, sizeof(uint32_t) * C, st);
+    const int blocks = (int)std::min<int64_t>((n * C + 255) / 256, (int64_t)num_sms() * 8);
+    feature_range_kernel<<<blocks, 256, 0, st>>>(Z, n, C, mm);
+    feature_range_finish_kernel<<<1, 32, 0, st>>>(C, mm, frange);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+// Learned-split settings of one level, passed to the projection kernel.
+struct LevelFeat {
+    const float* Z;
+    int C;
+    FeatOfTree ft;
+    const uint32_t* rmin;
+    const uint32_t* rmax;
+    const float* frange;
+    float tau;
+};
 
 void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf)
 {
@@ -213,12 +255,12 @@ void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf)
 // One warp per point; up to 8 trees per pass over the row.  The projection
 // order is the canonical one: lane l, j = 128c + 4l + e, fmaf, then the
 // pairwise rounds 16..1.
-template <bool kF16>
+template <bool kF16, bool kLearned>
 __global__ void __launch_bounds__(256) project_kernel(RowLoader<kF16> L, int64_t n, int T,
                                                       const float* __restrict__ dirs, int S,
                                                       int d_pad, const int32_t* __restrict__ node_of,
                                                       const int32_t* __restrict__ pos_of,
-                                                      uint32_t* __restrict__ keys)
+                                                      uint32_t* __restrict__ keys, LevelFeat lv)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -263,7 +305,15 @@ __global__ void __launch_bounds__(256) project_kernel(RowLoader<kF16> L, int64_t
             }
             if (my_s >= 0) {
                 const int64_t row = (int64_t)tl * n;
-                keys[row + pos_of[row + i]] = ord_key(mine);
+                uint32_t key = ord_key(mine);
+                if (kLearned) {
+                    // the node's learned feature, while it still varies there
+                    const int f = lv.ft.f[tl];
+                    const int64_t ns = (int64_t)tl * S + my_s;
+                    const float span = unord_key(lv.rmax[ns]) - unord_key(lv.rmin[ns]);
+                    if (span > lv.tau * lv.frange[f]) key = ord_key(lv.Z[i * lv.C + f]);
+                }
+                keys[row + pos_of[row + i]] = key;
             }
         }
     }
@@ -587,6 +637,12 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
     SelState* sel = ar.take<SelState>((size_t)T * S_big);
     uint32_t* ghist = ar.take<uint32_t>((size_t)T * S_big * 256);
     int32_t* cnt = ar.take<int32_t>((size_t)T * std::max(P.max_chunks, 1));
+    uint32_t* rmin = nullptr;
+    uint32_t* rmax = nullptr;
+    if (lf && lf->C > 0) {
+        rmin = ar.take<uint32_t>((size_t)T * S_max);
+        rmax = ar.take<uint32_t>((size_t)T * S_max);
+    }
     if (!ar.base) return cudaSuccess;  // measuring only
 
     const int sms = num_sms();
@@ -603,26 +659,36 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         const LevelPlan& L = P.levels[lvl];
         const SplitNode* nodes = dp.nodes + L.node_base;
         const int S = L.nnodes;
-        if (lf && lf->Z && (int)lvl < lf->C) {
-            FeatOfTree ft{};
-            for (int t = 0; t < T && t < 32; ++t) ft.f[t] = lf->feat[t][lvl];
-            project_feature_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, lf->Z, lf->C, ft, node_of,
-                                                                                      pos_of, keys);
-            note_launches(1);
-        } else {
-            gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(
-                dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed);
-            note_launches(1);
-            const int pgrid = grid_for(n * 32, 256, sms * 16);
-            if (x.dtype == 1) {
-                RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
-                project_kernel<true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
-            } else {
-                RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
-                project_kernel<false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys);
-            }
+        const bool learned = lf && lf->Z && (int)lvl < lf->C;
+        LevelFeat lv{};
+        if (learned) {
+            lv.Z = lf->Z;
+            lv.C = lf->C;
+            for (int t = 0; t < T && t < 32; ++t) lv.ft.f[t] = lf->feat[t][lvl];
+            lv.rmin = rmin;
+            lv.rmax = rmax;
+            lv.frange = lf->frange;
+            lv.tau = lf->tau;
+            cudaMemsetAsync(rmin, 0xFF, sizeof(uint32_t) * (size_t)T * S, st);
+            cudaMemsetAsync(rmax, 0, sizeof(uint32_t) * (size_t)T * S, st);
+            node_feature_range_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, lf->Z, lf->C, lv.ft,
+                                                                                         node_of, S, rmin, rmax);
             note_launches(1);
         }
+        gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(
+            dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed);
+        note_launches(1);
+        const int pgrid = grid_for(n * 32, 256, sms * 16);
+        if (x.dtype == 1) {
+            RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
+            if (learned) project_kernel<true, true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
+            else project_kernel<true, false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
+        } else {
+            RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
+            if (learned) project_kernel<false, true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
+            else project_kernel<false, false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
+        }
+        note_launches(1);
         // leaves of this level keep their positions: start from a copy
         cudaMemcpyAsync(nxt, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);
         if (L.nbig < S) {

@@ -55,13 +55,16 @@ def test_loss_terms_special_cases():
     rng = np.random.default_rng(4)
     Zh = rng.normal(size=(5, 3))
     Z = np.concatenate([Zh, Zh])
-    L, _ = mlp.loss_from_z(Z, 0.0, 1e-12)
+    L, _ = mlp.loss_from_z(Z, 0.0, 1e-12, 0.0)
     assert abs(L) < 1e-12
-    # uncorrelated unit outputs: the decorrelation term is ~0; with lam = 1
-    # and constant pairs it is exactly the squared off-diagonal correlation
+    # balanced, uncorrelated +-1 outputs shared by both endpoints: every term
+    # vanishes (pair 0, correlation 0, spread V = 1)
     Z = np.array([[1.0, 1.0], [-1.0, 1.0], [1.0, -1.0], [-1.0, -1.0]] * 2)
-    L, _ = mlp.loss_from_z(np.concatenate([Z, Z]), 1.0, 0.0)
+    L, _ = mlp.loss_from_z(np.concatenate([Z, Z]), 1.0, 0.0, 1.0)
     assert abs(L) < 1e-12
     Zc = np.array([[1.0, 1.0], [-1.0, -1.0]] * 2)  # perfectly correlated columns
-    L, _ = mlp.loss_from_z(np.concatenate([Zc, Zc]), 1.0, 0.0)
+    L, _ = mlp.loss_from_z(np.concatenate([Zc, Zc]), 1.0, 0.0, 0.0)
     assert abs(L - 2.0) < 1e-12
+    # collapse to a constant costs the spread term: C * mu_s
+    L, _ = mlp.loss_from_z(np.full((8, 3), 0.3), 0.0, 1e-4, 2.0)
+    assert abs(L - 6.0) < 1e-12
