@@ -55,6 +55,19 @@ def make_data(w, seed):
     raise ValueError(w["gen"])
 
 
+# ------------------------------------------------------------ multi-rank
+def aggregate(elapsed_s: float, points_per_rank: int, world: int, dist=None, device=None):
+    """Max over ranks of the timed seconds, and whole-job points/s
+    (world x points_per_rank / that time).  Every rank returns the same."""
+    el = float(elapsed_s)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([el], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    return el, points_per_rank * world / el
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
@@ -408,11 +421,7 @@ def main():
         torch.cuda.synchronize()
     knng.knng_set_stage_events(None, h)
     launches = knng.knng_launch_counter() - l0
-    el = t_start.elapsed_time(t_end) / 1e3
-    if dist:
-        tt = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        el = float(tt.item())
+    el, _ = aggregate(t_start.elapsed_time(t_end) / 1e3, n, world, dist, dev)
     sec = el / args.steps
     value = n * world / sec
     names = ["partition", "leaf_knn", "merge"] + [f"propagate_r{r}" for r in range(R)]
