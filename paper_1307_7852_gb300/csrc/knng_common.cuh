@@ -329,6 +329,97 @@ __device__ __forceinline__ bool hash_insert(int* tab, uint32_t hshift, uint32_t 
 
 namespace knng {
 
+// Sorted `want` smallest (want <= 64) of cnt unique keys key(0..cnt)
+// (cnt <= 32*PER), written ascending to out[0..min(want, cnt)) in shared
+// memory; returns that count.  The want-th smallest of the lane minima (or,
+// for want > 32, of the two smallest keys of every lane) bounds the want-th
+// smallest of all keys from above, so the keys up to it contain the answer;
+// usually few (<= 64) do and one small bitonic sort finishes.  Otherwise the
+// radix select decides.
+// scratch: >= 128 keys, hist: 256 words, both private to the warp.
+template <int PER, class KeyFn>
+__device__ int warp_topk_sorted(const KeyFn& key, int cnt, int want, uint64_t* out, uint64_t* scratch,
+                                uint32_t* hist)
+{
+    const int lane = threadIdx.x & 31;
+    if (want > cnt) want = cnt;
+    if (want <= 0) return 0;
+    uint64_t x[PER];
+    uint64_t a = kKeyMax, b = kKeyMax;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        const int idx = lane + 32 * e;
+        x[e] = idx < cnt ? key(idx) : kKeyMax;
+        if (x[e] < a) { b = a; a = x[e]; }
+        else if (x[e] < b) b = x[e];
+    }
+    const int wi = want - 1;
+    uint64_t tau;
+    if (want <= 32) {
+        // the want-th smallest lane minimum is already an upper bound
+        uint64_t s1[1] = {a};
+        warp_bitonic_sort<1>(s1);
+        tau = __shfl_sync(KNNG_FULL_MASK, s1[0], wi);
+    } else {
+        uint64_t s2[2] = {a, b};
+        warp_bitonic_sort<2>(s2);
+        tau = __shfl_sync(KNNG_FULL_MASK, (wi & 1) ? s2[1] : s2[0], wi >> 1);
+    }
+    int c = 0;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) c += __popc(__ballot_sync(KNNG_FULL_MASK, x[e] <= tau));
+    if (c <= 128) {
+        int base = 0;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const bool sel = x[e] <= tau;
+            const uint32_t bl = __ballot_sync(KNNG_FULL_MASK, sel);
+            if (sel) scratch[base + __popc(bl & lanemask_lt())] = x[e];
+            base += __popc(bl);
+        }
+        __syncwarp();
+        if (c <= 64) {
+            uint64_t v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) v[e] = lane * 2 + e < c ? scratch[lane * 2 + e] : kKeyMax;
+            warp_bitonic_sort<2>(v);
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (lane * 2 + e < want) out[lane * 2 + e] = v[e];
+        } else {
+            uint64_t v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = lane * 4 + e < c ? scratch[lane * 4 + e] : kKeyMax;
+            warp_bitonic_sort<4>(v);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (lane * 4 + e < want) out[lane * 4 + e] = v[e];
+        }
+    } else {
+        auto kx = [&](int idx) -> uint64_t { return key(idx); };
+        const uint64_t thr = warp_select_threshold(kx, cnt, want, hist);
+        int base = 0;
+        for (int it = 0; it < cnt; it += 32) {
+            const int idx = it + lane;
+            const uint64_t kv = idx < cnt ? key(idx) : kKeyMax;
+            const bool sel = idx < cnt && kv <= thr;
+            const uint32_t bl = __ballot_sync(KNNG_FULL_MASK, sel);
+            if (sel) scratch[base + __popc(bl & lanemask_lt())] = kv;
+            base += __popc(bl);
+        }
+        __syncwarp();
+        uint64_t v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) v[e] = lane * 2 + e < want ? scratch[lane * 2 + e] : kKeyMax;
+        warp_bitonic_sort<2>(v);
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if (lane * 2 + e < want) out[lane * 2 + e] = v[e];
+    }
+    __syncwarp();
+    return want;
+}
+
 // Canonical distances from point a to W points b[0..W) (W = 8, 16 or 32;
 // b in shared memory, entries c >= nb unused); lane l returns the distance to
 // b[l % W] (for l % W < nb).  Rows must be vector-aligned with d % 4 == 0.
@@ -401,56 +492,93 @@ __device__ __forceinline__ float warp_canon_dist16(const RowLoader<kF16>& L, int
 }
 
 // Finishes one row of a leaf graph (collective over one warp): from the
-// candidate distances Drow[0..m) (local index j; j == self excluded) pick the
-// kp smallest (D~, j), rescore them with the canonical FP32 distance between
-// the original rows, sort by (D, id) and write the k best to oi/od (padding
-// with -1 / +inf).  lid maps local index -> point id (ascending with j).
+// candidate distances Drow(j), j in [0, m) local indices (j == self
+// excluded), take the kp smallest (D~, j), rescore them with the canonical
+// FP32 distance between the original rows, sort by (D, id) and write the k
+// best to oi/od (padding with -1 / +inf).  lid maps local index -> point id
+// (ascending with j, so a local index ranks like the id).
 //
 // With rescore == false the candidate distances are taken as final: the
 // caller certifies that Drow(j) already equals the canonical distance (see
 // the exactness test of the tensor-core path), and kp should be k.
-template <int E, bool kF16, class DFn>
-__device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m, int self,
-                                const int32_t* lid, int k, int kp, uint32_t* hist, int* cand,
-                                int32_t* oi, float* od, bool rescore = true)
+//
+// ws: per-warp shared scratch of kLeafWarpScratch bytes.  m <= 32 * PER.
+constexpr int kLeafWarpScratch = 256 * 4 + 192 * 8;
+
+template <int PER, bool kF16, class DFn>
+__device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m, int self, const int32_t* lid,
+                                int k, int kp, unsigned char* ws, int32_t* oi, float* od, bool rescore = true)
 {
     const int lane = threadIdx.x & 31;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(ws + 1024);  // [0, 64) sorted picks, [64, 192) scratch
     auto key = [&](int j) -> uint64_t {
         return j == self ? kKeyMax : pack_key(Drow(j), (uint32_t)j);
     };
     const int want = min(kp, m - 1);
-    int nsel = 0;
-    if (want > 0) {
+    if (want > 64) {
+        // large k' (<= 128): radix select, then sort the picks
         const uint64_t thr = warp_select_threshold(key, m, want, hist);
-        nsel = warp_compact_le(key, m, thr, cand);
-    }
-    __syncwarp();
-    const int gi = lid[self];
-    uint64_t* keys = reinterpret_cast<uint64_t*>(hist);  // 128 keys (the histogram area is free again)
-    if (rescore) {
-        // local -> point ids, then rescore 32 (or fewer) candidates per pass
-        for (int c = lane; c < nsel; c += 32) cand[c] = lid[cand[c]];
+        int* cand = reinterpret_cast<int*>(hist);  // the histogram is free again
+        const int nsel = warp_compact_le(key, m, thr, cand);
         __syncwarp();
+        const int gi = lid[self];
+        uint64_t* rk = keys;  // 128 keys
         for (int c0 = 0; c0 < nsel; c0 += 16) {
             const int nb = min(16, nsel - c0);
-            const float dd = warp_canon_dist16(L, gi, cand + c0, nb);
-            if (lane < nb) keys[c0 + lane] = pack_key(dd, (uint32_t)cand[c0 + lane]);
+            int* ids16 = reinterpret_cast<int*>(keys + 128);  // 16 point ids
+            if (lane < nb) ids16[lane] = lid[cand[c0 + lane]];
+            __syncwarp();
+            float dd = 0.f;
+            if (rescore) dd = warp_canon_dist16(L, gi, ids16, nb);
+            else if (lane < nb) dd = Drow(cand[c0 + lane]);
+            if (lane < nb) rk[c0 + lane] = pack_key(dd, (uint32_t)ids16[lane]);
+            __syncwarp();
+        }
+        uint64_t v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = lane * 4 + e < nsel ? rk[lane * 4 + e] : kKeyMax;
+        warp_bitonic_sort<4>(v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = lane * 4 + e;
+            if (i < k) {
+                const bool ok = i < nsel;
+                oi[i] = ok ? (int32_t)(uint32_t)v[e] : -1;
+                od[i] = ok ? unord_key((uint32_t)(v[e] >> 32)) : __int_as_float(0x7f800000);
+            }
+        }
+        __syncwarp();
+        return;
+    }
+    const int nsel = warp_topk_sorted<PER>(key, m, want, keys, keys + 64, hist);
+    uint64_t v[2];
+    if (!rescore) {
+        // picks are final: (distance, local index) -> (distance, point id)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int i = lane * 2 + e;
+            v[e] = i < nsel ? ((keys[i] & 0xFFFFFFFF00000000ull) | (uint32_t)lid[(uint32_t)keys[i]]) : kKeyMax;
         }
     } else {
-        for (int c = lane; c < nsel; c += 32) keys[c] = pack_key(Drow(cand[c]), (uint32_t)lid[cand[c]]);
-    }
-    __syncwarp();
-    uint64_t v[E];
+        int* cid = reinterpret_cast<int*>(hist);  // 64 point ids
+        for (int c = lane; c < nsel; c += 32) cid[c] = lid[(uint32_t)keys[c]];
+        __syncwarp();
+        const int gi = lid[self];
+        uint64_t* rk = keys + 64;
+        for (int c0 = 0; c0 < nsel; c0 += 16) {
+            const int nb = min(16, nsel - c0);
+            const float dd = warp_canon_dist16(L, gi, cid + c0, nb);
+            if (lane < nb) rk[c0 + lane] = pack_key(dd, (uint32_t)cid[c0 + lane]);
+        }
+        __syncwarp();
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane * E + e;
-        v[e] = i < nsel ? keys[i] : kKeyMax;
+        for (int e = 0; e < 2; ++e) v[e] = lane * 2 + e < nsel ? rk[lane * 2 + e] : kKeyMax;
+        warp_bitonic_sort<2>(v);
     }
-    __syncwarp();
-    warp_bitonic_sort<E>(v);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane * E + e;
+    for (int e = 0; e < 2; ++e) {
+        const int i = lane * 2 + e;
         if (i < k) {
             const bool ok = i < nsel;
             oi[i] = ok ? (int32_t)(uint32_t)v[e] : -1;

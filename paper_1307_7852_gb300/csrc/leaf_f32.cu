@@ -26,18 +26,17 @@ struct LeafSmem {
     float* nrm;
     float* Bt;
     float* D;
-    uint32_t* hist;  // 256 per warp
-    int* cand;       // kCandCap per warp
+    unsigned char* ws;  // kLeafWarpScratch per warp
 };
 
 __host__ __device__ inline size_t leaf_smem_bytes(int m_pad)
 {
     return sizeof(int32_t) * m_pad + sizeof(float) * m_pad + sizeof(float) * kKC * (m_pad + 1) +
-           sizeof(float) * kRB * m_pad + (kNT / 32) * (256 * sizeof(uint32_t) + kCandCap * sizeof(int));
+           sizeof(float) * kRB * m_pad + 16 + (kNT / 32) * kLeafWarpScratch;
 }
 }  // namespace
 
-template <int CT, int E, bool kF16>
+template <int CT, bool kF16>
 __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, int64_t n,
                                                            const int32_t* __restrict__ perm,
                                                            const int32_t* __restrict__ leaf_off, int k,
@@ -53,8 +52,7 @@ __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, in
         sm.nrm = reinterpret_cast<float*>(p); p += sizeof(float) * m_pad;
         sm.Bt = reinterpret_cast<float*>(p); p += sizeof(float) * kKC * (m_pad + 1);
         sm.D = reinterpret_cast<float*>(p); p += sizeof(float) * kRB * m_pad;
-        sm.hist = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * 256 * (kNT / 32);
-        sm.cand = reinterpret_cast<int*>(p);
+        sm.ws = reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
     }
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int tx = tid & 31, ty = tid >> 5;
@@ -78,8 +76,7 @@ __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, in
         for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
         if (lane == 0) sm.nrm[r] = s;
     }
-    uint32_t* hist = sm.hist + 256 * w;
-    int* cand = sm.cand + kCandCap * w;
+    unsigned char* ws = sm.ws + (size_t)kLeafWarpScratch * w;
     constexpr int mp1 = m_pad + 1;
 
     for (int rb = 0; rb < m; rb += kRB) {
@@ -127,19 +124,19 @@ __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, in
             if (row >= m) break;
             const float* Drow = sm.D + r * m_pad;
             const int gi = sm.lid[row];
-            leaf_row_finish<E, kF16>(L, [&](int j) { return Drow[j]; }, m, row, sm.lid, k, kp, hist, cand,
-                                     out_ids + ((int64_t)t * n + gi) * k, out_d + ((int64_t)t * n + gi) * k);
+            leaf_row_finish<CT, kF16>(L, [&](int j) { return Drow[j]; }, m, row, sm.lid, k, kp, ws,
+                                  out_ids + ((int64_t)t * n + gi) * k, out_d + ((int64_t)t * n + gi) * k);
         }
     }
 }
 
-template <int CT, int E, bool kF16>
+template <int CT, bool kF16>
 static cudaError_t launch_leaf_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                                    const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
                                    cudaStream_t st)
 {
     const size_t smem = leaf_smem_bytes(32 * CT);
-    auto kern = leaf_knn_f32_kernel<CT, E, kF16>;
+    auto kern = leaf_knn_f32_kernel<CT, kF16>;
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -154,27 +151,17 @@ static cudaError_t launch_leaf_f32(const XDesc& x, const TreePlan& P, const DevP
     return cudaGetLastError();
 }
 
-template <int CT, bool kF16>
-static cudaError_t dispatch_e(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
-                              const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
-                              cudaStream_t st)
-{
-    if (kp <= 32) return launch_leaf_f32<CT, 1, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    if (kp <= 64) return launch_leaf_f32<CT, 2, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    return launch_leaf_f32<CT, 4, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-}
-
 template <bool kF16>
 static cudaError_t dispatch_ct(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                                const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
                                cudaStream_t st)
 {
     const int m = P.max_leaf;
-    if (m <= 32) return dispatch_e<1, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    if (m <= 64) return dispatch_e<2, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    if (m <= 128) return dispatch_e<4, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    if (m <= 256) return dispatch_e<8, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    return dispatch_e<16, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 32) return launch_leaf_f32<1, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 64) return launch_leaf_f32<2, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 128) return launch_leaf_f32<4, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 256) return launch_leaf_f32<8, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    return launch_leaf_f32<16, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
 }
 
 cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,

@@ -122,7 +122,7 @@ struct TcGeom {
     int smem;
 };
 
-template <int PREC, int E, bool kF16>
+template <int PREC, int PER, bool kF16>
 __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 RowLoader<kF16> L, int64_t n,
                                                                 const int32_t* __restrict__ perm,
@@ -140,9 +140,8 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
     int32_t* lid = reinterpret_cast<int32_t*>(base + G.pipe_bytes);
     float* qn = reinterpret_cast<float*>(lid + G.N_load);
     float* qs = qn + G.N_load;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(qs + G.N_load);
-    int* cand = reinterpret_cast<int*>(hist + kTcWarps * 256);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(cand + kTcWarps * kTcCand);
+    unsigned char* wsc = reinterpret_cast<unsigned char*>(((uintptr_t)(qs + G.N_load) + 15) & ~(uintptr_t)15);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsc + kTcWarps * kLeafWarpScratch);
     uint64_t* full = bars;
     uint64_t* empty = bars + G.S;
     uint64_t* done = bars + 2 * G.S;
@@ -284,9 +283,9 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 if (iloc >= m) break;
                 const float* drow = Dblk + (size_t)rr * ldD;
                 const int gi = lid[iloc];
-                leaf_row_finish<E, kF16>(L, [&](int j) { return drow[j]; }, m, iloc, lid, k, exact_leaf ? k : kp,
-                                         hist + 256 * w, cand + kTcCand * w, out_ids + ((int64_t)t * n + gi) * k,
-                                         out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
+                leaf_row_finish<PER, kF16>(L, [&](int j) { return drow[j]; }, m, iloc, lid, k, exact_leaf ? k : kp,
+                                      wsc + (size_t)kLeafWarpScratch * w, out_ids + ((int64_t)t * n + gi) * k,
+                                      out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
             }
             __syncthreads();
         }
@@ -339,7 +338,7 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec, const TcTile* tile
     }
     G.pipe_bytes = std::max(G.S * G.stage_bytes, G.RG * G.ldD * 4);
     G.pipe_bytes = (G.pipe_bytes + 1023) & ~1023;
-    G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + kTcWarps * (256 * 4 + kTcCand * 4) + (2 * G.S + 1) * 8 + 16;
+    G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + 16 + kTcWarps * kLeafWarpScratch + (2 * G.S + 1) * 8 + 16;
     return G;
 }
 
@@ -363,12 +362,12 @@ std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec)
     return out;
 }
 
-template <int PREC, int E, bool kF16>
+template <int PREC, int PER, bool kF16>
 static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                              const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
                              const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
 {
-    auto kern = leaf_tc_kernel<PREC, E, kF16>;
+    auto kern = leaf_tc_kernel<PREC, PER, kF16>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
     if (e != cudaSuccess) return e;
     RowLoader<kF16> rl{x.X, x.ld, x.d, x.vec};
@@ -385,9 +384,10 @@ static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const Tre
                                const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
                                const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
 {
-    if (kp <= 32) return launch_tc<PREC, 1, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
-    if (kp <= 64) return launch_tc<PREC, 2, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
-    return launch_tc<PREC, 4, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    // keys per lane in the row selection: leaves of up to 32 * PER points
+    if (P.max_leaf <= 128) return launch_tc<PREC, 4, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    if (P.max_leaf <= 256) return launch_tc<PREC, 8, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    return launch_tc<PREC, 16, kF16>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
 }
 
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,

@@ -45,10 +45,11 @@ static PropLayout prop_layout(int k)
     int lg = 0;
     while ((1 << lg) < H) ++lg;
     L.hshift = 32 - lg;
-    // tab[H] | cid[cap] | cd[cap] | hist[256] | sel[64] | own[64] | own_fl[64] (u64)
+    // tab[H] | cid[cap] | cd[cap] | hist[256] | sel[64] | own[64] | own_fl[64] (u64) | keys[192] (u64)
     L.cap = (L.cap + 1) & ~1;  // keeps own_fl 8-byte aligned
     L.per_warp = sizeof(int) * (size_t)H + (sizeof(int) + sizeof(float)) * (size_t)L.cap +
-                 sizeof(uint32_t) * 256 + sizeof(int) * 64 + sizeof(int) * 64 + sizeof(unsigned long long) * 64;
+                 sizeof(uint32_t) * 256 + sizeof(int) * 64 + sizeof(int) * 64 + sizeof(unsigned long long) * 64 +
+                 sizeof(unsigned long long) * 192;
     L.per_warp = (L.per_warp + 15) & ~(size_t)15;
     return L;
 }
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
     int* sel = reinterpret_cast<int*>(hist + 256);
     int* own = sel + 64;
     unsigned long long* own_fl = reinterpret_cast<unsigned long long*>(own + 64);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(own_fl + 64);
     const uint32_t hmask = (uint32_t)H - 1;
     const int kk = k * k;
 
@@ -145,19 +147,28 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         auto key = [&](int idx) -> uint64_t { return pack_key(cd[idx], (uint32_t)cid[idx]); };
         const int want = min(k, cnt);
         int nsel = 0;
-        if (want > 0) {
-            const uint64_t thr = warp_select_threshold(key, cnt, want, hist);
-            nsel = warp_compact_le(key, cnt, thr, sel);
-        }
-        __syncwarp();
         uint64_t v[E];
-        int from[E];
+        if (cnt <= 512 && want <= 64) {
+            nsel = warp_topk_sorted<16>(key, cnt, want, keys, keys + 64, hist);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int i = lane * E + e;
-            v[e] = i < nsel ? key(sel[i]) : kKeyMax;
+            for (int e = 0; e < E; ++e) {
+                const int i = lane * E + e;
+                v[e] = i < nsel ? keys[i] : kKeyMax;
+            }
+        } else {
+            if (want > 0) {
+                const uint64_t thr = warp_select_threshold(key, cnt, want, hist);
+                nsel = warp_compact_le(key, cnt, thr, sel);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane * E + e;
+                v[e] = i < nsel ? key(sel[i]) : kKeyMax;
+            }
+            warp_bitonic_sort<E>(v);
         }
-        warp_bitonic_sort<E>(v);
+        int from[E];
         // new-entry flags: an output id is new unless it was in p's list
         unsigned long long fl = 0;
 #pragma unroll
