@@ -13,7 +13,9 @@
  *    torch tensors, ...), owned by the caller; the library never frees them.
  *    Entry points whose name ends in _host take HOST pointers instead.
  *  - X is row-major: point i starts at element i*ld; ld >= d.  dtype is
- *    KNNG_DTYPE_F32 (float) or KNNG_DTYPE_F16 (IEEE half, widened exactly).
+ *    KNNG_DTYPE_F32 (float), KNNG_DTYPE_F16 (IEEE half) or KNNG_DTYPE_U8
+ *    (unsigned bytes, e.g. SIFT descriptors); F16 and U8 entries are widened
+ *    exactly to float, and every result is the one for the equal float rows.
  *  - Graph outputs are ids[n][k] (int32) and dists[n][k] (float): the
  *    neighbours of point i in row i, ordered by (distance, id) ascending,
  *    never containing i, without duplicates.  A distance is the SQUARED
@@ -52,6 +54,7 @@ extern "C" {
 /* ---- enumerations ---------------------------------------------------- */
 #define KNNG_DTYPE_F32 0
 #define KNNG_DTYPE_F16 1
+#define KNNG_DTYPE_U8 2
 
 /* Precision of the leaf candidate stage.  The leaf top-k' is chosen on
  * distances computed from rows at this precision, then every candidate is
@@ -105,7 +108,13 @@ int knng_leaf_offsets(int64_t n, int32_t leaf_size, int64_t* leaf_off);
 /* ---- whole method ---------------------------------------------------- */
 /* Builds the approximate k-NN graph of X[n][d] (Sec. 3): p->T divisions,
  * leaf graphs, merge, p->prop_rounds propagation rounds.  ids, dists: device
- * [n][k].  2 <= n < 2^31, 1 <= d <= 4096. */
+ * [n][k].  2 <= n < 2^31, 1 <= d <= 4096.
+ * Float rows with d <= 256 are also checked on the device, in one pass, for
+ * holding only integers 0..255 (descriptor data such as SIFT); if they do,
+ * the projection and propagation read an exact byte copy of X kept in the
+ * workspace (n * round_up(d, 16) bytes more).  The result does not change:
+ * the copy holds the same values, and with d * 255^2 < 2^24 every FP32
+ * distance between such rows is an exact integer. */
 int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                const knng_params* p, int32_t* ids, float* dists, void* stream);
 /* Same as knng_build with HOST X, ids and dists: copies X to the device,

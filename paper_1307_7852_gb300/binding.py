@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libknng.so")
 
 KNNG_OK = 0
-DTYPE_F32, DTYPE_F16 = 0, 1
+DTYPE_F32, DTYPE_F16, DTYPE_U8 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 PART_RANDOM = 0
 
@@ -163,8 +163,10 @@ def _xdesc(X):
         dt = DTYPE_F32
     elif X.dtype == torch.float16:
         dt = DTYPE_F16
+    elif X.dtype == torch.uint8:
+        dt = DTYPE_U8
     else:
-        raise TypeError("X must be float32 or float16")
+        raise TypeError("X must be float32, float16 or uint8")
     return ctypes.c_void_p(X.data_ptr()), dt, X.shape[0], X.shape[1], X.stride(0)
 
 
@@ -227,13 +229,14 @@ def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, resco
 def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32,
                     rescore_mult=2, ids=None, dists=None, stream=None, device: int = 0,
                     h: Handle = None):
-    """Host arrays in and out (X float32/float16 [n, d], C-contiguous rows)."""
+    """Host arrays in and out (X float32/float16/uint8 [n, d], unit stride along d)."""
     X = np.asarray(X)
     if X.ndim != 2 or X.strides[1] != X.itemsize:
         raise ValueError("X must be 2-D with unit stride along d")
-    dt = DTYPE_F16 if X.dtype == np.float16 else DTYPE_F32
-    if X.dtype not in (np.float16, np.float32):
-        raise TypeError("X must be float32 or float16")
+    dts = {np.dtype(np.float32): DTYPE_F32, np.dtype(np.float16): DTYPE_F16, np.dtype(np.uint8): DTYPE_U8}
+    if X.dtype not in dts:
+        raise TypeError("X must be float32, float16 or uint8")
+    dt = dts[X.dtype]
     n, d = X.shape
     ld = X.strides[0] // X.itemsize
     if ids is None:

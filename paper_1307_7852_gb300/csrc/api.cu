@@ -169,16 +169,22 @@ int ensure_plan(knng_handle* h, int64_t n, int g, cudaStream_t st)
     return KNNG_OK;
 }
 
+size_t dtype_size(int32_t dtype)
+{
+    return dtype == KNNG_DTYPE_F16 ? 2 : dtype == KNNG_DTYPE_U8 ? 1 : 4;
+}
+
 int check_x(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld, XDesc& x)
 {
     if (!h) return KNNG_ERR_INVALID_ARG;
     if (!X) return fail(h, KNNG_ERR_INVALID_ARG, "X is NULL");
-    if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16) return fail(h, KNNG_ERR_INVALID_ARG, "dtype %d", dtype);
+    if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16 && dtype != KNNG_DTYPE_U8)
+        return fail(h, KNNG_ERR_INVALID_ARG, "dtype %d", dtype);
     if (n < 2 || n >= (int64_t)1 << 31) return fail(h, KNNG_ERR_INVALID_ARG, "n = %lld out of [2, 2^31)", (long long)n);
     if (d < 1 || d > 4096) return fail(h, KNNG_ERR_INVALID_ARG, "d = %d out of [1, 4096]", d);
     if (ld < d || ld >= (int64_t)1 << 31) return fail(h, KNNG_ERR_INVALID_ARG, "ld = %lld out of [d, 2^31)", (long long)ld);
-    const size_t es = dtype == KNNG_DTYPE_F16 ? 2 : 4;
-    const size_t align = dtype == KNNG_DTYPE_F16 ? 8 : 16;
+    const size_t es = dtype_size(dtype);
+    const size_t align = dtype == KNNG_DTYPE_F16 ? 8 : dtype == KNNG_DTYPE_U8 ? 4 : 16;
     x.X = X;
     x.dtype = dtype;
     x.n = n;
@@ -240,10 +246,11 @@ int check_params(knng_handle* h, const knng_params* p, int64_t n)
 // The whole method over one point set (or one forest of sets): divisions,
 // leaf graphs, merge, propagation rounds.  Carves its buffers from ar; with
 // ar.base == nullptr it only measures them.
-int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc& x, const knng_params& p,
+int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc& x_in, const knng_params& p,
                    int32_t* ids, float* dists, Arena& a, cudaStream_t st, bool events,
-                   const LearnedFeat* lf = nullptr)
+                   const LearnedFeat* lf = nullptr, bool byte_copy = false)
 {
+    XDesc x = x_in;
     const int64_t n = x.n;
     const int T = p.T, k = p.k, R = p.prop_rounds;
     const size_t nk = (size_t)n * k;
@@ -258,6 +265,14 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         bi[b] = a.take<int32_t>(nk);
         bd[b] = a.take<float>(nk);
         fl[b] = a.take<unsigned long long>(n);
+    }
+    // float rows that hold only bytes: exact byte copy for the gathering kernels
+    uint8_t* xb = nullptr;
+    int* xb_bad = nullptr;
+    const int64_t ldb = ((int64_t)x.d + 15) & ~(int64_t)15;
+    if (byte_copy && x.dtype == KNNG_DTYPE_F32 && x.d <= 256) {
+        xb = a.take<uint8_t>((size_t)n * ldb);
+        xb_bad = a.take<int>(1);
     }
     const size_t fixed = a.off;
     int r;
@@ -275,7 +290,16 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         if (rec) cudaEventRecord(h->stage_ev[i], st);
     };
     mark(0);
-    cudaError_t e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf);
+    cudaError_t e;
+    if (xb) {
+        e = cudaMemsetAsync(xb_bad, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = run_byte_copy(x, xb, ldb, xb_bad, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "byte copy");
+        x.Xb = xb;
+        x.ldb = ldb;
+        x.xb_bad = xb_bad;
+    }
+    e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf);
     if (e != cudaSuccess) return cuda_fail(h, e, "partition");
     mark(1);
     const size_t part_end = a.off;
@@ -510,11 +534,11 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((r = ensure_plan(h, n, p->leaf_size, st))) return r;
     Arena m;
-    if ((r = build_pipeline(h, h->plan, h->dplan, x, *p, ids, dists, m, st, true))) return r;
+    if ((r = build_pipeline(h, h->plan, h->dplan, x, *p, ids, dists, m, st, true, nullptr, true))) return r;
     if ((r = ensure_ws(h, m.off, st))) return r;
     Arena a;
     a.base = h->ws;
-    return build_pipeline(h, h->plan, h->dplan, x, *p, ids, dists, a, st, true);
+    return build_pipeline(h, h->plan, h->dplan, x, *p, ids, dists, a, st, true, nullptr, true);
 }
 
 int knng_exact_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
@@ -687,7 +711,7 @@ int knng_build_batched(knng_handle* h, int32_t nsets, const knng_dataset* sets, 
         size_t need = 0;
         for (BatchGroup& g : B.groups) {
             Arena m;
-            const size_t es = g.dtype == KNNG_DTYPE_F16 ? 2 : 4;
+            const size_t es = dtype_size(g.dtype);
             m.take<char>((size_t)g.n * g.ld * es);
             m.take<int32_t>((size_t)g.n * p->k);
             m.take<float>((size_t)g.n * p->k);
@@ -705,7 +729,7 @@ int knng_build_batched(knng_handle* h, int32_t nsets, const knng_dataset* sets, 
         for (BatchGroup& g : B.groups) {
             Arena a;
             a.base = h->ws;
-            const size_t es = g.dtype == KNNG_DTYPE_F16 ? 2 : 4;
+            const size_t es = dtype_size(g.dtype);
             char* xc = a.take<char>((size_t)g.n * g.ld * es);
             int32_t* gi = a.take<int32_t>((size_t)g.n * p->k);
             float* gd = a.take<float>((size_t)g.n * p->k);
@@ -895,7 +919,7 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     m0.take<float>((size_t)n * M->C);
     m0.take<uint32_t>(2 * (size_t)M->C);
     m0.take<float>((size_t)M->C);
-    if ((r = build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, m0, st, true, &lf))) return r;
+    if ((r = build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, m0, st, true, &lf, true))) return r;
     if ((r = ensure_ws(h, m0.off, st))) return r;
     Arena a;
     a.base = h->ws;
@@ -909,7 +933,7 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     cudaError_t e = run_mlp_forward(*M, x, Z, h->dev_err, st);
     if (e == cudaSuccess) e = run_feature_range(Z, n, M->C, mm, frange, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "network inference");
-    return build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, a, st, true, &lf);
+    return build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, a, st, true, &lf, true);
 }
 
 int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
@@ -921,7 +945,7 @@ int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int
         return fail(h, KNNG_ERR_INVALID_ARG, "bad sizes");
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t es = dtype == KNNG_DTYPE_F16 ? 2 : 4;
+    const size_t es = dtype_size(dtype);
     const size_t xbytes = (size_t)((n - 1) * ld + d) * es;
     const size_t nk = (size_t)n * p->k;
     void* dx = nullptr;

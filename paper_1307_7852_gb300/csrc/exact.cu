@@ -7,6 +7,8 @@
 // shared memory in tiles of 32 rows, so each row is read once per block.
 // Every warp keeps a buffer of keys below its current k-th best and shrinks
 // it to the k best (warp radix select) whenever it fills.
+#include <type_traits>
+
 #include "knng_common.cuh"
 #include "knng_internal.h"
 
@@ -16,8 +18,8 @@ namespace {
 constexpr int kQB = 8;  // queries (warps) per block
 }
 
-template <bool kF16>
-__global__ void __launch_bounds__(kQB * 32) exact_knn_kernel(RowLoader<kF16> L, int64_t n,
+template <int kDT>
+__global__ void __launch_bounds__(kQB * 32) exact_knn_kernel(RowLoader<kDT> L, int64_t n,
                                                              const int32_t* __restrict__ queries, int nq,
                                                              int k, int cap, int32_t* __restrict__ out_ids,
                                                              float* __restrict__ out_d)
@@ -128,19 +130,17 @@ cudaError_t run_exact_knn(const XDesc& x, const int32_t* queries, int nq, int k,
                         sizeof(uint32_t) * 256 * kQB + sizeof(int) * 64 * kQB;
     if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
     const int grid = (nq + kQB - 1) / kQB;
-    if (x.dtype == 1) {
-        auto kern = exact_knn_kernel<true>;
+    auto launch = [&](auto dt) {
+        constexpr int kDT = decltype(dt)::value;
+        auto kern = exact_knn_kernel<kDT>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
+        RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
         kern<<<grid, kQB * 32, smem, st>>>(rl, x.n, queries, nq, k, cap, ids, dists);
         note_launches(1);
-    } else {
-        auto kern = exact_knn_kernel<false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
-        kern<<<grid, kQB * 32, smem, st>>>(rl, x.n, queries, nq, k, cap, ids, dists);
-        note_launches(1);
-    }
+    };
+    if (x.dtype == kDtF16) launch(std::integral_constant<int, kDtF16>{});
+    else if (x.dtype == kDtU8) launch(std::integral_constant<int, kDtU8>{});
+    else launch(std::integral_constant<int, kDtF32>{});
     return cudaGetLastError();
 }
 

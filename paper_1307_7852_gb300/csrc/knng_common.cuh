@@ -63,14 +63,24 @@ __device__ __forceinline__ uint64_t pack_key(float dist, uint32_t id)
 
 // ---------------------------------------------------------------------------
 // Row loads.  Point i of X starts at element i*ld; d entries.  load4 returns
-// entries j..j+3 (zero past d) widened to FP32.
+// entries j..j+3 (zero past d) widened to FP32.  Element types: FP32, FP16
+// and unsigned bytes (byte values widen exactly, so every FP32 computation
+// on them is the one on the equal float rows).
 // ---------------------------------------------------------------------------
-template <bool kF16>
+constexpr int kDtF32 = 0, kDtF16 = 1, kDtU8 = 2;
+
+__device__ __forceinline__ float4 bytes_to_float4(uint32_t u)
+{
+    return make_float4((float)(u & 0xFFu), (float)((u >> 8) & 0xFFu), (float)((u >> 16) & 0xFFu),
+                       (float)(u >> 24));
+}
+
+template <int kDT>
 struct RowLoader {
     const void* X;
     int64_t ld;
     int d;
-    bool vec;  // rows 16-byte (F32) / 8-byte (F16) aligned and ld multiple of 4
+    bool vec;  // rows 16-byte (F32) / 8-byte (F16) / 4-byte (U8) aligned and ld multiple of 4
 
     // element offset of row i (ids < 2^31, ld < 2^31: one 32x32->64 multiply)
     __device__ __forceinline__ uint64_t row_off(int64_t i) const
@@ -81,7 +91,7 @@ struct RowLoader {
     __device__ __forceinline__ float4 load4(int64_t i, int j) const
     {
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (kF16) {
+        if (kDT == kDtF16) {
             const __half* row = static_cast<const __half*>(X) + row_off(i);
             if (vec && j + 3 < d) {
                 const uint2 u = __ldg(reinterpret_cast<const uint2*>(row + j));
@@ -94,6 +104,16 @@ struct RowLoader {
                 if (j + 1 < d) r.y = __half2float(row[j + 1]);
                 if (j + 2 < d) r.z = __half2float(row[j + 2]);
                 if (j + 3 < d) r.w = __half2float(row[j + 3]);
+            }
+        } else if (kDT == kDtU8) {
+            const uint8_t* row = static_cast<const uint8_t*>(X) + row_off(i);
+            if (vec && j + 3 < d) {
+                r = bytes_to_float4(__ldg(reinterpret_cast<const unsigned int*>(row + j)));
+            } else {
+                if (j + 0 < d) r.x = (float)__ldg(row + j + 0);
+                if (j + 1 < d) r.y = (float)__ldg(row + j + 1);
+                if (j + 2 < d) r.z = (float)__ldg(row + j + 2);
+                if (j + 3 < d) r.w = (float)__ldg(row + j + 3);
             }
         } else {
             const float* row = static_cast<const float*>(X) + row_off(i);
@@ -111,20 +131,31 @@ struct RowLoader {
     // entries j..j+3 of row i when rows are vector-aligned and j + 3 < d
     __device__ __forceinline__ float4 load4v(int64_t i, int j) const
     {
-        if (kF16) {
+        if (kDT == kDtF16) {
             const uint2 u = __ldg(reinterpret_cast<const uint2*>(static_cast<const __half*>(X) + row_off(i) + j));
             const float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
             const float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
             return make_float4(fa.x, fa.y, fb.x, fb.y);
         }
+        if (kDT == kDtU8) return bytes_to_float4(load_u8x4(i, j));
         return __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(X) + row_off(i) + j));
+    }
+    // bytes j..j+3 of row i packed little-endian (U8 rows, vector-aligned)
+    __device__ __forceinline__ uint32_t load_u8x4(int64_t i, int j) const
+    {
+        return __ldg(reinterpret_cast<const unsigned int*>(static_cast<const uint8_t*>(X) + row_off(i) + j));
     }
     // every load of a row is a full vector load (aligned rows, d % 4 == 0)
     __device__ __forceinline__ bool all_vec() const { return vec && (d & 3) == 0; }
+    // byte rows whose squared distances stay below 2^24 (d * 255^2 < 2^24):
+    // every partial sum of the canonical FP32 distance is then an exact
+    // integer, so integer arithmetic in any order gives the same value
+    __device__ __forceinline__ bool int_exact() const { return kDT == kDtU8 && d <= 256; }
 
     __device__ __forceinline__ float load1(int64_t i, int j) const
     {
-        if (kF16) return __half2float(static_cast<const __half*>(X)[row_off(i) + j]);
+        if (kDT == kDtF16) return __half2float(static_cast<const __half*>(X)[row_off(i) + j]);
+        if (kDT == kDtU8) return (float)__ldg(static_cast<const uint8_t*>(X) + row_off(i) + j);
         return __ldg(static_cast<const float*>(X) + row_off(i) + j);
     }
 };
@@ -136,8 +167,8 @@ struct RowLoader {
 // offsets 16, 8, 4, 2, 1.  Every lane returns the same value, and the value
 // depends only on the two rows (so D(a, b) == D(b, a) bit for bit).
 // ---------------------------------------------------------------------------
-template <bool kF16>
-__device__ __forceinline__ float warp_canon_dist(const RowLoader<kF16>& L, int64_t a, int64_t b)
+template <int kDT>
+__device__ __forceinline__ float warp_canon_dist(const RowLoader<kDT>& L, int64_t a, int64_t b)
 {
     const int lane = threadIdx.x & 31;
     float s = 0.0f;
@@ -430,8 +461,8 @@ __device__ int warp_topk_sorted(const KeyFn& key, int cnt, int want, uint64_t* o
 // and receives its partner's copy of them).  These are the pairwise additions
 // of the xor butterfly in warp_canon_dist, so the result is bit-identical to
 // it, with far fewer shuffles and W row loads in flight.
-template <int W, bool kF16>
-__device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
+template <int W, int kDT>
+__device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kDT>& L, int64_t a, const int* b, int nb)
 {
     const int lane = threadIdx.x & 31;
     int bid[W];
@@ -475,13 +506,57 @@ __device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kF16>& L,
     return p[0];
 }
 
+// Byte rows with exact integer distances (RowLoader::int_exact): the same
+// lane split and reduction tree as warp_canon_dist_batch in 32-bit integer
+// arithmetic, |x - y| per byte and a 4-way dot product per word.  Equal to
+// the canonical FP32 distance, since every partial sum of that one is exact.
+template <int W, int kDT>
+__device__ __forceinline__ float warp_u8_dist_batch(const RowLoader<kDT>& L, int64_t a, const int* b, int nb)
+{
+    const int lane = threadIdx.x & 31;
+    int bid[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) bid[c] = c < nb ? b[c] : (int)a;
+    uint32_t p[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) p[c] = 0u;
+    for (int j = 4 * lane; j < L.d; j += 128) {
+        const uint32_t xa = L.load_u8x4(a, j);
+        uint32_t xb[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) xb[c] = L.load_u8x4(bid[c], j);
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const uint32_t t = __vabsdiffu4(xa, xb[c]);
+            p[c] = __dp4a(t, t, p[c]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= W; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) p[c] += __shfl_xor_sync(KNNG_FULL_MASK, p[c], o);
+    }
+#pragma unroll
+    for (int o = W / 2; o >= 1; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const uint32_t send = hi ? p[i] : p[i + o];
+            const uint32_t keep = hi ? p[i + o] : p[i];
+            p[i] = keep + __shfl_xor_sync(KNNG_FULL_MASK, send, o);
+        }
+    }
+    return (float)p[0];
+}
+
 // Canonical distances from a to b[0..nb) (nb <= 16): lane c < nb returns the
 // distance to b[c].  Vector-aligned rows take the batched path; other rows
 // one distance at a time.
-template <bool kF16>
-__device__ __forceinline__ float warp_canon_dist16(const RowLoader<kF16>& L, int64_t a, const int* b, int nb)
+template <int kDT>
+__device__ __forceinline__ float warp_canon_dist16(const RowLoader<kDT>& L, int64_t a, const int* b, int nb)
 {
-    if (L.all_vec()) return warp_canon_dist_batch<16, kF16>(L, a, b, nb);
+    if (kDT == kDtU8 && L.all_vec() && L.int_exact()) return warp_u8_dist_batch<16>(L, a, b, nb);
+    if (L.all_vec()) return warp_canon_dist_batch<16, kDT>(L, a, b, nb);
     const int lane = threadIdx.x & 31;
     float mine = 0.f;
     for (int c = 0; c < nb; ++c) {
@@ -505,8 +580,8 @@ __device__ __forceinline__ float warp_canon_dist16(const RowLoader<kF16>& L, int
 // ws: per-warp shared scratch of kLeafWarpScratch bytes.  m <= 32 * PER.
 constexpr int kLeafWarpScratch = 256 * 4 + 192 * 8;
 
-template <int PER, bool kF16, class DFn>
-__device__ void leaf_row_finish(const RowLoader<kF16>& L, const DFn& Drow, int m, int self, const int32_t* lid,
+template <int PER, int kDT, class DFn>
+__device__ void leaf_row_finish(const RowLoader<kDT>& L, const DFn& Drow, int m, int self, const int32_t* lid,
                                 int k, int kp, unsigned char* ws, int32_t* oi, float* od, bool rescore = true)
 {
     const int lane = threadIdx.x & 31;

@@ -103,11 +103,18 @@ struct Arena {
 
 struct XDesc {
     const void* X;
-    int dtype;  // 0 f32, 1 f16
+    int dtype;  // 0 f32, 1 f16, 2 u8
     int64_t n;
     int d;
     int64_t ld;
     bool vec;
+    // Optional byte copy of float rows (n rows of ldb bytes) and a device word
+    // that stays 0 when every entry of X is an integer in [0, 255] (d <= 256):
+    // the copy then holds exactly the same values, and the row-gathering
+    // kernels (projection, propagation) read it instead of X.
+    const uint8_t* Xb = nullptr;
+    int64_t ldb = 0;
+    const int* xb_bad = nullptr;
 };
 
 // Learned split features: Z[n][C] (FP32) and, per tree t, the feature used
@@ -167,6 +174,10 @@ cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const floa
 // One synchronous propagation round.  flags_in (nullable = every entry new)
 // marks, per point, the list entries that were not in the previous round's
 // list; flags_out (nullable) receives the same for the output lists.
+// Byte copy of float rows (see XDesc::Xb); *bad is set when an entry is not
+// an integer in [0, 255].  *bad must be 0 on entry.
+cudaError_t run_byte_copy(const XDesc& x, uint8_t* Xb, int64_t ldb, int* bad, cudaStream_t st);
+
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
                           unsigned long long* flags_out, cudaStream_t st);

@@ -36,8 +36,8 @@ __host__ __device__ inline size_t leaf_smem_bytes(int m_pad)
 }
 }  // namespace
 
-template <int CT, bool kF16>
-__global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, int64_t n,
+template <int CT, int kDT>
+__global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kDT> L, int64_t n,
                                                            const int32_t* __restrict__ perm,
                                                            const int32_t* __restrict__ leaf_off, int k,
                                                            int kp, int32_t* __restrict__ out_ids,
@@ -124,19 +124,19 @@ __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kF16> L, in
             if (row >= m) break;
             const float* Drow = sm.D + r * m_pad;
             const int gi = sm.lid[row];
-            leaf_row_finish<CT, kF16>(L, [&](int j) { return Drow[j]; }, m, row, sm.lid, k, kp, ws,
+            leaf_row_finish<CT, kDT>(L, [&](int j) { return Drow[j]; }, m, row, sm.lid, k, kp, ws,
                                   out_ids + ((int64_t)t * n + gi) * k, out_d + ((int64_t)t * n + gi) * k);
         }
     }
 }
 
-template <int CT, bool kF16>
+template <int CT, int kDT>
 static cudaError_t launch_leaf_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                                    const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
                                    cudaStream_t st)
 {
     const size_t smem = leaf_smem_bytes(32 * CT);
-    auto kern = leaf_knn_f32_kernel<CT, kF16>;
+    auto kern = leaf_knn_f32_kernel<CT, kDT>;
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -144,24 +144,24 @@ static cudaError_t launch_leaf_f32(const XDesc& x, const TreePlan& P, const DevP
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    RowLoader<kF16> rl{x.X, x.ld, x.d, x.vec};
+    RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
     const int nleaves = (int)P.leaf_off.size() - 1;
     kern<<<dim3(nleaves, T), kNT, smem, st>>>(rl, x.n, perm, dp.leaf_off, k, kp, ids, dists);
     note_launches(1);
     return cudaGetLastError();
 }
 
-template <bool kF16>
+template <int kDT>
 static cudaError_t dispatch_ct(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                                const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
                                cudaStream_t st)
 {
     const int m = P.max_leaf;
-    if (m <= 32) return launch_leaf_f32<1, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    if (m <= 64) return launch_leaf_f32<2, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    if (m <= 128) return launch_leaf_f32<4, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    if (m <= 256) return launch_leaf_f32<8, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    return launch_leaf_f32<16, kF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 32) return launch_leaf_f32<1, kDT>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 64) return launch_leaf_f32<2, kDT>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 128) return launch_leaf_f32<4, kDT>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (m <= 256) return launch_leaf_f32<8, kDT>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    return launch_leaf_f32<16, kDT>(x, P, dp, T, perm, k, kp, ids, dists, st);
 }
 
 cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
@@ -169,8 +169,9 @@ cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& d
                              cudaStream_t st)
 {
     if (kp > kCandCap) kp = kCandCap;
-    if (x.dtype == 1) return dispatch_ct<true>(x, P, dp, T, perm, k, kp, ids, dists, st);
-    return dispatch_ct<false>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (x.dtype == kDtF16) return dispatch_ct<kDtF16>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    if (x.dtype == kDtU8) return dispatch_ct<kDtU8>(x, P, dp, T, perm, k, kp, ids, dists, st);
+    return dispatch_ct<kDtF32>(x, P, dp, T, perm, k, kp, ids, dists, st);
 }
 
 }  // namespace knng

@@ -1,0 +1,349 @@
+#pragma once
+// Leaf graphs on the 5th-generation tensor cores (Sec. 3.1 of arXiv:1307.7852:
+// a brute-force k-NN graph inside every leaf), reduced-precision candidate
+// stage with exact FP32 rescoring.
+//
+//  1. gather_quant: writes every tree's points in leaf order as bfloat16 (or
+//     E4M3 codes with one FP32 scale per row), rows zero-padded to whole
+//     128-byte K slices, with the squared norm of each quantised row.
+//  2. leaf_tc: one CTA per (tree, leaf, block of 128 rows).  A single thread
+//     streams the leaf's rows through a TMA pipeline (128-byte swizzled
+//     tiles, mbarrier completion) and issues tcgen05.mma with the CTA's 128
+//     rows as A and all leaf rows as B (A is a slice of the B tile), so the
+//     Gram block S = X_rows X_leaf^T accumulates in TMEM in FP32.  The four
+//     warps read their TMEM lanes back (tcgen05.ld), form
+//     D~ = |x|^2 + |y|^2 - 2 S (with the row scales for E4M3) and, one warp
+//     per row, select the k' best candidates, rescore them with the canonical
+//     FP32 distance on the original rows and keep the k best.
+// Kernels and per-element-type launchers; the host side (tile geometry,
+// tensor map) is in leaf_tc.cu, one instantiation per element type in
+// leaf_tc_f32.cu / leaf_tc_f16.cu / leaf_tc_u8.cu.
+// Every mbarrier wait is bounded; a CTA that gives up records the failure in
+// the error word, waits for its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
+#include "knng_common.cuh"
+#include "knng_internal.h"
+#include "tc_ptx.cuh"
+
+namespace knng {
+
+namespace {
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
+constexpr int kTcThreads = 256;  // 8 warps: warps w and w+4 share TMEM lanes 32(w%4)..+31
+constexpr int kTcWarps = kTcThreads / 32;
+constexpr int kTcCand = 128;
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// 1. leaf-order gather and quantisation
+// ---------------------------------------------------------------------------
+//     For bfloat16 every row also gets an exactness bit: set when all its
+//     entries are integers of magnitude <= 256 and its squared norm is below
+//     2^23.  Between two such rows every bfloat16 value, product and partial
+//     sum of the Gram is an integer below 2^24, exact in FP32, so the
+//     candidate distance |x|^2 + |y|^2 - 2 x.y equals the true squared
+//     distance, which is also what the canonical FP32 distance returns.
+template <int PREC, int kDT>
+__global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kDT> L, int64_t rows,
+                                                           const int32_t* __restrict__ perm, int dq,
+                                                           void* __restrict__ out, float* __restrict__ nrm,
+                                                           float* __restrict__ scl, uint8_t* __restrict__ exact)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = gw; r < rows; r += nw) {
+        const int32_t id = perm[r];
+        float s = 0.f;
+        bool ex = true;
+        if (PREC == 1) {
+            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + r * dq;
+            for (int j = 4 * lane; j < dq; j += 128) {
+                const float4 v = j < L.d ? L.load4(id, j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ex &= v.x == rintf(v.x) && v.y == rintf(v.y) && v.z == rintf(v.z) && v.w == rintf(v.w);
+                ex &= fabsf(v.x) <= 256.f && fabsf(v.y) <= 256.f && fabsf(v.z) <= 256.f && fabsf(v.w) <= 256.f;
+                __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+                __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+                const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+                s = fmaf(fa.x, fa.x, s); s = fmaf(fa.y, fa.y, s);
+                s = fmaf(fb.x, fb.x, s); s = fmaf(fb.y, fb.y, s);
+                uint2 u;
+                u.x = *reinterpret_cast<uint32_t*>(&a);
+                u.y = *reinterpret_cast<uint32_t*>(&b);
+                *reinterpret_cast<uint2*>(o + j) = u;
+            }
+        } else {
+            float mx = 0.f;
+            for (int j = 4 * lane; j < L.d; j += 128) {
+                const float4 v = L.load4(id, j);
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(KNNG_FULL_MASK, mx, o));
+            const float sc = mx > 0.f ? mx / 448.0f : 1.0f;
+            uint8_t* o = static_cast<uint8_t*>(out) + r * dq;
+            for (int j = 4 * lane; j < dq; j += 128) {
+                const float4 v = j < L.d ? L.load4(id, j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const __nv_fp8_e4m3 q0(v.x / sc), q1(v.y / sc), q2(v.z / sc), q3(v.w / sc);
+                const float f0 = float(q0), f1 = float(q1), f2 = float(q2), f3 = float(q3);
+                s = fmaf(f0, f0, s); s = fmaf(f1, f1, s); s = fmaf(f2, f2, s); s = fmaf(f3, f3, s);
+                const uint32_t u = (uint32_t)q0.__x | ((uint32_t)q1.__x << 8) | ((uint32_t)q2.__x << 16) |
+                                   ((uint32_t)q3.__x << 24);
+                *reinterpret_cast<uint32_t*>(o + j) = u;
+            }
+            if (lane == 0) scl[r] = sc;
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
+        ex = __all_sync(KNNG_FULL_MASK, ex);
+        if (lane == 0) {
+            nrm[r] = s;
+            exact[r] = (PREC == 1 && ex && s < 8388608.0f) ? 1 : 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Gram on tcgen05 + selection + rescoring
+// ---------------------------------------------------------------------------
+struct TcGeom {
+    int N_load;      // largest MMA N over the leaves (multiple of 16)
+    int R_load;      // rows loaded per K slice (multiple of 128)
+    int box_rows;    // rows per TMA box (<= 256)
+    int nbox;        // boxes per K slice
+    int nK;          // K slices of 128 bytes
+    int S;           // pipeline stages
+    int stage_bytes;
+    int RG;          // epilogue rows per group
+    int ldD;         // row stride of the distance block (floats)
+    int pipe_bytes;
+    int smem;
+};
+
+template <int PREC, int PER, int kDT>
+__global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                RowLoader<kDT> L, int64_t n,
+                                                                const int32_t* __restrict__ perm,
+                                                                const int32_t* __restrict__ leaf_off,
+                                                                int nleaves, const float* __restrict__ qnrm,
+                                                                const float* __restrict__ qscl,
+                                                                const uint8_t* __restrict__ qexact, int k, int kp,
+                                                                TcGeom G, int32_t* __restrict__ out_ids,
+                                                                float* __restrict__ out_d, int* err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* pipe = base;
+    float* Dblk = reinterpret_cast<float*>(pipe);
+    int32_t* lid = reinterpret_cast<int32_t*>(base + G.pipe_bytes);
+    float* qn = reinterpret_cast<float*>(lid + G.N_load);
+    float* qs = qn + G.N_load;
+    unsigned char* wsc = reinterpret_cast<unsigned char*>(((uintptr_t)(qs + G.N_load) + 15) & ~(uintptr_t)15);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsc + kTcWarps * kLeafWarpScratch);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + G.S;
+    uint64_t* done = bars + 2 * G.S;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int t = blockIdx.y;
+    const int RB = gridDim.x / nleaves;
+    const int leaf = blockIdx.x / RB;
+    const int r0 = (blockIdx.x % RB) * 128;
+    const int off = leaf_off[leaf];
+    const int m = leaf_off[leaf + 1] - off;
+    if (r0 >= m) return;
+    const int Nm = min(G.N_load, (m + 15) & ~15);
+    const int N0 = min(Nm, 256), N1 = Nm - N0;
+    uint32_t ncols = 32;
+    while ((int)ncols < Nm) ncols <<= 1;
+
+    if (tid == 0) {
+        for (int s = 0; s < G.S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_mbar_init();
+        abort_flag = 0;
+        tc::prefetch_tmap(&tmap);
+    }
+    if (w == 0) {
+        tc::tmem_alloc(tslot, ncols);
+        tc::tmem_relinquish();
+    }
+    const int64_t rowbase = (int64_t)t * n + off;
+    bool ex = PREC == 1;
+    for (int j = tid; j < G.N_load; j += kTcThreads) {
+        const bool v = j < m;
+        lid[j] = v ? perm[rowbase + j] : 0;
+        qn[j] = v ? qnrm[rowbase + j] : 0.f;
+        qs[j] = (PREC == 2 && v) ? qscl[rowbase + j] : 1.f;
+        if (v) ex = ex && qexact[rowbase + j];
+    }
+    tc::fence_before_sync();
+    // the whole leaf is exact: candidate distances are final, no rescoring
+    const bool exact_leaf = __syncthreads_and(ex) != 0;
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    // ---- producer + MMA issuer (one thread) ------------------------------
+    if (tid == 0) {
+        constexpr uint32_t fmt = PREC == 1 ? 1u : 0u;  // BF16 | E4M3
+        const uint32_t id0 = tc::make_idesc(fmt, 128, (uint32_t)N0);
+        const uint32_t id1 = tc::make_idesc(fmt, 128, (uint32_t)(N1 > 0 ? N1 : 16));
+        const int xstep = PREC == 1 ? 64 : 128;  // elements per 128-byte K slice
+        const int64_t yrow = rowbase;
+        int loaded = 0, consumed = 0;
+        bool ok = true;
+        auto load = [&](int kc) {
+            const int s = kc % G.S;
+            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(G.nbox * G.box_rows * 128));
+            for (int b = 0; b < G.nbox; ++b)
+                tc::tma_load_2d(pipe + (size_t)s * G.stage_bytes + (size_t)b * G.box_rows * 128, &tmap, &full[s],
+                                kc * xstep, (int)(yrow + (int64_t)b * G.box_rows));
+        };
+        for (; loaded < min(G.S, G.nK); ++loaded) load(loaded);
+        for (int kc = 0; kc < G.nK; ++kc) {
+            const int s = kc % G.S;
+            const uint32_t ph = (uint32_t)(kc / G.S) & 1u;
+            if (!tc::mbar_wait(&full[s], ph, kWaitCycles)) { ok = false; break; }
+            consumed = kc + 1;
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(pipe + (size_t)s * G.stage_bytes);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = tc::sw128_desc(sa + (uint32_t)r0 * 128u + (uint32_t)kk * 32u);
+                const uint64_t bd0 = tc::sw128_desc(sa + (uint32_t)kk * 32u);
+                const uint32_t acc = (kc | kk) ? 1u : 0u;
+                if (PREC == 1) tc::mma_f16(tbase, ad, bd0, id0, acc);
+                else tc::mma_f8(tbase, ad, bd0, id0, acc);
+                if (N1 > 0) {
+                    const uint64_t bd1 = tc::sw128_desc(sa + 256u * 128u + (uint32_t)kk * 32u);
+                    if (PREC == 1) tc::mma_f16(tbase + 256, ad, bd1, id1, acc);
+                    else tc::mma_f8(tbase + 256, ad, bd1, id1, acc);
+                }
+            }
+            tc::mma_commit(&empty[s]);
+            if (kc + G.S < G.nK) {
+                if (!tc::mbar_wait(&empty[s], ph, kWaitCycles)) { ok = false; break; }
+                load(kc + G.S);
+                ++loaded;
+            }
+        }
+        tc::mma_commit(done);
+        if (!ok) {
+            abort_flag = 1;
+            atomicExch(err, 1);
+            // wait (bounded) for the copies this CTA still has in flight
+            for (int kc = consumed; kc < loaded; ++kc)
+                tc::mbar_wait(&full[kc % G.S], (uint32_t)(kc / G.S) & 1u, kWaitCycles);
+        }
+    }
+    __syncthreads();
+    if (!tc::mbar_wait(done, 0, kWaitCycles)) {
+        abort_flag = 1;
+        atomicExch(err, 1);
+    }
+    tc::fence_after_sync();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // pipeline smem is reused below
+    __syncthreads();
+
+    // ---- epilogue: TMEM -> distance block -> per-row selection ----------
+    if (!abort_flag) {
+        const int ldD = G.ldD;
+        const int quad = w & 3, half = w >> 2;
+        for (int g0 = 0; g0 < 128 && r0 + g0 < m; g0 += G.RG) {
+            if (32 * quad >= g0 && 32 * quad < g0 + G.RG) {
+                const int lr = 32 * quad + lane;
+                const int il = min(r0 + lr, G.N_load - 1);
+                const float ni = qn[il], si = qs[il];
+                float* drow = Dblk + (size_t)(lr - g0) * ldD;
+                for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, r);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int j = min(c0 + e, G.N_load - 1);
+                        const float sdot = __uint_as_float(r[e]);
+                        float dv;
+                        if (PREC == 1) dv = ni + qn[j] - 2.f * sdot;
+                        else dv = si * si * ni + qs[j] * qs[j] * qn[j] - 2.f * si * qs[j] * sdot;
+                        drow[c0 + e] = dv;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int rr = w; rr < G.RG && g0 + rr < 128; rr += kTcWarps) {
+                const int iloc = r0 + g0 + rr;
+                if (iloc >= m) break;
+                const float* drow = Dblk + (size_t)rr * ldD;
+                const int gi = lid[iloc];
+                leaf_row_finish<PER, kDT>(L, [&](int j) { return drow[j]; }, m, iloc, lid, k, exact_leaf ? k : kp,
+                                      wsc + (size_t)kLeafWarpScratch * w, out_ids + ((int64_t)t * n + gi) * k,
+                                      out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
+            }
+            __syncthreads();
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
+template <int PREC, int PER, int kDT>
+static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                             const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
+                             const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
+{
+    auto kern = leaf_tc_kernel<PREC, PER, kDT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
+    if (e != cudaSuccess) return e;
+    RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
+    const int nleaves = (int)P.leaf_off.size() - 1;
+    const int RB = (P.max_leaf + 127) / 128;
+    kern<<<dim3(nleaves * RB, T), kTcThreads, G.smem, st>>>(map, rl, x.n, perm, dp.leaf_off, nleaves, qn, qs, qx, k, kp,
+                                                            G, ids, dists, err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <int PREC, int kDT>
+static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                               const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
+                               const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
+{
+    // keys per lane in the row selection: leaves of up to 32 * PER points
+    if (P.max_leaf <= 128) return launch_tc<PREC, 4, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    if (P.max_leaf <= 256) return launch_tc<PREC, 8, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    return launch_tc<PREC, 16, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+}
+
+// Gather + quantise the leaf-ordered copy, then the leaf kernel, for one
+// element type of X (explicitly instantiated per type).
+template <int kDT>
+cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                        const int32_t* perm, int dq, void* Xq, float* qn, float* qs, uint8_t* qx, int k, int kp,
+                        const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
+{
+    const int64_t rows = (int64_t)T * x.n;
+    const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);
+    RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
+    if (prec == 1) gather_quant_kernel<1, kDT><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
+    else gather_quant_kernel<2, kDT><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (prec == 1) return dispatch_tc<1, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    return dispatch_tc<2, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+}
+
+}  // namespace knng

@@ -113,8 +113,8 @@ static void gemm(int M, int N, int K, const float* A, int lda, const float* B, i
 // Batch sampling: edge b takes a Philox-random point i and a random valid
 // slot of its list; row b of Xb is x_i, row B + b is x_j (FP32).
 // ---------------------------------------------------------------------------
-template <bool kF16>
-__global__ void sample_batch_kernel(RowLoader<kF16> L, int64_t n, const int32_t* __restrict__ ids, int k, int B,
+template <int kDT>
+__global__ void sample_batch_kernel(RowLoader<kDT> L, int64_t n, const int32_t* __restrict__ ids, int k, int B,
                                     uint64_t seed, uint32_t step, float* __restrict__ Xb)
 {
     const int lane = threadIdx.x & 31;
@@ -483,7 +483,7 @@ int knng_mlp_train(knng_mlp* o, const void* X, int32_t dtype, int64_t n, int32_t
                    void* stream)
 {
     if (!o || !X || !ids || n < 2 || k < 1 || steps < 0 || batch_edges < 2 || lr <= 0.f) return KNNG_ERR_INVALID_ARG;
-    if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16) return KNNG_ERR_INVALID_ARG;
+    if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16 && dtype != KNNG_DTYPE_U8) return KNNG_ERR_INVALID_ARG;
     MlpModel& M = o->m;
     if (d != M.d || ld < d || ld >= (int64_t)1 << 31 || n >= (int64_t)1 << 31) return KNNG_ERR_INVALID_ARG;
     int prev = 0;
@@ -491,17 +491,20 @@ int knng_mlp_train(knng_mlp* o, const void* X, int32_t dtype, int64_t n, int32_t
     cudaSetDevice(M.device);
     int rc = ensure_rows(&M, 2 * batch_edges);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t es = dtype == KNNG_DTYPE_F16 ? 2 : 4;
-    const size_t align = dtype == KNNG_DTYPE_F16 ? 8 : 16;
+    const size_t es = dtype == KNNG_DTYPE_F16 ? 2 : dtype == KNNG_DTYPE_U8 ? 1 : 4;
+    const size_t align = dtype == KNNG_DTYPE_F16 ? 8 : dtype == KNNG_DTYPE_U8 ? 4 : 16;
     const bool vec = ((uintptr_t)X % align == 0) && ((size_t)ld * es % align == 0);
     for (int s = 0; s < steps && rc == KNNG_OK; ++s) {
         const int blocks = (batch_edges * 32 + 255) / 256;
         if (dtype == KNNG_DTYPE_F16) {
-            RowLoader<true> L{X, ld, d, vec};
-            sample_batch_kernel<true><<<blocks, 256, 0, st>>>(L, n, ids, k, batch_edges, seed, (uint32_t)s, M.Xb);
+            RowLoader<kDtF16> L{X, ld, d, vec};
+            sample_batch_kernel<kDtF16><<<blocks, 256, 0, st>>>(L, n, ids, k, batch_edges, seed, (uint32_t)s, M.Xb);
+        } else if (dtype == KNNG_DTYPE_U8) {
+            RowLoader<kDtU8> L{X, ld, d, vec};
+            sample_batch_kernel<kDtU8><<<blocks, 256, 0, st>>>(L, n, ids, k, batch_edges, seed, (uint32_t)s, M.Xb);
         } else {
-            RowLoader<false> L{X, ld, d, vec};
-            sample_batch_kernel<false><<<blocks, 256, 0, st>>>(L, n, ids, k, batch_edges, seed, (uint32_t)s, M.Xb);
+            RowLoader<kDtF32> L{X, ld, d, vec};
+            sample_batch_kernel<kDtF32><<<blocks, 256, 0, st>>>(L, n, ids, k, batch_edges, seed, (uint32_t)s, M.Xb);
         }
         note_launches(1);
         cudaError_t e = loss_grad(&M, M.Xb, batch_edges, st);

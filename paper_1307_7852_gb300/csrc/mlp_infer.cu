@@ -37,8 +37,8 @@ __device__ __forceinline__ float gelu_inf(float a)
     return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f));
 }
 
-template <bool kF16, int C>
-__global__ void __launch_bounds__(128, 1) mlp_infer_kernel(RowLoader<kF16> L, int64_t n, const uint8_t* __restrict__ img,
+template <int kDT, int C>
+__global__ void __launch_bounds__(128, 1) mlp_infer_kernel(RowLoader<kDT> L, int64_t n, const uint8_t* __restrict__ img,
                                                            int K1pad, int H, const float* __restrict__ b1,
                                                            const float* __restrict__ b2, float* __restrict__ Z,
                                                            int* err)
@@ -214,18 +214,20 @@ cudaError_t run_mlp_forward(MlpModel& M, const XDesc& x, float* Z, int* err, cud
     const int64_t tiles = (x.n + 127) / 128;
     const int grid = (int)std::min<int64_t>(tiles, num_sms());
     cudaError_t e;
-#define KNNG_MLP_LAUNCH(F16, CC)                                                                                     \
+#define KNNG_MLP_LAUNCH(DT, CC)                                                                                      \
     {                                                                                                                \
-        auto kern = mlp_infer_kernel<F16, CC>;                                                                       \
+        auto kern = mlp_infer_kernel<DT, CC>;                                                                        \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
         if (e != cudaSuccess) return e;                                                                              \
-        RowLoader<F16> rl{x.X, x.ld, x.d, x.vec};                                                                    \
+        RowLoader<DT> rl{x.X, x.ld, x.d, x.vec};                                                                     \
         kern<<<grid, 128, smem, st>>>(rl, x.n, static_cast<const uint8_t*>(M.img), K1pad, M.H, M.b1(), M.b2(), Z, err); \
     }
-    if (x.dtype == 1) {
-        if (M.C == 16) KNNG_MLP_LAUNCH(true, 16) else KNNG_MLP_LAUNCH(true, 32)
+    if (x.dtype == kDtF16) {
+        if (M.C == 16) KNNG_MLP_LAUNCH(kDtF16, 16) else KNNG_MLP_LAUNCH(kDtF16, 32)
+    } else if (x.dtype == kDtU8) {
+        if (M.C == 16) KNNG_MLP_LAUNCH(kDtU8, 16) else KNNG_MLP_LAUNCH(kDtU8, 32)
     } else {
-        if (M.C == 16) KNNG_MLP_LAUNCH(false, 16) else KNNG_MLP_LAUNCH(false, 32)
+        if (M.C == 16) KNNG_MLP_LAUNCH(kDtF32, 16) else KNNG_MLP_LAUNCH(kDtF32, 32)
     }
 #undef KNNG_MLP_LAUNCH
     note_launches(1);

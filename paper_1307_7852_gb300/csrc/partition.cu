@@ -18,6 +18,8 @@
 // in canonical order without a final sort.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "knng_common.cuh"
 #include "knng_internal.h"
 
@@ -255,12 +257,11 @@ void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf)
 // One warp per point; up to 8 trees per pass over the row.  The projection
 // order is the canonical one: lane l, j = 128c + 4l + e, fmaf, then the
 // pairwise rounds 16..1.
-template <bool kF16, bool kLearned>
-__global__ void __launch_bounds__(256) project_kernel(RowLoader<kF16> L, int64_t n, int T,
-                                                      const float* __restrict__ dirs, int S,
-                                                      int d_pad, const int32_t* __restrict__ node_of,
-                                                      const int32_t* __restrict__ pos_of,
-                                                      uint32_t* __restrict__ keys, LevelFeat lv)
+template <bool kLearned, class Loader>
+__device__ __forceinline__ void project_body(const Loader& L, int64_t n, int T, const float* __restrict__ dirs,
+                                             int S, int d_pad, const int32_t* __restrict__ node_of,
+                                             const int32_t* __restrict__ pos_of, uint32_t* __restrict__ keys,
+                                             const LevelFeat& lv)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -317,6 +318,25 @@ __global__ void __launch_bounds__(256) project_kernel(RowLoader<kF16> L, int64_t
             }
         }
     }
+}
+
+// Float rows whose byte copy is exact (*xb_bad == 0, see XDesc) are read from
+// the copy: the same float values, a quarter of the bytes.
+template <int kDT, bool kLearned>
+__global__ void __launch_bounds__(256) project_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
+                                                      const int* __restrict__ xb_bad, int64_t n, int T,
+                                                      const float* __restrict__ dirs, int S, int d_pad,
+                                                      const int32_t* __restrict__ node_of,
+                                                      const int32_t* __restrict__ pos_of,
+                                                      uint32_t* __restrict__ keys, LevelFeat lv)
+{
+    if constexpr (kDT == kDtF32) {
+        if (xb_bad && *xb_bad == 0) {
+            project_body<kLearned>(Lb, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
+            return;
+        }
+    }
+    project_body<kLearned>(L, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
 }
 
 // ---- block radix select (one block, keys in shared memory) ---------------
@@ -679,15 +699,20 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
             dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed);
         note_launches(1);
         const int pgrid = grid_for(n * 32, 256, sms * 16);
-        if (x.dtype == 1) {
-            RowLoader<true> rl{x.X, x.ld, x.d, x.vec};
-            if (learned) project_kernel<true, true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
-            else project_kernel<true, false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
-        } else {
-            RowLoader<false> rl{x.X, x.ld, x.d, x.vec};
-            if (learned) project_kernel<false, true><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
-            else project_kernel<false, false><<<pgrid, 256, 0, st>>>(rl, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
-        }
+        auto project = [&](auto dt) {
+            constexpr int kDT = decltype(dt)::value;
+            RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
+            const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
+            if (learned)
+                project_kernel<kDT, true><<<pgrid, 256, 0, st>>>(rl, rb, x.xb_bad, n, T, dirs, S, d_pad, node_of, pos_of,
+                                                                 keys, lv);
+            else
+                project_kernel<kDT, false><<<pgrid, 256, 0, st>>>(rl, rb, x.xb_bad, n, T, dirs, S, d_pad, node_of, pos_of,
+                                                                  keys, lv);
+        };
+        if (x.dtype == kDtF16) project(std::integral_constant<int, kDtF16>{});
+        else if (x.dtype == kDtU8) project(std::integral_constant<int, kDtU8>{});
+        else project(std::integral_constant<int, kDtF32>{});
         note_launches(1);
         // leaves of this level keep their positions: start from a copy
         cudaMemcpyAsync(nxt, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);

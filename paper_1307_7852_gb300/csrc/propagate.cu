@@ -14,7 +14,9 @@
 //    was a candidate of p in the previous round, so either c is in p's list
 //    or k listed points beat it, and it cannot enter the new list.
 //  * Scoring: 16 candidates at a time by warp_canon_dist16 (coalesced 16-byte
-//    row loads, 16 rows in flight per warp, bit-identical canonical FP32).
+//    row loads, 16 rows in flight per warp, bit-identical canonical FP32);
+//    float rows holding only bytes are scored on their exact byte copy in
+//    integer arithmetic (4-byte loads, the same values).
 //  * The k best by (dist, id): warp radix select and a warp bitonic sort; the
 //    output flags mark the entries that were not in p's input list.
 #include "knng_common.cuh"
@@ -54,8 +56,9 @@ static PropLayout prop_layout(int k)
     return L;
 }
 
-template <int E, bool kF16>
-__global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(RowLoader<kF16> L, int64_t n, int k, const int32_t* __restrict__ order,
+template <int E, int kDT>
+__global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
+                                 const int* __restrict__ xb_bad, int64_t n, int k, const int32_t* __restrict__ order,
                                  const int32_t* __restrict__ ids_in, const float* __restrict__ d_in,
                                  const unsigned long long* __restrict__ flags_in, int32_t* __restrict__ ids_out,
                                  float* __restrict__ d_out, unsigned long long* __restrict__ flags_out, int H,
@@ -74,6 +77,9 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
     uint64_t* keys = reinterpret_cast<uint64_t*>(own_fl + 64);
     const uint32_t hmask = (uint32_t)H - 1;
     const int kk = k * k;
+    // float rows with an exact byte copy: score on the copy (same values)
+    bool bytes = false;
+    if constexpr (kDT == kDtF32) bytes = xb_bad && *xb_bad == 0;
 
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -140,7 +146,9 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         // score the new candidates, 32 at a time
         for (int c0 = nknown; c0 < cnt; c0 += 16) {
             const int nb = min(16, cnt - c0);
-            const float dd = warp_canon_dist16(L, p, cid + c0, nb);
+            float dd;
+            if (kDT == kDtF32 && bytes) dd = warp_canon_dist16(Lb, p, cid + c0, nb);
+            else dd = warp_canon_dist16(L, p, cid + c0, nb);
             if (lane < nb) cd[c0 + lane] = dd;
         }
         __syncwarp();
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
     }
 }
 
-template <int E, bool kF16>
+template <int E, int kDT>
 static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                                const unsigned long long* fin, int32_t* ids, float* dists, unsigned long long* fout,
                                cudaStream_t st)
@@ -207,7 +215,7 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     if (warps > 8) warps = 8;
     if (warps < 1) return cudaErrorInvalidConfiguration;
     const size_t smem = PL.per_warp * warps;
-    auto kern = propagate_kernel<E, kF16>;
+    auto kern = propagate_kernel<E, kDT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -216,28 +224,30 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     int64_t blocks = (int64_t)num_sms() * per_sm;
     const int64_t need = (x.n + warps - 1) / warps;
     if (blocks > need) blocks = need;
-    RowLoader<kF16> rl{x.X, x.ld, x.d, x.vec};
-    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
+    RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
+    const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
+    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
                                                 PL.hshift, PL.cap, (int)PL.per_warp);
     note_launches(1);
     return cudaGetLastError();
 }
 
-template <bool kF16>
+template <int kDT>
 static cudaError_t prop_dispatch(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
                                  const float* d_in, const unsigned long long* fin, int32_t* ids, float* dists,
                                  unsigned long long* fout, cudaStream_t st)
 {
-    if (k <= 32) return launch_prop<1, kF16>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
-    return launch_prop<2, kF16>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
+    if (k <= 32) return launch_prop<1, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
+    return launch_prop<2, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
 }
 
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
                           unsigned long long* flags_out, cudaStream_t st)
 {
-    if (x.dtype == 1) return prop_dispatch<true>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
-    return prop_dispatch<false>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
+    if (x.dtype == kDtF16) return prop_dispatch<kDtF16>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
+    if (x.dtype == kDtU8) return prop_dispatch<kDtU8>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
+    return prop_dispatch<kDtF32>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
 }
 
 }  // namespace knng
