@@ -65,6 +65,16 @@ extern "C" {
 
 #define KNNG_PART_RANDOM 0  /* Philox random directions (the only value knng_build takes) */
 
+/* Distance.  L2: the squared Euclidean distance.  COSINE: 1 - cos of the
+ * angle between two rows (App. after Lemma 1: random projections partition
+ * for the cosine distance too).  For COSINE the rows are first scaled to
+ * unit length in FP32 (knng_normalize_rows) and the method runs on the unit
+ * rows u, whose |u - v|^2 / 2 is 1 - cos; a zero row stays zero (distance
+ * 1/2 to every unit row).  The scaled copy takes n * round_up(d, 4) floats
+ * of the workspace. */
+#define KNNG_METRIC_L2 0
+#define KNNG_METRIC_COSINE 1
+
 /* ---- parameters ------------------------------------------------------ */
 typedef struct knng_params {
     int32_t k;            /* neighbours per point, 1 <= k <= 64, k < leaf_size/2     */
@@ -75,7 +85,7 @@ typedef struct knng_params {
     int32_t precision;    /* KNNG_PREC_*                                             */
     int32_t rescore_mult; /* k' = rescore_mult * k candidates per leaf row, 1..4     */
     int32_t partitioner;  /* KNNG_PART_RANDOM                                        */
-    int32_t reserved;     /* must be 0                                               */
+    int32_t metric;       /* KNNG_METRIC_L2 or KNNG_METRIC_COSINE                    */
 } knng_params;
 
 typedef struct knng_handle knng_handle;
@@ -265,6 +275,15 @@ int knng_propagate_noalloc(const void* X, int32_t dtype, int64_t n, int32_t d, i
                            float* dists, void* stream);
 
 /* ---- measurement ----------------------------------------------------- */
+/* Scales every row of X[n][d] to unit length in FP32 and writes it to the
+ * device array Xn (rows of ldn >= d floats; entries d..ldn-1 set to 0): the
+ * squared norm is summed in the canonical order of the projection (lane
+ * partials over j = 128c + 4l + e, pairwise rounds 16, 8, 4, 2, 1), then
+ * sqrtf and one division per entry (IEEE).  A zero row stays zero.  This is
+ * the first step of KNNG_METRIC_COSINE. */
+int knng_normalize_rows(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld, float* Xn,
+                        int64_t ldn, void* stream);
+
 /* Exact k-NN lists (Def. 1) of nq query points against all n points, by
  * brute force with the same FP32 distance as the graph (the yardstick of the
  * accuracy measure of Sec. 4).  queries: device int32 [nq] point ids;

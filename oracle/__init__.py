@@ -34,6 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
+METRIC_L2, METRIC_COSINE = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +73,7 @@ def _load():
             lib.orc_propagate.argtypes = [P, i64, i32, i64, i32, P, P, P]
             lib.orc_knn_exact.argtypes = [P, i64, i32, i64, i32, P, i64, P, P]
             lib.orc_pair_dist.argtypes = [P, i32, i64, P, P, i64, P]
+            lib.orc_normalize_rows.argtypes = [P, i64, i32, i64, P]
             lib.orc_bf16_round.argtypes = [ctypes.c_float]
             lib.orc_bf16_round.restype = ctypes.c_float
             lib.orc_e4m3_round.argtypes = [ctypes.c_float]
@@ -239,9 +241,25 @@ def pair_dist(X, a, b) -> np.ndarray:
 
 
 # ------------------------------------------------------------ whole method --
+def normalize_rows(X) -> np.ndarray:
+    """Rows scaled to unit length in FP32 (the cosine metric's input)."""
+    X = _as_f32(X)
+    n, d = X.shape
+    out = np.empty((n, d), dtype=np.float32)
+    _load().orc_normalize_rows(_ptr(X), n, d, X.strides[0] // 4, _ptr(out))
+    return out
+
+
 def build_graph(X, k: int, T: int, g: int, R: int, seed: int,
-                precision: int = PREC_FP32, rescore_mult: int = 2):
-    """T random divisions, leaf graphs, merge, then R propagation rounds."""
+                precision: int = PREC_FP32, rescore_mult: int = 2, metric: int = METRIC_L2):
+    """T random divisions, leaf graphs, merge, then R propagation rounds.
+
+    metric = METRIC_COSINE: the same method on the rows scaled to unit length
+    (normalize_rows), distances halved: 1 - cos of the scaled rows.
+    """
+    if metric == METRIC_COSINE:
+        ids, dists = build_graph(normalize_rows(X), k, T, g, R, seed, precision, rescore_mult)
+        return ids, (dists * np.float32(0.5)).astype(np.float32)
     X = _as_f32(X)
     n = X.shape[0]
     lists = np.empty((T, n, k), dtype=np.int32)

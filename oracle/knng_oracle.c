@@ -447,6 +447,28 @@ int orc_pair_dist(const float* X, int d, int64_t ld, const int32_t* a, const int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Cosine metric (App., after the proof of Lemma 1: for the cosine distance  */
+/* a random projection builds the partition tree).  Every row is scaled to  */
+/* unit length in FP32: its squared norm in the fixed order of orc_project  */
+/* (the row itself in place of the direction), the IEEE square root, one    */
+/* IEEE division per entry.  A zero row stays zero.  The cosine distance of */
+/* two rows, 1 - cos, is then |u - v|^2 / 2 over the scaled rows u, v, so   */
+/* the method runs unchanged on the scaled rows and halves the distances.   */
+/* ------------------------------------------------------------------------ */
+int orc_normalize_rows(const float* X, int64_t n, int d, int64_t ld, float* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const float* x = X + i * ld;
+        float* u = out + i * (int64_t)d;
+        const float s = orc_project(x, x, d);
+        const float r = sqrtf(s);
+        for (int j = 0; j < d; ++j) u[j] = s > 0.0f ? x[j] / r : 0.0f;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Reduced-precision encodings of the candidate stage.                      */
 /* ------------------------------------------------------------------------ */
 

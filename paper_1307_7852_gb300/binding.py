@@ -21,6 +21,7 @@ KNNG_OK = 0
 DTYPE_F32, DTYPE_F16, DTYPE_U8 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 PART_RANDOM = 0
+METRIC_L2, METRIC_COSINE = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -43,7 +44,7 @@ class knng_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("T", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("prop_rounds", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("rescore_mult", ctypes.c_int32),
-                ("partitioner", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("partitioner", ctypes.c_int32), ("metric", ctypes.c_int32)]
 
 
 # exported entry points -> argtypes
@@ -61,6 +62,7 @@ SIGNATURES = {
     "knng_leaf_knn": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _I32, _I32, _I32, _P, _P, _P],
     "knng_merge": [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P],
     "knng_propagate": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
+    "knng_normalize_rows": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _P],
     "knng_exact_knn": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _I32, _P, _P, _P],
     "knng_set_stage_events": [_P, _P, _I32],
     "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
@@ -191,9 +193,9 @@ def _ptr(t):
 
 
 def make_params(k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
-                partitioner=PART_RANDOM) -> knng_params:
+                partitioner=PART_RANDOM, metric=0) -> knng_params:
     return knng_params(int(k), int(T), int(leaf_size), int(prop_rounds), int(seed) & (2**64 - 1),
-                       int(precision), int(rescore_mult), int(partitioner), 0)
+                       int(precision), int(rescore_mult), int(partitioner), int(metric))
 
 
 # ----------------------------------------------------------- entry points --
@@ -214,13 +216,13 @@ def knng_leaf_offsets(n: int, leaf_size: int) -> np.ndarray:
 
 
 def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
-               ids=None, dists=None, stream=None, h: Handle = None):
+               ids=None, dists=None, stream=None, h: Handle = None, metric: int = METRIC_L2):
     torch = _torch()
     xp, dt, n, d, ld = _xdesc(X)
     h = h or handle(X.device.index or 0)
     ids = _out((n, k), torch.int32, X.device, ids)
     dists = _out((n, k), torch.float32, X.device, dists)
-    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric)
     h.check(lib().knng_build(h.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
                              _stream(X.device, stream)), "knng_build")
     return ids, dists
@@ -228,7 +230,7 @@ def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, resco
 
 def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32,
                     rescore_mult=2, ids=None, dists=None, stream=None, device: int = 0,
-                    h: Handle = None):
+                    h: Handle = None, metric: int = METRIC_L2):
     """Host arrays in and out (X float32/float16/uint8 [n, d], unit stride along d)."""
     X = np.asarray(X)
     if X.ndim != 2 or X.strides[1] != X.itemsize:
@@ -244,7 +246,7 @@ def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision
     if dists is None:
         dists = np.empty((n, k), dtype=np.float32)
     h = h or handle(device)
-    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric)
     torch = _torch()
     st = _stream(torch.device("cuda", device), stream)
     h.check(lib().knng_build_host(h.ptr, ctypes.c_void_p(X.ctypes.data), dt, n, d, ld, ctypes.byref(p),
@@ -308,6 +310,17 @@ def knng_propagate(X, ids_in, dists_in, rounds=1, ids=None, dists=None, stream=N
     return ids, dists
 
 
+def knng_normalize_rows(X, out=None, stream=None, h: Handle = None):
+    """Rows of X (CUDA tensor) scaled to unit length in FP32 (cosine metric)."""
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    out = _out((n, d), torch.float32, X.device, out)
+    h.check(lib().knng_normalize_rows(h.ptr, xp, dt, n, d, ld, _ptr(out), d, _stream(X.device, stream)),
+            "knng_normalize_rows")
+    return out
+
+
 def knng_exact_knn(X, queries, k, ids=None, dists=None, stream=None, h: Handle = None):
     """Exact k-NN lists of the query ids (device int32 [nq]) against all points."""
     torch = _torch()
@@ -368,7 +381,7 @@ def knng_propagate_noalloc(X, ids_in, dists_in, rounds=1, ids=None, dists=None, 
 
 
 def knng_build_batched(Xs, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
-                       outs=None, stream=None, h: Handle = None):
+                       outs=None, stream=None, h: Handle = None, metric: int = METRIC_L2):
     """Graphs of many independent point sets (CUDA tensors) in one recorded
     launch; returns a list of (ids, dists) per set."""
     torch = _torch()
@@ -385,7 +398,7 @@ def knng_build_batched(Xs, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP
         od = _out((n, k), torch.float32, dev, od)
         arr[i] = knng_dataset(xp.value, dt, d, n, ld, oi.data_ptr(), od.data_ptr())
         res.append((oi, od))
-    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric)
     h.check(lib().knng_build_batched(h.ptr, len(Xs), arr, ctypes.byref(p), _stream(dev, stream)),
             "knng_build_batched")
     return res

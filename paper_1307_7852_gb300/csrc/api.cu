@@ -239,7 +239,8 @@ int check_params(knng_handle* h, const knng_params* p, int64_t n)
     if (p->prop_rounds < 0 || p->prop_rounds > 16) return fail(h, KNNG_ERR_INVALID_ARG, "prop_rounds %d", p->prop_rounds);
     if (p->rescore_mult < 1 || p->rescore_mult > 4) return fail(h, KNNG_ERR_INVALID_ARG, "rescore_mult %d", p->rescore_mult);
     if (p->partitioner != KNNG_PART_RANDOM) return fail(h, KNNG_ERR_UNSUPPORTED, "partitioner %d", p->partitioner);
-    if (p->reserved != 0) return fail(h, KNNG_ERR_INVALID_ARG, "reserved must be 0");
+    if (p->metric != KNNG_METRIC_L2 && p->metric != KNNG_METRIC_COSINE)
+        return fail(h, KNNG_ERR_INVALID_ARG, "metric %d", p->metric);
     return KNNG_OK;
 }
 
@@ -266,11 +267,22 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         bd[b] = a.take<float>(nk);
         fl[b] = a.take<unsigned long long>(n);
     }
+    // cosine metric: the method runs on the rows scaled to unit length
+    const bool cosine = p.metric == KNNG_METRIC_COSINE;
+    if (cosine) {
+        const int64_t ldn = ((int64_t)x.d + 3) & ~(int64_t)3;
+        float* xn = a.take<float>((size_t)n * ldn);
+        if (a.base) {
+            const cudaError_t e = run_normalize_rows(x, xn, ldn, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "normalize rows");
+        }
+        x = XDesc{xn, KNNG_DTYPE_F32, n, x.d, ldn, true};
+    }
     // float rows that hold only bytes: exact byte copy for the gathering kernels
     uint8_t* xb = nullptr;
     int* xb_bad = nullptr;
     const int64_t ldb = ((int64_t)x.d + 15) & ~(int64_t)15;
-    if (byte_copy && x.dtype == KNNG_DTYPE_F32 && x.d <= 256) {
+    if (byte_copy && !cosine && x.dtype == KNNG_DTYPE_F32 && x.d <= 256) {
         xb = a.take<uint8_t>((size_t)n * ldb);
         xb_bad = a.take<int>(1);
     }
@@ -324,6 +336,11 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
         mark(4 + rd);
+    }
+    if (cosine) {
+        // |u - v|^2 / 2 = 1 - cos between unit rows (exact halving)
+        e = run_scale(dists, (int64_t)nk, 0.5f, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cosine distances");
     }
     return KNNG_OK;
 }
@@ -539,6 +556,20 @@ int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t 
     Arena a;
     a.base = h->ws;
     return build_pipeline(h, h->plan, h->dplan, x, *p, ids, dists, a, st, true, nullptr, true);
+}
+
+int knng_normalize_rows(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld, float* Xn,
+                        int64_t ldn, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    if (!Xn) return fail(h, KNNG_ERR_INVALID_ARG, "NULL output");
+    if (ldn < d) return fail(h, KNNG_ERR_INVALID_ARG, "ldn = %lld < d", (long long)ldn);
+    DeviceGuard dg(h->device);
+    const cudaError_t e = run_normalize_rows(x, Xn, ldn, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "normalize rows");
+    return KNNG_OK;
 }
 
 int knng_exact_knn(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
@@ -908,6 +939,7 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     if (!M || !ids || !dists) return fail(h, KNNG_ERR_INVALID_ARG, "NULL network or output");
     if (M->d != d) return fail(h, KNNG_ERR_INVALID_ARG, "network input %d != d %d", M->d, d);
     if (d > 128) return fail(h, KNNG_ERR_UNSUPPORTED, "tensor-core inference supports d <= 128");
+    if (q.metric != KNNG_METRIC_L2) return fail(h, KNNG_ERR_UNSUPPORTED, "learned splits use the L2 metric");
     if (q.T > 32) return fail(h, KNNG_ERR_INVALID_ARG, "T");
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -178,6 +178,11 @@ cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const floa
 // an integer in [0, 255].  *bad must be 0 on entry.
 cudaError_t run_byte_copy(const XDesc& x, uint8_t* Xb, int64_t ldb, int* bad, cudaStream_t st);
 
+// Cosine metric: rows scaled to unit length (FP32, out rows of ldo floats),
+// and an in-place scale of n floats.
+cudaError_t run_normalize_rows(const XDesc& x, float* out, int64_t ldo, cudaStream_t st);
+cudaError_t run_scale(float* v, int64_t cnt, float f, cudaStream_t st);
+
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
                           unsigned long long* flags_out, cudaStream_t st);

@@ -404,3 +404,48 @@ def test_build_recall_grows_with_trees_and_propagation():
     r4 = oracle.recall(X, oracle.build_graph(X, k, 4, 64, 0, 2)[0], k, sample, exact)[0]
     r4p = oracle.recall(X, oracle.build_graph(X, k, 4, 64, 1, 2)[0], k, sample, exact)[0]
     assert r1 < r4 < r4p <= 1.0
+
+
+# ------------------------------------------------------------ cosine metric --
+def test_normalize_rows_pins():
+    rng = np.random.default_rng(41)
+    X = rng.normal(size=(300, 37)).astype(np.float32)
+    X[7] = 0.0
+    U = oracle.normalize_rows(X)
+    nrm = np.linalg.norm(U.astype(np.float64), axis=1)
+    live = np.ones(300, bool)
+    live[7] = False
+    assert np.all(np.abs(nrm[live] - 1.0) < 4e-7)
+    assert np.all(U[7] == 0.0)
+    # each entry is the FP32 rounding of x_j / |x| up to the rounding of |x|
+    ref = X.astype(np.float64) / np.linalg.norm(X.astype(np.float64), axis=1, keepdims=True).clip(1e-300)
+    assert np.max(np.abs(U[live] - ref[live]) / np.abs(ref[live]).clip(1e-30)) < 3e-7
+    # scaling a row by a power of two leaves its unit row bit-identical
+    S = X * (2.0 ** rng.integers(-20, 20, size=(300, 1))).astype(np.float32)
+    np.testing.assert_array_equal(oracle.normalize_rows(S), U)
+
+
+def test_cosine_graph_is_brute_force_cosine_on_one_leaf():
+    # one leaf holding every point (g >= n), no propagation: the cosine
+    # graph must be the textbook one, 1 - x.y / (|x| |y|) in FP64
+    rng = np.random.default_rng(42)
+    n, d, k = 250, 24, 9
+    X = (rng.normal(size=(n, d)) * rng.uniform(0.1, 10.0, size=(n, 1))).astype(np.float32)
+    ids, dists = oracle.build_graph(X, k, 1, 256, 0, 3, metric=oracle.METRIC_COSINE)
+    Xd = X.astype(np.float64)
+    nx = np.linalg.norm(Xd, axis=1)
+    C = 1.0 - (Xd @ Xd.T) / np.outer(nx, nx)
+    np.fill_diagonal(C, np.inf)
+    want = np.argsort(C, axis=1, kind="stable")[:, :k]
+    np.testing.assert_array_equal(ids, want)
+    np.testing.assert_allclose(dists, np.take_along_axis(C, want, axis=1), rtol=2e-6)
+
+
+def test_cosine_graph_is_scale_invariant():
+    X = synthetic.gist_like(1500, 40, centers=12, seed=5)
+    rng = np.random.default_rng(43)
+    S = (X * (2.0 ** rng.integers(-6, 7, size=(1500, 1)))).astype(np.float32)
+    a = oracle.build_graph(X, 8, 2, 48, 1, 4, metric=oracle.METRIC_COSINE)
+    b = oracle.build_graph(S, 8, 2, 48, 1, 4, metric=oracle.METRIC_COSINE)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
