@@ -35,6 +35,7 @@ _lib = None
 
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 METRIC_L2, METRIC_COSINE = 0, 1
+PROP_FIRST_ORDER, PROP_BEST_FIRST, PROP_PAIRWISE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -74,6 +75,10 @@ def _load():
             lib.orc_knn_exact.argtypes = [P, i64, i32, i64, i32, P, i64, P, P]
             lib.orc_pair_dist.argtypes = [P, i32, i64, P, P, i64, P]
             lib.orc_normalize_rows.argtypes = [P, i64, i32, i64, P]
+            lib.orc_canon_dist32.argtypes = [P, P, i32]
+            lib.orc_canon_dist32.restype = ctypes.c_float
+            lib.orc_propagate_best_first.argtypes = [P, i64, i32, i64, i32, P, i32, P, P]
+            lib.orc_propagate_pairwise.argtypes = [P, i64, i32, i64, i32, P, P, P]
             lib.orc_bf16_round.argtypes = [ctypes.c_float]
             lib.orc_bf16_round.restype = ctypes.c_float
             lib.orc_e4m3_round.argtypes = [ctypes.c_float]
@@ -218,6 +223,53 @@ def propagate(X, ids_in, k: int):
     return ids, dists
 
 
+def canon_dist32(x, y) -> np.float32:
+    """Canonical FP32 squared distance (32-lane order, pairwise rounds)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    return np.float32(_load().orc_canon_dist32(_ptr(x), _ptr(y), x.shape[0]))
+
+
+def propagate_best_first(X, ids_in, k: int, budget: int):
+    """One synchronous pass of budgeted best-first propagation (Sec. 3.2)."""
+    X = _as_f32(X)
+    n, d = X.shape
+    ids_in = np.ascontiguousarray(ids_in, dtype=np.int32)
+    assert ids_in.shape == (n, k) and budget >= k
+    ids = np.empty((n, k), dtype=np.int32)
+    dists = np.empty((n, k), dtype=np.float32)
+    rc = _load().orc_propagate_best_first(_ptr(X), n, d, d, k, _ptr(ids_in), int(budget), _ptr(ids), _ptr(dists))
+    assert rc == 0
+    return ids, dists
+
+
+def propagate_pairwise(X, ids_in, k: int):
+    """One first-order round with pairwise updating (Sec. 3.4)."""
+    X = _as_f32(X)
+    n, d = X.shape
+    ids_in = np.ascontiguousarray(ids_in, dtype=np.int32)
+    assert ids_in.shape == (n, k)
+    ids = np.empty((n, k), dtype=np.int32)
+    dists = np.empty((n, k), dtype=np.float32)
+    _load().orc_propagate_pairwise(_ptr(X), n, d, d, k, _ptr(ids_in), _ptr(ids), _ptr(dists))
+    return ids, dists
+
+
+def effective_rate(prev_ids, ids) -> float:
+    """r_m of Sec. 3.2: the share of list entries after division m that were
+    not in the lists after division m - 1 (padding -1 excluded)."""
+    ids = np.asarray(ids)
+    total = int(np.sum(ids >= 0))
+    if prev_ids is None:
+        return 1.0 if total else 0.0
+    prev = np.asarray(prev_ids)
+    new = 0
+    for r in range(ids.shape[0]):
+        cur = ids[r][ids[r] >= 0]
+        new += int(np.sum(~np.isin(cur, prev[r])))
+    return new / total if total else 0.0
+
+
 def knn_exact(X, k: int, queries=None):
     lib = _load()
     X = _as_f32(X)
@@ -251,27 +303,54 @@ def normalize_rows(X) -> np.ndarray:
 
 
 def build_graph(X, k: int, T: int, g: int, R: int, seed: int,
-                precision: int = PREC_FP32, rescore_mult: int = 2, metric: int = METRIC_L2):
+                precision: int = PREC_FP32, rescore_mult: int = 2, metric: int = METRIC_L2,
+                r_stop: float = 0.0, prop: int = 0, budget: int = 0, info=None):
     """T random divisions, leaf graphs, merge, then R propagation rounds.
 
     metric = METRIC_COSINE: the same method on the rows scaled to unit length
     (normalize_rows), distances halved: 1 - cos of the scaled rows.
+    r_stop > 0: divisions are added one by one until r_m < r_stop (at most
+    T); info["divisions"] receives the number used, info["rates"] the r_m.
+    prop: PROP_FIRST_ORDER (Theorem 1), PROP_BEST_FIRST (Sec. 3.2, visit
+    budget `budget`) or PROP_PAIRWISE (first order with pairwise updating).
     """
     if metric == METRIC_COSINE:
-        ids, dists = build_graph(normalize_rows(X), k, T, g, R, seed, precision, rescore_mult)
+        ids, dists = build_graph(normalize_rows(X), k, T, g, R, seed, precision, rescore_mult,
+                                 r_stop=r_stop, prop=prop, budget=budget, info=info)
         return ids, (dists * np.float32(0.5)).astype(np.float32)
     X = _as_f32(X)
     n = X.shape[0]
     lists = np.empty((T, n, k), dtype=np.int32)
+    ids = dists = None
+    rates = []
+    used = T
     for t in range(T):
         perm, off = partition(X, seed, t, g)
         if precision == PREC_FP32:
             lists[t], _ = leaf_knn(X, perm, off, k)
         else:
             lists[t], _ = leaf_knn_quant(X, perm, off, k, rescore_mult * k, precision)
-    ids, dists = merge(X, lists, k)
+        if r_stop > 0:
+            # Sec. 4: add divisions until the m-th one's effective rate r_m
+            # falls below the threshold, then start the propagation
+            prev = ids
+            ids, dists = merge(X, lists[:t + 1], k)
+            rates.append(effective_rate(prev, ids))
+            if rates[-1] < r_stop:
+                used = t + 1
+                break
+    if r_stop <= 0:
+        ids, dists = merge(X, lists, k)
+    if info is not None:
+        info["divisions"] = used
+        info["rates"] = rates
     for _ in range(R):
-        ids, dists = propagate(X, ids, k)
+        if prop == PROP_BEST_FIRST:
+            ids, dists = propagate_best_first(X, ids, k, budget)
+        elif prop == PROP_PAIRWISE:
+            ids, dists = propagate_pairwise(X, ids, k)
+        else:
+            ids, dists = propagate(X, ids, k)
     return ids, dists
 
 

@@ -413,6 +413,184 @@ int orc_propagate(const float* X, int64_t n, int d, int64_t ld, int k, const int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Canonical FP32 squared distance: the 32-lane order of orc_project with    */
+/* t_j = x_j - y_j in place of the product, s_l = fmaf(t_j, t_j, s_l), then  */
+/* the five pairwise rounds.  Used where an FP32 distance decides an order   */
+/* (the best-first queue below), so that the decision is the kernel's.       */
+/* ------------------------------------------------------------------------ */
+float orc_canon_dist32(const float* x, const float* y, int d)
+{
+    float s[32];
+    for (int l = 0; l < 32; ++l) s[l] = 0.0f;
+    int nchunks = (d + 127) / 128;
+    for (int l = 0; l < 32; ++l)
+        for (int c = 0; c < nchunks; ++c)
+            for (int e = 0; e < 4; ++e) {
+                int j = 128 * c + 4 * l + e;
+                if (j < d) {
+                    float t = x[j] - y[j];
+                    s[l] = fmaf(t, t, s[l]);
+                }
+            }
+    for (int o = 16; o >= 1; o >>= 1) {
+        float nxt[32];
+        for (int l = 0; l < 32; ++l) nxt[l] = s[l] + s[l ^ o];
+        for (int l = 0; l < 32; ++l) s[l] = nxt[l];
+    }
+    return s[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Best-first neighbourhood propagation with a visit budget (Sec. 3.2): for  */
+/* every point p, over a frozen snapshot of the lists (a synchronous pass):  */
+/*   - p's own neighbours are visited first, in list order, and pushed into  */
+/*     a priority queue keyed by their distance to p (nearest on top);       */
+/*   - then the top point q is popped and its not yet visited neighbours are */
+/*     visited, in q's list order, and pushed; and so on,                    */
+/*   - until the queue is empty or `budget` points have been visited (the    */
+/*     budget may end a list part way);                                      */
+/*   - p's new list is the k best of all visited points by (D, id).          */
+/* The queue orders by the canonical FP32 distance with ties by id (the      */
+/* kernel's decision); the final list by the FP64 distance as elsewhere.     */
+/* budget >= k.  Ids outside [0, n) are empty slots.                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    float D32;
+    int32_t id;
+    int popped;
+} bf_entry;
+
+static int bf_less(const bf_entry* a, const bf_entry* b)
+{
+    if (a->D32 != b->D32) return a->D32 < b->D32;
+    return a->id < b->id;
+}
+
+int orc_propagate_best_first(const float* X, int64_t n, int d, int64_t ld, int k, const int32_t* in_ids, int budget,
+                             int32_t* ids, float* dists)
+{
+    if (budget < k) return -1;
+#pragma omp parallel
+    {
+        int32_t* mark = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        bf_entry* q = (bf_entry*)malloc((size_t)budget * sizeof(bf_entry));
+        cand_t* c = (cand_t*)malloc((size_t)budget * sizeof(cand_t));
+        for (int64_t i = 0; i < n; ++i) mark[i] = -1;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t p = 0; p < n; ++p) {
+            const float* xp = X + p * ld;
+            int cnt = 0;
+            mark[p] = (int32_t)p;
+            /* visit o (if new and the budget allows); returns 0 when full */
+#define BF_VISIT(o)                                                                   \
+    do {                                                                              \
+        int32_t o_ = (o);                                                             \
+        if (o_ >= 0 && o_ < n && mark[o_] != (int32_t)p) {                            \
+            mark[o_] = (int32_t)p;                                                    \
+            q[cnt].D32 = orc_canon_dist32(xp, X + (int64_t)o_ * ld, d);               \
+            q[cnt].id = o_;                                                           \
+            q[cnt].popped = 0;                                                        \
+            ++cnt;                                                                    \
+        }                                                                             \
+    } while (0)
+            for (int e = 0; e < k && cnt < budget; ++e) BF_VISIT(in_ids[p * k + e]);
+            while (cnt < budget) {
+                int top = -1;
+                for (int i = 0; i < cnt; ++i)
+                    if (!q[i].popped && (top < 0 || bf_less(&q[i], &q[top]))) top = i;
+                if (top < 0) break; /* queue empty */
+                q[top].popped = 1;
+                const int32_t u = q[top].id;
+                for (int f = 0; f < k && cnt < budget; ++f) BF_VISIT(in_ids[(int64_t)u * k + f]);
+            }
+#undef BF_VISIT
+            for (int i = 0; i < cnt; ++i) {
+                c[i].id = q[i].id;
+                c[i].D = sqdist64(xp, X + (int64_t)q[i].id * ld, d);
+            }
+            emit_topk(c, cnt, k, ids + p * k, dists + p * k);
+        }
+        free(c);
+        free(q);
+        free(mark);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* First-order propagation with pairwise updating (Sec. 3.4 "Speedup": when  */
+/* v is considered for u's list, u is also considered for v's list), in the  */
+/* synchronous form: with C(p) = N(p) u N(N(p)) \ {p} the candidates of the  */
+/* plain round, p's new list is the k best of C(p) together with every q     */
+/* whose candidates contain p, {q : p in C(q)}.                              */
+/* ------------------------------------------------------------------------ */
+int orc_propagate_pairwise(const float* X, int64_t n, int d, int64_t ld, int k, const int32_t* in_ids,
+                           int32_t* ids, float* dists)
+{
+    const int64_t cap = (int64_t)k + (int64_t)k * k;
+    int32_t* C = (int32_t*)malloc((size_t)(n * cap) * sizeof(int32_t));
+    int32_t* len = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    /* pass 1: the candidate sets C(p), deduplicated */
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t p = 0; p < n; ++p) {
+        int32_t* u = C + p * cap;
+        int64_t cnt = 0;
+        for (int e = 0; e < k; ++e) {
+            int32_t qq = in_ids[p * k + e];
+            if (qq < 0 || qq >= n) continue;
+            if (qq != p) u[cnt++] = qq;
+            for (int f = 0; f < k; ++f) {
+                int32_t o = in_ids[(int64_t)qq * k + f];
+                if (o < 0 || o >= n || o == p) continue;
+                u[cnt++] = o;
+            }
+        }
+        qsort(u, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        int64_t m = 0;
+        for (int64_t e = 0; e < cnt; ++e)
+            if (e == 0 || u[e] != u[e - 1]) u[m++] = u[e];
+        len[p] = (int32_t)m;
+    }
+    /* reverse offers: rev[c] = {p : c in C(p)} */
+    int64_t* roff = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int64_t p = 0; p < n; ++p)
+        for (int32_t e = 0; e < len[p]; ++e) roff[C[p * cap + e] + 1]++;
+    for (int64_t i = 0; i < n; ++i) roff[i + 1] += roff[i];
+    int32_t* rev = (int32_t*)malloc((size_t)(roff[n] > 0 ? roff[n] : 1) * sizeof(int32_t));
+    int64_t* fill = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) fill[i] = roff[i];
+    for (int64_t p = 0; p < n; ++p)
+        for (int32_t e = 0; e < len[p]; ++e) rev[fill[C[p * cap + e]]++] = (int32_t)p;
+    /* pass 2: k best of C(p) u rev(p) */
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t nr = roff[p + 1] - roff[p];
+        int32_t* u = (int32_t*)malloc((size_t)(len[p] + nr + 1) * sizeof(int32_t));
+        int64_t cnt = 0;
+        for (int32_t e = 0; e < len[p]; ++e) u[cnt++] = C[p * cap + e];
+        for (int64_t e = 0; e < nr; ++e) u[cnt++] = rev[roff[p] + e];
+        qsort(u, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        cand_t* c = (cand_t*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(cand_t));
+        int64_t m = 0;
+        for (int64_t e = 0; e < cnt; ++e) {
+            if (e > 0 && u[e] == u[e - 1]) continue;
+            c[m].id = u[e];
+            c[m].D = sqdist64(X + p * ld, X + (int64_t)u[e] * ld, d);
+            ++m;
+        }
+        emit_topk(c, m, k, ids + p * k, dists + p * k);
+        free(c);
+        free(u);
+    }
+    free(fill);
+    free(rev);
+    free(roff);
+    free(len);
+    free(C);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact k-NN lists (Def. 1) of the query points against all n points, by    */
 /* brute force; the accuracy of Sec. 4 is measured against these.           */
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,145 @@
+"""Pins of the oracle's propagation variants and division trigger (CPU).
+
+Best-first propagation with a visit budget (Sec. 3.2), pairwise updating
+(Sec. 3.4) and the effective-rate trigger r_m < threshold (Sec. 3.2, Sec. 4)
+are pinned against properties the paper and the definitions fix: the budget
+k visits only the point's own list, visit sets grow with the budget, an
+unlimited budget on a connected graph reaches the exact graph, no list ever
+gets worse, every pairwise offer is honoured, and r_m is 1 for the first
+division and 0 once a division adds nothing.
+"""
+import numpy as np
+
+import oracle
+from paper_1307_7852_gb300 import synthetic
+
+
+def _graph(n=1200, d=24, k=8, T=2, g=40, seed=3):
+    X = synthetic.sift_like(n, d, centers=12, seed=seed)
+    ids, dists = oracle.build_graph(X, k, T, g, 0, seed)
+    return X, ids, dists
+
+
+def test_canon_dist32_is_the_fp32_distance_of_integers():
+    X = synthetic.sift_like(50, 130, centers=3, seed=1)
+    for a, b in [(0, 1), (5, 9), (7, 7)]:
+        want = float(np.sum((X[a].astype(np.float64) - X[b]) ** 2))
+        assert float(oracle.canon_dist32(X[a], X[b])) == want  # integers < 2^24: exact
+
+
+def test_best_first_budget_k_keeps_the_own_list():
+    X, ids, dists = _graph()
+    bi, bd = oracle.propagate_best_first(X, ids, 8, 8)
+    np.testing.assert_array_equal(bi, ids)
+    np.testing.assert_array_equal(bd, dists)
+
+
+def test_best_first_never_worsens_and_grows_with_budget():
+    X, ids, dists = _graph()
+    prev = dists
+    for B in (8, 16, 40, 100, 300):
+        bi, bd = oracle.propagate_best_first(X, ids, 8, B)
+        assert np.all(bd <= prev)   # visit sets are prefixes of one sequence
+        prev = bd
+        assert np.all(bd <= dists)
+        for r in range(0, 1200, 97):
+            assert len(set(bi[r])) == 8 and r not in set(bi[r])
+
+
+def test_best_first_unlimited_budget_is_brute_force_over_the_reachable_set():
+    # with a budget of n the visits stop only when the queue is empty, i.e.
+    # after every point reachable from p along the lists was visited: the
+    # new list is the brute-force k best over that set (found here by BFS)
+    X = synthetic.sift_like(300, 16, centers=3, seed=5)
+    k = 12
+    ids, _ = oracle.build_graph(X, k, 3, 64, 1, 5)
+    bi, bd = oracle.propagate_best_first(X, ids, k, 300)
+    Xd = X.astype(np.float64)
+    for p in range(0, 300, 7):
+        seen, frontier = {p}, [p]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for o in ids[u]:
+                    if o >= 0 and o not in seen:
+                        seen.add(int(o))
+                        nxt.append(int(o))
+            frontier = nxt
+        cand = sorted(seen - {p})
+        D = np.sum((Xd[cand] - Xd[p]) ** 2, axis=1)
+        order = sorted(range(len(cand)), key=lambda i: (D[i], cand[i]))[:k]
+        np.testing.assert_array_equal(bi[p], [cand[i] for i in order])
+        np.testing.assert_array_equal(bd[p], D[order].astype(np.float32))
+
+
+def test_best_first_order_differs_from_first_order():
+    # a small budget explores the nearest neighbours' lists first and may go
+    # past the first order; both never worsen the input
+    X, ids, dists = _graph(seed=7)
+    bi, bd = oracle.propagate_best_first(X, ids, 8, 24)
+    fi, fd = oracle.propagate(X, ids, 8)
+    assert np.all(bd <= dists) and np.all(fd <= dists)
+    assert np.any(bi != fi)
+
+
+def test_pairwise_honours_every_offer():
+    X, ids, dists = _graph(seed=9)
+    k = 8
+    pi, pd = oracle.propagate_pairwise(X, ids, k)
+    fi, fd = oracle.propagate(X, ids, k)
+    assert np.all(pd <= fd)         # candidate superset of the plain round
+    n = X.shape[0]
+    # every q in C(p) offered p: q's new list holds p or k better entries
+    for p in range(0, n, 37):
+        C = set()
+        for q in ids[p]:
+            if q < 0:
+                continue
+            if q != p:
+                C.add(int(q))
+            C.update(int(o) for o in ids[q] if o >= 0 and o != p)
+        for q in C:
+            D = float(np.sum((X[p].astype(np.float64) - X[q]) ** 2))
+            if p in set(pi[q]):
+                continue
+            kth = (float(pd[q, -1]), int(pi[q, -1]))
+            assert kth < (D, p), (p, q)
+
+
+def test_effective_rate_pins():
+    X = synthetic.sift_like(500, 16, centers=4, seed=11)
+    info = {}
+    # one leaf holds all points: every division yields the exact graph, so
+    # the second division adds nothing (r_2 = 0) and the trigger fires there
+    ids, _ = oracle.build_graph(X, 6, 8, 512, 0, 2, r_stop=0.05, info=info)
+    assert info["rates"][0] == 1.0 and info["rates"][1] == 0.0 and info["divisions"] == 2
+    ei, _ = oracle.knn_exact(X, 6)
+    np.testing.assert_array_equal(ids, ei)
+    # small leaves: rates fall from 1 and stay within [0, 1]; the adaptive
+    # graph equals the plain merge of the divisions it used
+    info = {}
+    ids, dists = oracle.build_graph(X, 6, 8, 24, 0, 2, r_stop=0.3, info=info)
+    r = info["rates"]
+    assert r[0] == 1.0 and all(0.0 <= v <= 1.0 for v in r) and r[-1] < 0.3
+    m = info["divisions"]
+    pi, pd = oracle.build_graph(X, 6, m, 24, 0, 2)
+    np.testing.assert_array_equal(ids, pi)
+    np.testing.assert_array_equal(dists, pd)
+
+
+def test_best_first_pops_the_nearest_neighbour_first():
+    # budget k + j: the own list, then the first j not yet visited entries
+    # of the list of p's nearest neighbour (the top of the queue), in list
+    # order; the new list is the brute-force k best over those points
+    X, ids, _ = _graph(seed=13)
+    k, j = 8, 5
+    bi, bd = oracle.propagate_best_first(X, ids, k, k + j)
+    Xd = X.astype(np.float64)
+    for p in range(0, 1200, 41):
+        seen = [int(o) for o in ids[p] if o >= 0 and o != p]
+        top = seen[0]
+        extra = [int(o) for o in ids[top] if o >= 0 and o != p and o not in seen][:j]
+        cand = seen + extra
+        D = np.sum((Xd[cand] - Xd[p]) ** 2, axis=1)
+        order = sorted(range(len(cand)), key=lambda i: (D[i], cand[i]))[:k]
+        np.testing.assert_array_equal(bi[p], [cand[i] for i in order])
