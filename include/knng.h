@@ -75,6 +75,22 @@ extern "C" {
 #define KNNG_METRIC_L2 0
 #define KNNG_METRIC_COSINE 1
 
+/* Propagation scheme of the prop_rounds rounds.
+ * FIRST_ORDER (Theorem 1): every point takes the k best of its list and its
+ *   neighbours' lists.
+ * BEST_FIRST (Sec. 3.2): every point visits its neighbours, then repeatedly
+ *   the not yet visited neighbours of the nearest visited point it has not
+ *   expanded (a priority queue keyed by the FP32 distance, ties by id), until
+ *   `budget` points were visited or nothing is left; it keeps the k best
+ *   visited.  Each round reads a frozen snapshot of the lists.
+ * PAIRWISE (Sec. 3.4): FIRST_ORDER in which every candidate pair (p, c) is
+ *   also offered the other way: p enters c's list if it is among c's k best.
+ *   Offers are buffered, 4 per list entry; knng_sync reports
+ *   KNNG_ERR_LIMIT if a round had more (the lists stay valid). */
+#define KNNG_PROP_FIRST_ORDER 0
+#define KNNG_PROP_BEST_FIRST 1
+#define KNNG_PROP_PAIRWISE 2
+
 /* ---- parameters ------------------------------------------------------ */
 typedef struct knng_params {
     int32_t k;            /* neighbours per point, 1 <= k <= 64, k < leaf_size/2     */
@@ -86,6 +102,12 @@ typedef struct knng_params {
     int32_t rescore_mult; /* k' = rescore_mult * k candidates per leaf row, 1..4     */
     int32_t partitioner;  /* KNNG_PART_RANDOM                                        */
     int32_t metric;       /* KNNG_METRIC_L2 or KNNG_METRIC_COSINE                    */
+    int32_t propagation;  /* KNNG_PROP_*                                             */
+    int32_t budget;       /* KNNG_PROP_BEST_FIRST: points visited per point, k..512  */
+    float r_stop;         /* > 0: divisions are added one by one until the effective
+                             rate r_m of the last one is below r_stop (Sec. 4 uses
+                             0.05), at most T; 0: exactly T divisions            */
+    int32_t reserved;     /* must be 0                                               */
 } knng_params;
 
 typedef struct knng_handle knng_handle;
@@ -203,6 +225,27 @@ int knng_merge(knng_handle* h, int64_t n, int32_t T, int32_t k, const int32_t* i
 int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                    int32_t k, int32_t rounds, const int32_t* ids_in, const float* dists_in,
                    int32_t* ids, float* dists, void* stream);
+
+/* Best-first propagation with a visit budget (Sec. 3.2; see
+ * KNNG_PROP_BEST_FIRST): `rounds` synchronous passes.  k <= budget <= 512.
+ * ids_in: device [n][k]; ids, dists: [n][k], not overlapping the input. */
+int knng_propagate_best_first(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                              int32_t k, int32_t budget, int32_t rounds, const int32_t* ids_in, int32_t* ids,
+                              float* dists, void* stream);
+
+/* First-order propagation with pairwise updating (Sec. 3.4; see
+ * KNNG_PROP_PAIRWISE): `rounds` synchronous rounds.  Buffers as in
+ * knng_propagate; the offer buffer is part of the handle's workspace. */
+int knng_propagate_pairwise(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                            int32_t k, int32_t rounds, const int32_t* ids_in, const float* dists_in, int32_t* ids,
+                            float* dists, void* stream);
+
+/* Divisions used by the last build on h (p->T unless p->r_stop > 0) and, for
+ * an adaptive build, their effective rates r_1.. (Sec. 3.2: the share of
+ * list entries after division m that were not there after division m - 1;
+ * r_1 = 1), up to cap of them written to the host array rates.  Valid after
+ * the build's work completed (the adaptive build synchronises its stream). */
+int knng_divisions_used(const knng_handle* h, int32_t* m, float* rates, int32_t cap);
 
 /* ---- learned partitioner ----------------------------------------------- */
 /* The paper splits along random principal directions (Sec. 3.4) or random

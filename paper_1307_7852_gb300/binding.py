@@ -22,6 +22,7 @@ DTYPE_F32, DTYPE_F16, DTYPE_U8 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
 PART_RANDOM = 0
 METRIC_L2, METRIC_COSINE = 0, 1
+PROP_FIRST_ORDER, PROP_BEST_FIRST, PROP_PAIRWISE = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -44,7 +45,9 @@ class knng_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("T", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("prop_rounds", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("rescore_mult", ctypes.c_int32),
-                ("partitioner", ctypes.c_int32), ("metric", ctypes.c_int32)]
+                ("partitioner", ctypes.c_int32), ("metric", ctypes.c_int32),
+                ("propagation", ctypes.c_int32), ("budget", ctypes.c_int32), ("r_stop", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
 
 
 # exported entry points -> argtypes
@@ -62,6 +65,9 @@ SIGNATURES = {
     "knng_leaf_knn": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _I32, _I32, _I32, _P, _P, _P],
     "knng_merge": [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P],
     "knng_propagate": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
+    "knng_propagate_best_first": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _I32, _P, _P, _P, _P],
+    "knng_propagate_pairwise": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
+    "knng_divisions_used": [_P, _P, _P, _I32],
     "knng_normalize_rows": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _P],
     "knng_exact_knn": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _I32, _P, _P, _P],
     "knng_set_stage_events": [_P, _P, _I32],
@@ -193,9 +199,10 @@ def _ptr(t):
 
 
 def make_params(k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
-                partitioner=PART_RANDOM, metric=0) -> knng_params:
+                partitioner=PART_RANDOM, metric=0, propagation=0, budget=0, r_stop=0.0) -> knng_params:
     return knng_params(int(k), int(T), int(leaf_size), int(prop_rounds), int(seed) & (2**64 - 1),
-                       int(precision), int(rescore_mult), int(partitioner), int(metric))
+                       int(precision), int(rescore_mult), int(partitioner), int(metric), int(propagation),
+                       int(budget), float(r_stop), 0)
 
 
 # ----------------------------------------------------------- entry points --
@@ -216,13 +223,15 @@ def knng_leaf_offsets(n: int, leaf_size: int) -> np.ndarray:
 
 
 def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
-               ids=None, dists=None, stream=None, h: Handle = None, metric: int = METRIC_L2):
+               ids=None, dists=None, stream=None, h: Handle = None, metric: int = METRIC_L2,
+               propagation: int = PROP_FIRST_ORDER, budget: int = 0, r_stop: float = 0.0):
     torch = _torch()
     xp, dt, n, d, ld = _xdesc(X)
     h = h or handle(X.device.index or 0)
     ids = _out((n, k), torch.int32, X.device, ids)
     dists = _out((n, k), torch.float32, X.device, dists)
-    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric,
+                    propagation=propagation, budget=budget, r_stop=r_stop)
     h.check(lib().knng_build(h.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
                              _stream(X.device, stream)), "knng_build")
     return ids, dists
@@ -230,7 +239,8 @@ def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, resco
 
 def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32,
                     rescore_mult=2, ids=None, dists=None, stream=None, device: int = 0,
-                    h: Handle = None, metric: int = METRIC_L2):
+                    h: Handle = None, metric: int = METRIC_L2, propagation: int = PROP_FIRST_ORDER,
+                    budget: int = 0, r_stop: float = 0.0):
     """Host arrays in and out (X float32/float16/uint8 [n, d], unit stride along d)."""
     X = np.asarray(X)
     if X.ndim != 2 or X.strides[1] != X.itemsize:
@@ -246,7 +256,8 @@ def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision
     if dists is None:
         dists = np.empty((n, k), dtype=np.float32)
     h = h or handle(device)
-    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric,
+                    propagation=propagation, budget=budget, r_stop=r_stop)
     torch = _torch()
     st = _stream(torch.device("cuda", device), stream)
     h.check(lib().knng_build_host(h.ptr, ctypes.c_void_p(X.ctypes.data), dt, n, d, ld, ctypes.byref(p),
@@ -308,6 +319,43 @@ def knng_propagate(X, ids_in, dists_in, rounds=1, ids=None, dists=None, stream=N
                                  _ptr(dists_in), _ptr(ids), _ptr(dists), _stream(X.device, stream)),
             "knng_propagate")
     return ids, dists
+
+
+def knng_propagate_best_first(X, ids_in, budget, rounds=1, ids=None, dists=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    k = ids_in.shape[1]
+    h = h or handle(X.device.index or 0)
+    ids = _out((n, k), torch.int32, X.device, ids)
+    dists = _out((n, k), torch.float32, X.device, dists)
+    h.check(lib().knng_propagate_best_first(h.ptr, xp, dt, n, d, ld, k, int(budget), int(rounds), _ptr(ids_in),
+                                            _ptr(ids), _ptr(dists), _stream(X.device, stream)),
+            "knng_propagate_best_first")
+    return ids, dists
+
+
+def knng_propagate_pairwise(X, ids_in, dists_in, rounds=1, ids=None, dists=None, stream=None, h: Handle = None):
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    k = ids_in.shape[1]
+    h = h or handle(X.device.index or 0)
+    ids = _out((n, k), torch.int32, X.device, ids)
+    dists = _out((n, k), torch.float32, X.device, dists)
+    h.check(lib().knng_propagate_pairwise(h.ptr, xp, dt, n, d, ld, k, int(rounds), _ptr(ids_in), _ptr(dists_in),
+                                          _ptr(ids), _ptr(dists), _stream(X.device, stream)),
+            "knng_propagate_pairwise")
+    return ids, dists
+
+
+def knng_divisions_used(h: Handle = None, device: int = 0, cap: int = 32):
+    """(divisions used by the last build on h, their effective rates)."""
+    h = h or handle(device)
+    m = ctypes.c_int32()
+    rates = (ctypes.c_float * cap)()
+    rc = lib().knng_divisions_used(h.ptr, ctypes.byref(m), rates, cap)
+    if rc != KNNG_OK:
+        raise KnngError(rc, "knng_divisions_used")
+    return int(m.value), [float(r) for r in rates[:min(cap, m.value)]]
 
 
 def knng_normalize_rows(X, out=None, stream=None, h: Handle = None):
@@ -381,7 +429,8 @@ def knng_propagate_noalloc(X, ids_in, dists_in, rounds=1, ids=None, dists=None, 
 
 
 def knng_build_batched(Xs, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
-                       outs=None, stream=None, h: Handle = None, metric: int = METRIC_L2):
+                       outs=None, stream=None, h: Handle = None, metric: int = METRIC_L2,
+                       propagation: int = PROP_FIRST_ORDER, budget: int = 0, r_stop: float = 0.0):
     """Graphs of many independent point sets (CUDA tensors) in one recorded
     launch; returns a list of (ids, dists) per set."""
     torch = _torch()
@@ -398,7 +447,8 @@ def knng_build_batched(Xs, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP
         od = _out((n, k), torch.float32, dev, od)
         arr[i] = knng_dataset(xp.value, dt, d, n, ld, oi.data_ptr(), od.data_ptr())
         res.append((oi, od))
-    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric,
+                    propagation=propagation, budget=budget, r_stop=r_stop)
     h.check(lib().knng_build_batched(h.ptr, len(Xs), arr, ctypes.byref(p), _stream(dev, stream)),
             "knng_build_batched")
     return res
@@ -513,13 +563,15 @@ def knng_mlp_forward(mlp: Mlp, X, Z=None, stream=None, h: Handle = None):
 
 
 def knng_build_learned(mlp: Mlp, X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
-                       ids=None, dists=None, stream=None, h: Handle = None):
+                       ids=None, dists=None, stream=None, h: Handle = None, propagation: int = PROP_FIRST_ORDER,
+                       budget: int = 0, r_stop: float = 0.0):
     torch = _torch()
     xp, dt, n, d, ld = _xdesc(X)
     h = h or handle(X.device.index or 0)
     ids = _out((n, k), torch.int32, X.device, ids)
     dists = _out((n, k), torch.float32, X.device, dists)
-    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult)
+    p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, propagation=propagation,
+                    budget=budget, r_stop=r_stop)
     h.check(lib().knng_build_learned(h.ptr, mlp.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
                                      _stream(X.device, stream)), "knng_build_learned")
     return ids, dists

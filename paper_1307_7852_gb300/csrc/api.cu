@@ -66,6 +66,8 @@ struct knng_handle {
     BatchCache batch;
     std::map<TcKey, TcTile> tune;  // tile choices found by knng_autotune
     std::string err;
+    int div_used = 0;            // divisions used by the last build
+    std::vector<float> div_rates;  // their effective rates r_m (adaptive builds)
 };
 
 namespace {
@@ -241,6 +243,13 @@ int check_params(knng_handle* h, const knng_params* p, int64_t n)
     if (p->partitioner != KNNG_PART_RANDOM) return fail(h, KNNG_ERR_UNSUPPORTED, "partitioner %d", p->partitioner);
     if (p->metric != KNNG_METRIC_L2 && p->metric != KNNG_METRIC_COSINE)
         return fail(h, KNNG_ERR_INVALID_ARG, "metric %d", p->metric);
+    if (p->propagation != KNNG_PROP_FIRST_ORDER && p->propagation != KNNG_PROP_BEST_FIRST &&
+        p->propagation != KNNG_PROP_PAIRWISE)
+        return fail(h, KNNG_ERR_INVALID_ARG, "propagation %d", p->propagation);
+    if (p->propagation == KNNG_PROP_BEST_FIRST && (p->budget < p->k || p->budget > 512))
+        return fail(h, KNNG_ERR_INVALID_ARG, "budget %d out of [k, 512]", p->budget);
+    if (!(p->r_stop >= 0.f && p->r_stop <= 1.f)) return fail(h, KNNG_ERR_INVALID_ARG, "r_stop out of [0, 1]");
+    if (p->reserved != 0) return fail(h, KNNG_ERR_INVALID_ARG, "reserved must be 0");
     return KNNG_OK;
 }
 
@@ -286,6 +295,10 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         xb = a.take<uint8_t>((size_t)n * ldb);
         xb_bad = a.take<int>(1);
     }
+    unsigned long long* rate_cnt = a.take<unsigned long long>(2);
+    const bool adaptive = p.r_stop > 0.f;
+    PairScratch pw;
+    if (p.propagation == KNNG_PROP_PAIRWISE && R > 0) pairwise_take(a, n, k, pw);
     const size_t fixed = a.off;
     int r;
     if (!a.base) {
@@ -302,6 +315,8 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         if (rec) cudaEventRecord(h->stage_ev[i], st);
     };
     mark(0);
+    h->div_used = T;
+    h->div_rates.clear();
     cudaError_t e;
     if (xb) {
         e = cudaMemsetAsync(xb_bad, 0, sizeof(int), st);
@@ -311,30 +326,93 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         x.ldb = ldb;
         x.xb_bad = xb_bad;
     }
-    e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf);
-    if (e != cudaSuccess) return cuda_fail(h, e, "partition");
-    mark(1);
-    const size_t part_end = a.off;
-    a.off = fixed;  // the partition scratch is dead: the leaf stage reuses it
-    if ((r = leaf_stage(h, P, dp, x, T, perm, k, p.precision, p.rescore_mult, li, ld_, a, st))) return r;
-    a.off = std::max(part_end, a.off);
-    mark(2);
-    int32_t* mi = R == 0 ? ids : bi[0];
-    float* md = R == 0 ? dists : bd[0];
-    e = run_merge(n, T, k, li, ld_, mi, md, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "merge");
-    mark(3);
+    int cur = 0;  // bi[cur] / bd[cur]: the merged graph when R > 0
+    if (!adaptive) {
+        e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf);
+        if (e != cudaSuccess) return cuda_fail(h, e, "partition");
+        mark(1);
+        const size_t part_end = a.off;
+        a.off = fixed;  // the partition scratch is dead: the leaf stage reuses it
+        if ((r = leaf_stage(h, P, dp, x, T, perm, k, p.precision, p.rescore_mult, li, ld_, a, st))) return r;
+        a.off = std::max(part_end, a.off);
+        mark(2);
+        int32_t* mi = R == 0 ? ids : bi[0];
+        float* md = R == 0 ? dists : bd[0];
+        e = run_merge(n, T, k, li, ld_, mi, md, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "merge");
+        mark(3);
+    } else {
+        // Sec. 4: divisions are added one by one until the effective rate
+        // r_m of the last one falls below r_stop; trees are partitioned and
+        // their leaf graphs built two at a time, then merged one at a time
+        // with a host check of r_m after each (a tree past the stop is
+        // discarded unused).
+        constexpr int kChunk = 2;
+        bool stop = false;
+        for (int t0 = 0; t0 < T && !stop; t0 += kChunk) {
+            const int tc = std::min(kChunk, T - t0);
+            const size_t base = a.off;
+            e = run_partition(x, P, dp, tc, p.seed, perm + (size_t)t0 * n, a, st, lf, t0);
+            if (e != cudaSuccess) return cuda_fail(h, e, "partition");
+            const size_t part_end = a.off;
+            a.off = base;
+            if ((r = leaf_stage(h, P, dp, x, tc, perm + (size_t)t0 * n, k, p.precision, p.rescore_mult,
+                                li + (size_t)t0 * nk, ld_ + (size_t)t0 * nk, a, st)))
+                return r;
+            a.off = std::max(part_end, a.off);
+            a.off = base;
+            for (int j = 0; j < tc && !stop; ++j) {
+                const int t = t0 + j;
+                float rate = 1.f;
+                if (t == 0) {
+                    e = run_merge(n, 1, k, li, ld_, bi[0], bd[0], st);
+                    cur = 0;
+                } else {
+                    unsigned long long hc[2] = {0, 0};
+                    e = cudaMemsetAsync(rate_cnt, 0, sizeof hc, st);
+                    if (e == cudaSuccess)
+                        e = run_merge_add(n, k, bi[cur], bd[cur], li + (size_t)t * nk, ld_ + (size_t)t * nk,
+                                          bi[cur ^ 1], bd[cur ^ 1], rate_cnt, st);
+                    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, rate_cnt, sizeof hc, cudaMemcpyDeviceToHost, st);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                    cur ^= 1;
+                    rate = hc[1] ? (float)((double)hc[0] / (double)hc[1]) : 0.f;
+                }
+                if (e != cudaSuccess) return cuda_fail(h, e, "merge");
+                h->div_rates.push_back(rate);
+                if (rate < p.r_stop) {
+                    h->div_used = t + 1;
+                    stop = true;
+                }
+            }
+        }
+        if (R == 0) {
+            e = cudaMemcpyAsync(ids, bi[cur], nk * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dists, bd[cur], nk * sizeof(float), cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy");
+        }
+        mark(1);
+        mark(2);
+        mark(3);
+    }
     // propagation visits points in the leaf order of tree 0: neighbouring
     // points run together, so candidate rows are shared through L2.
     for (int rd = 0; rd < R; ++rd) {
-        const int32_t* si = bi[rd & 1];
-        const float* sd = bd[rd & 1];
-        const unsigned long long* sf = rd == 0 ? nullptr : fl[rd & 1];
-        int32_t* oi = rd == R - 1 ? ids : bi[(rd + 1) & 1];
-        float* od = rd == R - 1 ? dists : bd[(rd + 1) & 1];
-        unsigned long long* of = rd == R - 1 ? nullptr : fl[(rd + 1) & 1];
-        e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st);
+        const int32_t* si = bi[cur];
+        const float* sd = bd[cur];
+        const unsigned long long* sf = rd == 0 ? nullptr : fl[cur];
+        const bool last = rd == R - 1;
+        int32_t* oi = last ? ids : bi[cur ^ 1];
+        float* od = last ? dists : bd[cur ^ 1];
+        unsigned long long* of = last ? nullptr : fl[cur ^ 1];
+        if (p.propagation == KNNG_PROP_BEST_FIRST)
+            e = run_propagate_best_first(x, k, p.budget, perm, si, oi, od, st);
+        else if (p.propagation == KNNG_PROP_PAIRWISE)
+            e = run_propagate_pairwise(x, k, perm, si, sd, sf, oi, od, of, pw, h->dev_err, st);
+        else
+            e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
+        cur ^= 1;
         mark(4 + rd);
     }
     if (cosine) {
@@ -539,6 +617,98 @@ int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int3
     return KNNG_OK;
 }
 
+int knng_propagate_best_first(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                              int32_t k, int32_t budget, int32_t rounds, const int32_t* ids_in, int32_t* ids,
+                              float* dists, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    if ((r = check_k(h, k, -1))) return r;
+    if (budget < k || budget > 512) return fail(h, KNNG_ERR_INVALID_ARG, "budget %d out of [k, 512]", budget);
+    if (rounds < 1 || rounds > 16) return fail(h, KNNG_ERR_INVALID_ARG, "rounds = %d out of [1, 16]", rounds);
+    if (!ids_in || !ids || !dists) return fail(h, KNNG_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t nk = (size_t)n * k;
+    int32_t* bi[2] = {nullptr, nullptr};
+    float* bd[2] = {nullptr, nullptr};
+    if (rounds > 1) {
+        Arena m;
+        for (int b = 0; b < 2; ++b) { m.take<int32_t>(nk); m.take<float>(nk); }
+        if ((r = ensure_ws(h, m.off, st))) return r;
+        Arena a;
+        a.base = h->ws;
+        for (int b = 0; b < 2; ++b) { bi[b] = a.take<int32_t>(nk); bd[b] = a.take<float>(nk); }
+    }
+    const int32_t* si = ids_in;
+    for (int rd = 0; rd < rounds; ++rd) {
+        const bool last = rd == rounds - 1;
+        int32_t* oi = last ? ids : bi[rd & 1];
+        float* od = last ? dists : bd[rd & 1];
+        const cudaError_t e = run_propagate_best_first(x, k, budget, nullptr, si, oi, od, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "best-first propagation");
+        si = oi;
+    }
+    return KNNG_OK;
+}
+
+int knng_propagate_pairwise(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
+                            int32_t k, int32_t rounds, const int32_t* ids_in, const float* dists_in, int32_t* ids,
+                            float* dists, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    if ((r = check_k(h, k, -1))) return r;
+    if (rounds < 1 || rounds > 16) return fail(h, KNNG_ERR_INVALID_ARG, "rounds = %d out of [1, 16]", rounds);
+    if (!ids_in || !dists_in || !ids || !dists) return fail(h, KNNG_ERR_INVALID_ARG, "NULL pointer");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t nk = (size_t)n * k;
+    auto carve = [&](Arena& a, int32_t** bi, float** bd, unsigned long long** fl, PairScratch& pw) {
+        for (int b = 0; b < 2; ++b) {
+            bi[b] = a.take<int32_t>(nk);
+            bd[b] = a.take<float>(nk);
+            fl[b] = a.take<unsigned long long>(n);
+        }
+        pairwise_take(a, n, k, pw);
+    };
+    int32_t* bi[2];
+    float* bd[2];
+    unsigned long long* fl[2];
+    PairScratch pw;
+    Arena m;
+    carve(m, bi, bd, fl, pw);
+    if ((r = ensure_ws(h, m.off, st))) return r;
+    Arena a;
+    a.base = h->ws;
+    carve(a, bi, bd, fl, pw);
+    const int32_t* si = ids_in;
+    const float* sd = dists_in;
+    const unsigned long long* sf = nullptr;  // the input lists count as all new
+    for (int rd = 0; rd < rounds; ++rd) {
+        const bool last = rd == rounds - 1;
+        int32_t* oi = last ? ids : bi[rd & 1];
+        float* od = last ? dists : bd[rd & 1];
+        unsigned long long* of = last ? nullptr : fl[rd & 1];
+        const cudaError_t e = run_propagate_pairwise(x, k, nullptr, si, sd, sf, oi, od, of, pw, h->dev_err, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "pairwise propagation");
+        si = oi;
+        sd = od;
+        sf = of;
+    }
+    return KNNG_OK;
+}
+
+int knng_divisions_used(const knng_handle* h, int32_t* m, float* rates, int32_t cap)
+{
+    if (!h || !m || cap < 0 || (cap > 0 && !rates)) return KNNG_ERR_INVALID_ARG;
+    *m = h->div_used;
+    for (int32_t i = 0; i < cap && i < (int32_t)h->div_rates.size(); ++i) rates[i] = h->div_rates[i];
+    return KNNG_OK;
+}
+
 int knng_build(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                const knng_params* p, int32_t* ids, float* dists, void* stream)
 {
@@ -601,6 +771,9 @@ int knng_sync(knng_handle* h, void* stream)
     if (e != cudaSuccess) return cuda_fail(h, e, "error word");
     if (flag) {
         cudaMemset(h->dev_err, 0, sizeof(int));
+        if (flag == 2)
+            return fail(h, KNNG_ERR_LIMIT, "pairwise updating: more offers than the buffer holds (4 per list entry); "
+                                           "the lists are valid but some offers were dropped");
         return fail(h, KNNG_ERR_TIMEOUT, "a bounded device wait gave up; results of the affected calls are invalid");
     }
     return KNNG_OK;
@@ -637,6 +810,8 @@ int knng_build_batched(knng_handle* h, int32_t nsets, const knng_dataset* sets, 
     if (!h) return KNNG_ERR_INVALID_ARG;
     if (nsets < 1 || nsets > 65536 || !sets) return fail(h, KNNG_ERR_INVALID_ARG, "nsets = %d", nsets);
     if (!p) return fail(h, KNNG_ERR_INVALID_ARG, "params is NULL");
+    if (p->r_stop > 0.f)
+        return fail(h, KNNG_ERR_UNSUPPORTED, "adaptive divisions check r_m on the host; a recorded batch cannot");
     int r;
     for (int i = 0; i < nsets; ++i) {
         XDesc x;

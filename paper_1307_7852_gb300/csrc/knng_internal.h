@@ -135,9 +135,10 @@ cudaError_t run_feature_range(const float* Z, int64_t n, int C, uint32_t* scratc
 void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf);
 
 // ---- stages (each carves its scratch from the arena) -------------------
+// Trees t0 .. t0 + T - 1 (perm_out[T][n]).
 cudaError_t run_partition(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
                           uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st,
-                          const LearnedFeat* lf = nullptr);
+                          const LearnedFeat* lf = nullptr, int t0 = 0);
 
 cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                              const int32_t* perm, int k, int kp, int32_t* ids, float* dists,
@@ -170,6 +171,13 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
 
 cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
                       int32_t* ids, float* dists, cudaStream_t st);
+// One more division into the running graph: lists (ia, da) and (ib, db) ->
+// the k best of both; counts[0] += entries not in a, counts[1] += entries.
+cudaError_t run_merge_add(int64_t n, int k, const int32_t* ia, const float* da, const int32_t* ib, const float* db,
+                          int32_t* ids, float* dists, unsigned long long* counts, cudaStream_t st);
+// Budgeted best-first propagation pass (Sec. 3.2), synchronous.
+cudaError_t run_propagate_best_first(const XDesc& x, int k, int budget, const int32_t* order, const int32_t* ids_in,
+                                     int32_t* ids, float* dists, cudaStream_t st);
 
 // One synchronous propagation round.  flags_in (nullable = every entry new)
 // marks, per point, the list entries that were not in the previous round's
@@ -183,9 +191,36 @@ cudaError_t run_byte_copy(const XDesc& x, uint8_t* Xb, int64_t ldb, int* bad, cu
 cudaError_t run_normalize_rows(const XDesc& x, float* out, int64_t ldo, cudaStream_t st);
 cudaError_t run_scale(float* v, int64_t cnt, float f, cudaStream_t st);
 
+// Pairwise-updating offers of one propagation round (see propagate.cu):
+// offer (target c, packed (dist, source p)) pairs, at most cap of them, a
+// running count, per-target counts, and the error word (2 = overflow).
+struct PairOffers {
+    int32_t* tgt = nullptr;
+    uint64_t* key = nullptr;
+    unsigned long long* count = nullptr;
+    int32_t* per_tgt = nullptr;
+    unsigned long long cap = 0;
+    int* err = nullptr;
+};
+
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
-                          unsigned long long* flags_out, cudaStream_t st);
+                          unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers = nullptr);
+
+// Scratch of a pairwise round: offers (cap entries), per-target counts and
+// offsets, forward lists.  pairwise_bytes() sizes it.
+struct PairScratch {
+    PairOffers po;
+    int64_t* off = nullptr;       // [n + 1]
+    int64_t* bsum = nullptr;      // scan block sums
+    uint64_t* sorted = nullptr;   // [cap] offers grouped by target
+    int32_t* fwd_i = nullptr;     // [n][k]
+    float* fwd_d = nullptr;       // [n][k]
+};
+void pairwise_take(Arena& a, int64_t n, int k, PairScratch& s);
+cudaError_t run_propagate_pairwise(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
+                                   const float* d_in, const unsigned long long* flags_in, int32_t* ids, float* dists,
+                                   unsigned long long* flags_out, const PairScratch& s, int* err, cudaStream_t st);
 
 cudaError_t run_exact_knn(const XDesc& x, const int32_t* queries, int nq, int k, int32_t* ids,
                           float* dists, cudaStream_t st);

@@ -155,9 +155,10 @@ __global__ void init_root_nodes_kernel(int64_t n, const SplitNode* __restrict__ 
     for (int e = threadIdx.x; e < nd.size; e += blockDim.x) row[nd.off + e] = (int32_t)blockIdx.x;
 }
 
-// dirs[t][s][0..d_pad): direction of split node s of this level in tree t.
+// dirs[t][s][0..d_pad): direction of split node s of this level in tree
+// t0 + t (a tree's directions depend on its own index only).
 __global__ void gen_dirs_kernel(float* dirs, int T, int S, int d, int d_pad,
-                                const SplitNode* nodes, uint32_t level, uint64_t seed)
+                                const SplitNode* nodes, uint32_t level, uint64_t seed, uint32_t t0)
 {
     const int q4 = d_pad / 4;
     const int64_t total = (int64_t)T * S * q4;
@@ -167,7 +168,7 @@ __global__ void gen_dirs_kernel(float* dirs, int T, int S, int d, int d_pad,
         const int q = (int)(e % q4);
         const int s = (int)((e / q4) % S);
         const int t = (int)(e / ((int64_t)q4 * S));
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)t, level, nodes[s].v, (uint32_t)q), key);
+        const uint4 w = philox4x32_10(make_uint4(t0 + (uint32_t)t, level, nodes[s].v, (uint32_t)q), key);
         const int j = 4 * q;
         float4 a;
         a.x = (j + 0 < d) ? tri_entry(w.x) : 0.f;
@@ -642,7 +643,8 @@ static inline int grid_for(int64_t work, int per_block, int cap)
 }
 
 cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
-                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st, const LearnedFeat* lf)
+                          uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st, const LearnedFeat* lf,
+                          int t0)
 {
     const int64_t n = x.n;
     const int d_pad = (x.d + 3) & ~3;
@@ -684,7 +686,7 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         if (learned) {
             lv.Z = lf->Z;
             lv.C = lf->C;
-            for (int t = 0; t < T && t < 32; ++t) lv.ft.f[t] = lf->feat[t][lvl];
+            for (int t = 0; t < T && t0 + t < 32; ++t) lv.ft.f[t] = lf->feat[t0 + t][lvl];
             lv.rmin = rmin;
             lv.rmax = rmax;
             lv.frange = lf->frange;
@@ -696,7 +698,7 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
             note_launches(1);
         }
         gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(
-            dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed);
+            dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed, (uint32_t)t0);
         note_launches(1);
         const int pgrid = grid_for(n * 32, 256, sms * 16);
         auto project = [&](auto dt) {

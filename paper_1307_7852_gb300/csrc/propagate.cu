@@ -58,7 +58,8 @@ static PropLayout prop_layout(int k)
 
 template <int E, int kDT>
 __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
-                                 const int* __restrict__ xb_bad, int64_t n, int k, const int32_t* __restrict__ order,
+                                 const int* __restrict__ xb_bad, PairOffers po, int64_t n, int k,
+                                 const int32_t* __restrict__ order,
                                  const int32_t* __restrict__ ids_in, const float* __restrict__ d_in,
                                  const unsigned long long* __restrict__ flags_in, int32_t* __restrict__ ids_out,
                                  float* __restrict__ d_out, unsigned long long* __restrict__ flags_out, int H,
@@ -152,6 +153,40 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
             if (lane < nb) cd[c0 + lane] = dd;
         }
         __syncwarp();
+        if (po.tgt) {
+            // pairwise updating: offer p to every candidate c whose input
+            // list it would enter, i.e. (D, p) below c's k-th (dist, id)
+            for (int i0 = 0; i0 < cnt; i0 += 32) {
+                const int i = i0 + lane;
+                bool emit = false;
+                int32_t c = -1;
+                uint64_t kk = 0;
+                if (i < cnt) {
+                    c = cid[i];
+                    kk = pack_key(cd[i], (uint32_t)p);
+                    const int32_t last = ids_in[(int64_t)c * k + k - 1];
+                    const uint64_t thr =
+                        (last < 0 || last >= n) ? kKeyMax : pack_key(d_in[(int64_t)c * k + k - 1], (uint32_t)last);
+                    emit = kk < thr;
+                }
+                const uint32_t b = __ballot_sync(KNNG_FULL_MASK, emit);
+                if (b) {
+                    unsigned long long slot0 = 0;
+                    if (lane == 0) slot0 = atomicAdd(po.count, (unsigned long long)__popc(b));
+                    slot0 = __shfl_sync(KNNG_FULL_MASK, slot0, 0);
+                    if (emit) {
+                        const unsigned long long slot = slot0 + __popc(b & lanemask_lt());
+                        if (slot < po.cap) {
+                            po.tgt[slot] = c;
+                            po.key[slot] = kk;
+                            atomicAdd(&po.per_tgt[c], 1);
+                        } else {
+                            atomicExch(po.err, 2);
+                        }
+                    }
+                }
+            }
+        }
         auto key = [&](int idx) -> uint64_t { return pack_key(cd[idx], (uint32_t)cid[idx]); };
         const int want = min(k, cnt);
         int nsel = 0;
@@ -208,7 +243,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
 template <int E, int kDT>
 static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                                const unsigned long long* fin, int32_t* ids, float* dists, unsigned long long* fout,
-                               cudaStream_t st)
+                               const PairOffers& po, cudaStream_t st)
 {
     const PropLayout PL = prop_layout(k);
     int warps = (int)((200 * 1024) / PL.per_warp);
@@ -226,7 +261,7 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     if (blocks > need) blocks = need;
     RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
     const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
-    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
+    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, po, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
                                                 PL.hshift, PL.cap, (int)PL.per_warp);
     note_launches(1);
     return cudaGetLastError();
@@ -235,19 +270,22 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
 template <int kDT>
 static cudaError_t prop_dispatch(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
                                  const float* d_in, const unsigned long long* fin, int32_t* ids, float* dists,
-                                 unsigned long long* fout, cudaStream_t st)
+                                 unsigned long long* fout, const PairOffers& po, cudaStream_t st)
 {
-    if (k <= 32) return launch_prop<1, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
-    return launch_prop<2, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, st);
+    if (k <= 32) return launch_prop<1, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, st);
+    return launch_prop<2, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, st);
 }
 
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
-                          unsigned long long* flags_out, cudaStream_t st)
+                          unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers)
 {
-    if (x.dtype == kDtF16) return prop_dispatch<kDtF16>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
-    if (x.dtype == kDtU8) return prop_dispatch<kDtU8>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
-    return prop_dispatch<kDtF32>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, st);
+    const PairOffers po = offers ? *offers : PairOffers{};
+    if (x.dtype == kDtF16)
+        return prop_dispatch<kDtF16>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, st);
+    if (x.dtype == kDtU8)
+        return prop_dispatch<kDtU8>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, st);
+    return prop_dispatch<kDtF32>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, st);
 }
 
 }  // namespace knng
