@@ -68,6 +68,7 @@ def _load():
             lib.orc_leaf_count.argtypes = [i64, i32]
             lib.orc_leaf_count.restype = i64
             lib.orc_partition.argtypes = [P, i64, i32, i64, u64, u32, i32, P, P]
+            lib.orc_partition_dirs.argtypes = [P, i64, i32, i64, P, i32, P, P]
             lib.orc_leaf_knn.argtypes = [P, i64, i32, i64, P, P, i64, i32, P, P]
             lib.orc_leaf_knn_quant.argtypes = [P, i64, i32, i64, P, P, P, i64, i32, i32, P, P]
             lib.orc_merge.argtypes = [P, i64, i32, i64, i32, i32, P, P, P]
@@ -147,6 +148,43 @@ def partition(X, seed: int, t: int, g: int):
     off = np.zeros(leaf_count(n, g) + 1, dtype=np.int64)
     lib.orc_partition(_ptr(X), n, d, d, seed, t, g, _ptr(perm), _ptr(off))
     return perm, off
+
+
+def partition_with_dirs(X, dirs, g: int):
+    """Tree whose node (level, v) splits along dirs[2^level - 1 + v]."""
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    dirs = np.ascontiguousarray(dirs, dtype=np.float32)
+    assert dirs.ndim == 2 and dirs.shape[1] == d
+    perm = np.zeros(n, dtype=np.int32)
+    off = np.zeros(leaf_count(n, g) + 1, dtype=np.int64)
+    lib.orc_partition_dirs(_ptr(X), n, d, d, _ptr(dirs), g, _ptr(perm), _ptr(off))
+    return perm, off
+
+
+def split_nodes(n: int, g: int):
+    """(level, v, first position, size) of every split node of the tree
+    shape (floor/ceil halving), in level order."""
+    out = []
+    level = [(0, n)]
+    lvl = 0
+    while level:
+        nxt = []
+        for v, (off, m) in enumerate(level):
+            if m is None:
+                nxt += [(0, None), (0, None)]
+                continue
+            if m > g:
+                out.append((lvl, v, off, m))
+                nxt += [(off, m // 2), (off + m // 2, m - m // 2)]
+            else:
+                nxt += [(0, None), (0, None)]
+        if not any(m is not None for _, m in nxt):
+            break
+        level = nxt
+        lvl += 1
+    return out
 
 
 # -------------------------------------------------------------- leaf graph --

@@ -202,6 +202,7 @@ typedef struct {
     uint64_t seed;
     uint32_t t;
     int g;
+    const float* dirs; /* optional: direction of node (level, v) in row 2^level - 1 + v */
     int32_t* perm;     /* output, n entries */
     int64_t* leaf_off; /* output, nleaves + 1 entries */
     int64_t nleaves;
@@ -219,7 +220,10 @@ static void split_node(part_ctx* c, int32_t* ids, int64_t m, uint32_t level, uin
     }
     float* a = (float*)malloc((size_t)c->d * sizeof(float));
     uint64_t* keys = (uint64_t*)malloc((size_t)m * sizeof(uint64_t));
-    orc_direction(c->seed, c->t, level, v, c->d, a);
+    if (c->dirs)
+        memcpy(a, c->dirs + (((int64_t)1 << level) - 1 + v) * c->d, (size_t)c->d * sizeof(float));
+    else
+        orc_direction(c->seed, c->t, level, v, c->d, a);
     for (int64_t i = 0; i < m; ++i) {
         float s = orc_project(c->X + (int64_t)ids[i] * c->ld, a, c->d);
         keys[i] = ((uint64_t)orc_ord(s) << 32) | (uint32_t)ids[i];
@@ -266,6 +270,34 @@ int orc_partition(const float* X, int64_t n, int d, int64_t ld, uint64_t seed, u
     c.leaf_off = leaf_off;
     c.nleaves = 0;
     c.pos = 0;
+    c.dirs = NULL;
+    int32_t* ids = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    for (int64_t i = 0; i < n; ++i) ids[i] = (int32_t)i;
+    split_node(&c, ids, n, 0, 0);
+    free(ids);
+    leaf_off[c.nleaves] = n;
+    return 0;
+}
+
+/* The same tree with given split directions instead of the random ones:
+ * dirs holds the direction of node (level, v) in row 2^level - 1 + v (rows of
+ * d floats).  Used to replay a partition whose directions were computed
+ * elsewhere (the principal directions of Sec. 3.4). */
+int orc_partition_dirs(const float* X, int64_t n, int d, int64_t ld, const float* dirs, int g, int32_t* perm,
+                       int64_t* leaf_off)
+{
+    part_ctx c;
+    c.X = X;
+    c.d = d;
+    c.ld = ld;
+    c.seed = 0;
+    c.t = 0;
+    c.g = g;
+    c.perm = perm;
+    c.leaf_off = leaf_off;
+    c.nleaves = 0;
+    c.pos = 0;
+    c.dirs = dirs;
     int32_t* ids = (int32_t*)malloc((size_t)n * sizeof(int32_t));
     for (int64_t i = 0; i < n; ++i) ids[i] = (int32_t)i;
     split_node(&c, ids, n, 0, 0);
