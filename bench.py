@@ -43,6 +43,7 @@ WORKLOADS = {
                    desc="1M x 960 GIST-like normalised mixture (256 centres), k=10, T=8, g=512, R=1"),
 }
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+PROPAGATION = {"first_order": 0, "best_first": 1, "pairwise": 2}
 METRIC = "points/sec to build the k-NN graph (recall@k reported on a 10k-point sample)"
 
 
@@ -359,6 +360,13 @@ def main():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed builds only (for profiler runs)")
+    ap.add_argument("--trees", type=int, default=None, help="override T of the workload")
+    ap.add_argument("--rounds", type=int, default=None, help="override R of the workload")
+    ap.add_argument("--propagation", choices=sorted(PROPAGATION), default="first_order")
+    ap.add_argument("--budget", type=int, default=0, help="best-first visit budget")
+    ap.add_argument("--r-stop", type=float, default=0.0, help="> 0: divisions until r_m < r_stop (at most T)")
+    ap.add_argument("--metric-kind", choices=["l2", "cosine"], default="l2")
+    ap.add_argument("--partitioner", choices=["random", "pca"], default="random")
     args = ap.parse_args()
     if args.workload in ("batched256", "learned10m"):
         if args.impl == "reference":
@@ -366,7 +374,16 @@ def main():
                               "on the sift1m workload only"}))
             return 0
         return run_batched(args) if args.workload == "batched256" else run_learned(args)
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.trees is not None:
+        w["T"] = args.trees
+    if args.rounds is not None:
+        w["R"] = args.rounds
+    if (args.trees, args.rounds) != (None, None) or args.propagation != "first_order" or args.r_stop > 0 \
+            or args.metric_kind != "l2" or args.partitioner != "random":
+        w["desc"] += f" [T={w['T']}, R={w['R']}, {args.propagation}" + \
+            (f", budget {args.budget}" if args.propagation == "best_first" else "") + \
+            (f", r_stop {args.r_stop}" if args.r_stop > 0 else "") + f", {args.metric_kind}, {args.partitioner}]"
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -398,10 +415,13 @@ def main():
         for e_ in row:
             e_.record(stream)
 
+    opts = dict(metric=1 if args.metric_kind == "cosine" else 0, propagation=PROPAGATION[args.propagation],
+                budget=args.budget, r_stop=args.r_stop, partitioner=1 if args.partitioner == "pca" else 0)
+
     def step(events=None):
         if events is not None:
             knng.knng_set_stage_events(events, h)
-        knng.knng_build(Xd, k, T, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h)
+        knng.knng_build(Xd, k, T, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h, **opts)
 
     for _ in range(args.warmup):
         step()
@@ -421,6 +441,7 @@ def main():
         torch.cuda.synchronize()
     knng.knng_set_stage_events(None, h)
     launches = knng.knng_launch_counter() - l0
+    div_used, div_rates = knng.knng_divisions_used(h)
     el, _ = aggregate(t_start.elapsed_time(t_end) / 1e3, n, world, dist, dev)
     sec = el / args.steps
     value = n * world / sec
@@ -435,10 +456,13 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "n": n, "d": d, "k": k, "T": T,
                    "leaf_size": g, "rounds": R, "precision": args.precision, "seed": args.seed,
+                   "propagation": args.propagation, "budget": args.budget, "r_stop": args.r_stop,
+                   "metric": args.metric_kind, "partitioner": args.partitioner,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2 (X = {X.nbytes / 2**20:.0f} MiB > 126 MiB)"},
         "stage_ms": {k_: round(v, 4) for k_, v in stage_ms.items()},
         "gpu_launches": launches,
+        "divisions_used": div_used,
         "clocks": clk.summary(),
     }
 
@@ -460,10 +484,18 @@ def main():
         samp = rng.choice(n, size=min(n, 20000), replace=False)
         u = [unique_candidates(gph.cpu().numpy(), samp) for gph in graphs[:R]]
         del perm, li, ld_, graphs
-        s_el = 4  # FP32 rows
+        # bytes per row entry the propagation reads: float rows holding only
+        # bytes (d <= 256) are read from their exact byte copy
+        byte_rows = X.dtype == np.float32 and d <= 256 and args.metric_kind == "l2" and bool(
+            np.all((X >= 0) & (X <= 255) & (X == np.rint(X))))
+        s_el = 1 if byte_rows else X.itemsize
         roof = {}
         if R > 0:
-            per_launch = [n * (k * k * 4 + u_r * d * s_el + 2 * k * 8 + d * s_el) for u_r in u]
+            if args.propagation == "best_first":
+                # every visit reads one row and one list slot
+                per_launch = [n * (args.budget * (d * s_el + 4) + 2 * k * 8 + d * s_el) for _ in u]
+            else:
+                per_launch = [n * (k * k * 4 + u_r * d * s_el + 2 * k * 8 + d * s_el) for u_r in u]
             t_prop = [stage_ms[f"propagate_r{r}"] / 1e3 for r in range(R)]
             ach = sum(per_launch) / sum(t_prop) / 1e9
             roof["propagate"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
@@ -516,12 +548,13 @@ def main():
             oi = torch.empty((n, k), dtype=torch.int32).pin_memory()
             od = torch.empty((n, k), dtype=torch.float32).pin_memory()
             Xn, oin, odn = Xp.numpy(), oi.numpy(), od.numpy()
-            knng.knng_build_host(Xn, k, T, g, R, args.seed, prec, 2, ids=oin, dists=odn, device=local, h=h)
+            knng.knng_build_host(Xn, k, T, g, R, args.seed, prec, 2, ids=oin, dists=odn, device=local, h=h, **opts)
             tt = []
             for _ in range(args.e2e_steps):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                knng.knng_build_host(Xn, k, T, g, R, args.seed, prec, 2, ids=oin, dists=odn, device=local, h=h)
+                knng.knng_build_host(Xn, k, T, g, R, args.seed, prec, 2, ids=oin, dists=odn, device=local, h=h,
+                                     **opts)
                 tt.append(time.perf_counter() - t0)
             e2e_sec = statistics.mean(tt)
             line["e2e"] = {"value": n / e2e_sec, "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes),
@@ -529,12 +562,13 @@ def main():
                            "api": "knng_build_host (pinned host buffers)"}
 
     # ---- the CPU oracle on a bounded sample (rank 0, N = 1 only)
-    if not args.no_extras and not args.no_cpu_baseline and rank == 0 and world == 1:
+    if not args.no_extras and not args.no_cpu_baseline and rank == 0 and world == 1 and args.partitioner == "random":
         import oracle
         ns = min(args.cpu_sample, n)
         Xs = np.ascontiguousarray(X[:ns])
         t0 = time.perf_counter()
-        oracle.build_graph(Xs, k, T, g, R, args.seed)
+        oracle.build_graph(Xs, k, T, g, R, args.seed, metric=opts["metric"], prop=opts["propagation"],
+                           budget=opts["budget"], r_stop=opts["r_stop"])  # (random partitioner only)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": ns / dt, "unit": "points/s", "cores": oracle.num_threads(),
                                 "kind": "oracle", "sample": f"first {ns} points of the workload, whole method "

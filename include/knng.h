@@ -63,7 +63,8 @@ extern "C" {
 #define KNNG_PREC_BF16 1
 #define KNNG_PREC_FP8E4M3 2
 
-#define KNNG_PART_RANDOM 0  /* Philox random directions (the only value knng_build takes) */
+#define KNNG_PART_RANDOM 0  /* Philox random directions (App. after Lemma 1)                  */
+#define KNNG_PART_PCA 1     /* random principal directions (Sec. 3.4): see knng_partition_pca */
 
 /* Distance.  L2: the squared Euclidean distance.  COSINE: 1 - cos of the
  * angle between two rows (App. after Lemma 1: random projections partition
@@ -100,7 +101,7 @@ typedef struct knng_params {
     uint64_t seed;        /* key of the Philox directions; same seed -> same trees   */
     int32_t precision;    /* KNNG_PREC_*                                             */
     int32_t rescore_mult; /* k' = rescore_mult * k candidates per leaf row, 1..4     */
-    int32_t partitioner;  /* KNNG_PART_RANDOM                                        */
+    int32_t partitioner;  /* KNNG_PART_RANDOM or KNNG_PART_PCA (d <= 1024)           */
     int32_t metric;       /* KNNG_METRIC_L2 or KNNG_METRIC_COSINE                    */
     int32_t propagation;  /* KNNG_PROP_*                                             */
     int32_t budget;       /* KNNG_PROP_BEST_FIRST: points visited per point, k..512  */
@@ -202,6 +203,28 @@ int knng_tune_load(knng_handle* h, const char* path);
  * (X, seed, t, leaf_size). */
 int knng_partition(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                    int32_t T, int32_t leaf_size, uint64_t seed, int32_t* perm, void* stream);
+
+/* Number of split levels of the tree shape of (n, g) (host only): the
+ * depth L of the deepest split node + 1; the nodes of level l are numbered
+ * v = 0 .. 2^l - 1 left to right. */
+int knng_split_levels(int64_t n, int32_t g, int32_t* levels);
+
+/* Random partition trees with principal-direction splits (Sec. 3.4, "Random
+ * division"): every node of m > g points splits at the median along the
+ * principal direction of points sampled from it.  Readings (the paper gives
+ * no sizes): a node with m <= s_cap points uses all of them, otherwise
+ * s_cap members chosen with replacement by Philox4x32-10 (counter (tree,
+ * level | 2^30, node, r / 4), key seed; member index = word mod m, members in
+ * ascending id order); s_cap = clamp(floor(40960 / d), 8, 128).  The
+ * direction: at most min(8, d) Lanczos steps with full reorthogonalisation
+ * on the FP32 covariance of the centred sample, started from the node's
+ * random direction, stopping once beta <= 1e-4 * max alpha; the top Ritz
+ * vector, unit length, largest-magnitude entry positive.  perm as in
+ * knng_partition.  dirs_out (device, may be NULL): T x (2^L - 1) x d floats,
+ * tree t's node (level, v) direction in row 2^level - 1 + v (rows of other
+ * slots are left untouched); L from knng_split_levels.  d <= 1024. */
+int knng_partition_pca(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld, int32_t T,
+                       int32_t g, uint64_t seed, int32_t* perm, float* dirs_out, void* stream);
 
 /* Leaf graphs (Sec. 3.1): for every tree t and point i, the k nearest other
  * members of i's leaf.  perm: device [T][n] as written by knng_partition.

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libknng.so")
 KNNG_OK = 0
 DTYPE_F32, DTYPE_F16, DTYPE_U8 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
-PART_RANDOM = 0
+PART_RANDOM, PART_PCA = 0, 1
 METRIC_L2, METRIC_COSINE = 0, 1
 PROP_FIRST_ORDER, PROP_BEST_FIRST, PROP_PAIRWISE = 0, 1, 2
 
@@ -68,6 +68,8 @@ SIGNATURES = {
     "knng_propagate_best_first": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _I32, _P, _P, _P, _P],
     "knng_propagate_pairwise": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
     "knng_divisions_used": [_P, _P, _P, _I32],
+    "knng_split_levels": [_I64, _I32, _P],
+    "knng_partition_pca": [_P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _U64, _P, _P, _P],
     "knng_normalize_rows": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _P],
     "knng_exact_knn": [_P, _P, _I32, _I64, _I32, _I64, _P, _I64, _I32, _P, _P, _P],
     "knng_set_stage_events": [_P, _P, _I32],
@@ -224,14 +226,15 @@ def knng_leaf_offsets(n: int, leaf_size: int) -> np.ndarray:
 
 def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
                ids=None, dists=None, stream=None, h: Handle = None, metric: int = METRIC_L2,
-               propagation: int = PROP_FIRST_ORDER, budget: int = 0, r_stop: float = 0.0):
+               propagation: int = PROP_FIRST_ORDER, budget: int = 0, r_stop: float = 0.0,
+               partitioner: int = PART_RANDOM):
     torch = _torch()
     xp, dt, n, d, ld = _xdesc(X)
     h = h or handle(X.device.index or 0)
     ids = _out((n, k), torch.int32, X.device, ids)
     dists = _out((n, k), torch.float32, X.device, dists)
     p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric,
-                    propagation=propagation, budget=budget, r_stop=r_stop)
+                    propagation=propagation, budget=budget, r_stop=r_stop, partitioner=partitioner)
     h.check(lib().knng_build(h.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
                              _stream(X.device, stream)), "knng_build")
     return ids, dists
@@ -240,7 +243,7 @@ def knng_build(X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, resco
 def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32,
                     rescore_mult=2, ids=None, dists=None, stream=None, device: int = 0,
                     h: Handle = None, metric: int = METRIC_L2, propagation: int = PROP_FIRST_ORDER,
-                    budget: int = 0, r_stop: float = 0.0):
+                    budget: int = 0, r_stop: float = 0.0, partitioner: int = PART_RANDOM):
     """Host arrays in and out (X float32/float16/uint8 [n, d], unit stride along d)."""
     X = np.asarray(X)
     if X.ndim != 2 or X.strides[1] != X.itemsize:
@@ -257,7 +260,7 @@ def knng_build_host(X: np.ndarray, k, T, leaf_size, prop_rounds, seed, precision
         dists = np.empty((n, k), dtype=np.float32)
     h = h or handle(device)
     p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, metric=metric,
-                    propagation=propagation, budget=budget, r_stop=r_stop)
+                    propagation=propagation, budget=budget, r_stop=r_stop, partitioner=partitioner)
     torch = _torch()
     st = _stream(torch.device("cuda", device), stream)
     h.check(lib().knng_build_host(h.ptr, ctypes.c_void_p(X.ctypes.data), dt, n, d, ld, ctypes.byref(p),
@@ -274,6 +277,31 @@ def knng_partition(X, T, leaf_size, seed, perm=None, stream=None, h: Handle = No
     h.check(lib().knng_partition(h.ptr, xp, dt, n, d, ld, int(T), int(leaf_size), int(seed) & (2**64 - 1),
                                  _ptr(perm), _stream(X.device, stream)), "knng_partition")
     return perm
+
+
+def knng_split_levels(n: int, leaf_size: int) -> int:
+    out = ctypes.c_int32()
+    rc = lib().knng_split_levels(int(n), int(leaf_size), ctypes.byref(out))
+    if rc != KNNG_OK:
+        raise KnngError(rc, "knng_split_levels")
+    return int(out.value)
+
+
+def knng_partition_pca(X, T, leaf_size, seed, perm=None, with_dirs=False, stream=None, h: Handle = None):
+    """Principal-direction trees; returns perm [T, n] (and, with with_dirs,
+    the directions [T, 2^L - 1, d] by (level, node))."""
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    perm = _out((T, n), torch.int32, X.device, perm)
+    dirs = None
+    if with_dirs:
+        L = knng_split_levels(n, leaf_size)
+        dirs = torch.zeros((T, 2 ** L - 1, d), dtype=torch.float32, device=X.device)
+    h.check(lib().knng_partition_pca(h.ptr, xp, dt, n, d, ld, int(T), int(leaf_size), int(seed) & (2**64 - 1),
+                                     _ptr(perm), _ptr(dirs) if dirs is not None else None,
+                                     _stream(X.device, stream)), "knng_partition_pca")
+    return (perm, dirs) if with_dirs else perm
 
 
 def knng_leaf_knn(X, T, leaf_size, perm, k, precision=PREC_FP32, rescore_mult=2, ids=None,

@@ -240,7 +240,8 @@ int check_params(knng_handle* h, const knng_params* p, int64_t n)
     if ((r = check_k(h, p->k, n > p->leaf_size ? p->leaf_size : -1))) return r;
     if (p->prop_rounds < 0 || p->prop_rounds > 16) return fail(h, KNNG_ERR_INVALID_ARG, "prop_rounds %d", p->prop_rounds);
     if (p->rescore_mult < 1 || p->rescore_mult > 4) return fail(h, KNNG_ERR_INVALID_ARG, "rescore_mult %d", p->rescore_mult);
-    if (p->partitioner != KNNG_PART_RANDOM) return fail(h, KNNG_ERR_UNSUPPORTED, "partitioner %d", p->partitioner);
+    if (p->partitioner != KNNG_PART_RANDOM && p->partitioner != KNNG_PART_PCA)
+        return fail(h, KNNG_ERR_INVALID_ARG, "partitioner %d", p->partitioner);
     if (p->metric != KNNG_METRIC_L2 && p->metric != KNNG_METRIC_COSINE)
         return fail(h, KNNG_ERR_INVALID_ARG, "metric %d", p->metric);
     if (p->propagation != KNNG_PROP_FIRST_ORDER && p->propagation != KNNG_PROP_BEST_FIRST &&
@@ -296,6 +297,9 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         xb_bad = a.take<int>(1);
     }
     unsigned long long* rate_cnt = a.take<unsigned long long>(2);
+    PcaOpt pca;
+    pca.on = p.partitioner == KNNG_PART_PCA;
+    if (pca.on && x.d > 1024) return fail(h, KNNG_ERR_UNSUPPORTED, "principal directions support d <= 1024");
     const bool adaptive = p.r_stop > 0.f;
     PairScratch pw;
     if (p.propagation == KNNG_PROP_PAIRWISE && R > 0) pairwise_take(a, n, k, pw);
@@ -328,7 +332,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
     }
     int cur = 0;  // bi[cur] / bd[cur]: the merged graph when R > 0
     if (!adaptive) {
-        e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf);
+        e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf, 0, &pca);
         if (e != cudaSuccess) return cuda_fail(h, e, "partition");
         mark(1);
         const size_t part_end = a.off;
@@ -352,7 +356,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         for (int t0 = 0; t0 < T && !stop; t0 += kChunk) {
             const int tc = std::min(kChunk, T - t0);
             const size_t base = a.off;
-            e = run_partition(x, P, dp, tc, p.seed, perm + (size_t)t0 * n, a, st, lf, t0);
+            e = run_partition(x, P, dp, tc, p.seed, perm + (size_t)t0 * n, a, st, lf, t0, &pca);
             if (e != cudaSuccess) return cuda_fail(h, e, "partition");
             const size_t part_end = a.off;
             a.off = base;
@@ -531,6 +535,41 @@ int knng_partition(knng_handle* h, const void* X, int32_t dtype, int64_t n, int3
     Arena a;
     a.base = h->ws;
     cudaError_t e = run_partition(x, h->plan, h->dplan, T, seed, perm, a, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "partition");
+    return KNNG_OK;
+}
+
+int knng_split_levels(int64_t n, int32_t g, int32_t* levels)
+{
+    if (!levels || n < 1 || g < 1) return KNNG_ERR_INVALID_ARG;
+    TreePlan P;
+    make_tree_plan(n, g, P);
+    *levels = (int32_t)P.levels.size();
+    return KNNG_OK;
+}
+
+int knng_partition_pca(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld, int32_t T,
+                       int32_t g, uint64_t seed, int32_t* perm, float* dirs_out, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    if ((r = check_tree(h, T, g))) return r;
+    if (!perm) return fail(h, KNNG_ERR_INVALID_ARG, "perm is NULL");
+    if (d > 1024) return fail(h, KNNG_ERR_UNSUPPORTED, "principal directions support d <= 1024");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((r = ensure_plan(h, n, g, st))) return r;
+    PcaOpt pca;
+    pca.on = true;
+    pca.out = dirs_out;
+    pca.stride = ((((int64_t)1) << h->plan.levels.size()) - 1) * d;
+    Arena m;
+    run_partition(x, h->plan, h->dplan, T, seed, nullptr, m, st, nullptr, 0, &pca);
+    if ((r = ensure_ws(h, m.off, st))) return r;
+    Arena a;
+    a.base = h->ws;
+    const cudaError_t e = run_partition(x, h->plan, h->dplan, T, seed, perm, a, st, nullptr, 0, &pca);
     if (e != cudaSuccess) return cuda_fail(h, e, "partition");
     return KNNG_OK;
 }

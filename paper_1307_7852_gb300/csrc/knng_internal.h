@@ -135,10 +135,21 @@ cudaError_t run_feature_range(const float* Z, int64_t n, int C, uint32_t* scratc
 void learned_feature_order(uint64_t seed, int T, int C, LearnedFeat& lf);
 
 // ---- stages (each carves its scratch from the arena) -------------------
+// Principal-direction splits (Sec. 3.4): on, and an optional output of the
+// directions, tree t's node (level, v) at out[t * stride + (2^level - 1 + v) * d].
+struct PcaOpt {
+    bool on = false;
+    float* out = nullptr;
+    int64_t stride = 0;
+};
+cudaError_t run_pca_dirs(const XDesc& x, int T, int S, const SplitNode* nodes, const int32_t* cur, int dp,
+                         uint32_t level, uint64_t seed, int t0, float* dirs, float* out, int64_t out_tree_stride,
+                         cudaStream_t st);
+
 // Trees t0 .. t0 + T - 1 (perm_out[T][n]).
 cudaError_t run_partition(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
                           uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st,
-                          const LearnedFeat* lf = nullptr, int t0 = 0);
+                          const LearnedFeat* lf = nullptr, int t0 = 0, const PcaOpt* pca = nullptr);
 
 cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                              const int32_t* perm, int k, int kp, int32_t* ids, float* dists,

@@ -644,7 +644,7 @@ static inline int grid_for(int64_t work, int per_block, int cap)
 
 cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                           uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st, const LearnedFeat* lf,
-                          int t0)
+                          int t0, const PcaOpt* pca)
 {
     const int64_t n = x.n;
     const int d_pad = (x.d + 3) & ~3;
@@ -700,6 +700,12 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(
             dirs, T, S, x.d, d_pad, nodes, (uint32_t)lvl, seed, (uint32_t)t0);
         note_launches(1);
+        if (pca && pca->on) {
+            // principal directions of the nodes' samples, from the random ones
+            const cudaError_t e = run_pca_dirs(x, T, S, nodes, cur, d_pad, (uint32_t)lvl, seed, t0, dirs, pca->out,
+                                               pca->stride, st);
+            if (e != cudaSuccess) return e;
+        }
         const int pgrid = grid_for(n * 32, 256, sms * 16);
         auto project = [&](auto dt) {
             constexpr int kDT = decltype(dt)::value;
