@@ -230,6 +230,41 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[E])
     }
 }
 
+// The same network on 32-bit values.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort32(uint32_t (&v)[E])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kk = 2; kk <= 32 * E; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                const int lj = j / E;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = lane * E + e;
+                    const uint32_t other = __shfl_xor_sync(KNNG_FULL_MASK, v[e], lj);
+                    const bool keep_min = ((i & j) == 0) == ((i & kk) == 0);
+                    v[e] = keep_min ? min(v[e], other) : max(v[e], other);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int p = e ^ j;
+                    if (p > e) {
+                        const int i = lane * E + e;
+                        const bool up = (i & kk) == 0;
+                        const uint32_t lo = min(v[e], v[p]), hi = max(v[e], v[p]);
+                        v[e] = up ? lo : hi;
+                        v[p] = up ? hi : lo;
+                    }
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
     uint32_t m;
@@ -362,11 +397,12 @@ namespace knng {
 
 // Sorted `want` smallest (want <= 64) of cnt unique keys key(0..cnt)
 // (cnt <= 32*PER), written ascending to out[0..min(want, cnt)) in shared
-// memory; returns that count.  The want-th smallest of the lane minima (or,
-// for want > 32, of the two smallest keys of every lane) bounds the want-th
-// smallest of all keys from above, so the keys up to it contain the answer;
-// usually few (<= 64) do and one small bitonic sort finishes.  Otherwise the
-// radix select decides.
+// memory; returns that count.  The want-th smallest distance part (high 32
+// bits) among the lane minima (or, for want > 32, among every lane's two
+// smallest keys) bounds the answer from above: the keys whose distance part
+// is at most that value contain it.  Usually few do: up to 32 are ranked by
+// counting, up to 128 sorted by a small bitonic network; otherwise the radix
+// select decides.
 // scratch: >= 128 keys, hist: 256 words, both private to the warp.
 template <int PER, class KeyFn>
 __device__ int warp_topk_sorted(const KeyFn& key, int cnt, int want, uint64_t* out, uint64_t* scratch,
@@ -376,40 +412,52 @@ __device__ int warp_topk_sorted(const KeyFn& key, int cnt, int want, uint64_t* o
     if (want > cnt) want = cnt;
     if (want <= 0) return 0;
     uint64_t x[PER];
-    uint64_t a = kKeyMax, b = kKeyMax;
+    // distance parts (high 32 bits) of each lane's two smallest keys
+    uint32_t a = 0xFFFFFFFFu, b = 0xFFFFFFFFu;
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
         const int idx = lane + 32 * e;
         x[e] = idx < cnt ? key(idx) : kKeyMax;
-        if (x[e] < a) { b = a; a = x[e]; }
-        else if (x[e] < b) b = x[e];
+        const uint32_t h = (uint32_t)(x[e] >> 32);
+        if (h < a) { b = a; a = h; }
+        else if (h < b) b = h;
     }
+    // tau: the want-th smallest of those distance parts.  At least `want`
+    // keys have a distance part <= tau, so every key of the answer does too.
     const int wi = want - 1;
-    uint64_t tau;
+    uint32_t tau;
     if (want <= 32) {
-        // the want-th smallest lane minimum is already an upper bound
-        uint64_t s1[1] = {a};
-        warp_bitonic_sort<1>(s1);
+        uint32_t s1[1] = {a};
+        warp_bitonic_sort32<1>(s1);
         tau = __shfl_sync(KNNG_FULL_MASK, s1[0], wi);
     } else {
-        uint64_t s2[2] = {a, b};
-        warp_bitonic_sort<2>(s2);
+        uint32_t s2[2] = {a, b};
+        warp_bitonic_sort32<2>(s2);
         tau = __shfl_sync(KNNG_FULL_MASK, (wi & 1) ? s2[1] : s2[0], wi >> 1);
     }
     int c = 0;
 #pragma unroll
-    for (int e = 0; e < PER; ++e) c += __popc(__ballot_sync(KNNG_FULL_MASK, x[e] <= tau));
+    for (int e = 0; e < PER; ++e) c += __popc(__ballot_sync(KNNG_FULL_MASK, (uint32_t)(x[e] >> 32) <= tau));
     if (c <= 128) {
         int base = 0;
 #pragma unroll
         for (int e = 0; e < PER; ++e) {
-            const bool sel = x[e] <= tau;
+            const bool sel = (uint32_t)(x[e] >> 32) <= tau;
             const uint32_t bl = __ballot_sync(KNNG_FULL_MASK, sel);
             if (sel) scratch[base + __popc(bl & lanemask_lt())] = x[e];
             base += __popc(bl);
         }
         __syncwarp();
-        if (c <= 64) {
+        if (c <= 32) {
+            // rank by counting (position breaks equal keys, so ranks differ)
+            const uint64_t v = lane < c ? scratch[lane] : kKeyMax;
+            int rank = 0;
+            for (int j = 0; j < c; ++j) {
+                const uint64_t y = scratch[j];
+                rank += (y < v || (y == v && j < lane)) ? 1 : 0;
+            }
+            if (lane < c && rank < want) out[rank] = v;
+        } else if (c <= 64) {
             uint64_t v[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) v[e] = lane * 2 + e < c ? scratch[lane * 2 + e] : kKeyMax;
@@ -564,6 +612,21 @@ __device__ __forceinline__ float warp_canon_dist16(const RowLoader<kDT>& L, int6
         if (lane == c) mine = dd;
     }
     return mine;
+}
+
+// Canonical distances from a to b[0..nb) (nb <= 32): lane c < nb returns the
+// distance to b[c].  Byte rows with exact integer distances take one batch
+// of 32 (32 rows in flight per warp), other rows two batches of 16.
+template <int kDT>
+__device__ __forceinline__ float warp_canon_dist32(const RowLoader<kDT>& L, int64_t a, const int* b, int nb)
+{
+    if (kDT == kDtU8 && L.all_vec() && L.int_exact()) return warp_u8_dist_batch<32>(L, a, b, nb);
+    const int lane = threadIdx.x & 31;
+    const float lo = warp_canon_dist16(L, a, b, min(nb, 16));
+    float hi = 0.f;
+    if (nb > 16) hi = warp_canon_dist16(L, a, b + 16, nb - 16);
+    const float hi_l = __shfl_sync(KNNG_FULL_MASK, hi, lane & 15);
+    return lane < 16 ? lo : hi_l;
 }
 
 // Finishes one row of a leaf graph (collective over one warp): from the

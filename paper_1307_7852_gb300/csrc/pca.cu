@@ -11,9 +11,10 @@
 //  3. Lanczos with full reorthogonalisation (Gram-Schmidt twice) on
 //     C = A^T A / s from the node's random direction, at most min(8, d)
 //     steps, stopping once beta_j <= 1e-4 * max alpha;
-//  4. the top eigenvector of the tridiagonal matrix (cyclic Jacobi in
-//     FP64 by one thread), the Ritz vector, normalised, its largest entry
-//     made positive (ties: the lowest index).
+//  4. the top eigenvector of the tridiagonal matrix (one warp: Sturm
+//     multisection for the eigenvalue, inverse iteration for the vector),
+//     the Ritz vector, normalised, its largest entry made positive (ties:
+//     the lowest index).
 // The direction replaces the node's random direction before the projection
 // (the split itself is unchanged) and is optionally written out by
 // (level, node) for replay.
@@ -41,61 +42,98 @@ size_t pca_smem_bytes(int d)
 {
     const int dp = (d + 3) & ~3;
     const int s = pca_sample_cap(d);
-    return sizeof(float) * ((size_t)s * dp + (size_t)(kPcaSteps + 1) * dp + 2 * (size_t)dp + 128 + 64);
+    return sizeof(float) * ((size_t)s * dp + (size_t)(kPcaSteps + 1) * dp + 2 * (size_t)dp + 128 +
+                            (kPcaThreads / 32) * kPcaSteps + 8);
 }
 
-// Sum over the block (fixed order: lane butterflies, then the warps in order).
-__device__ __forceinline__ float pca_block_sum(float v, float* red)
+// Number of eigenvalues of the symmetric tridiagonal matrix (alpha, beta)
+// below x (Sturm sequence of the LDL^T pivots).
+__device__ __forceinline__ int sturm_below(const float* alpha, const float* beta, int q, float x)
+{
+    int c = 0;
+    float dv = 1.f;
+    for (int i = 0; i < q; ++i) {
+        const float b2 = i > 0 ? beta[i - 1] * beta[i - 1] : 0.f;
+        dv = (alpha[i] - x) - (i > 0 ? b2 / dv : 0.f);
+        if (dv == 0.f) dv = -1e-30f;
+        c += dv < 0.f ? 1 : 0;
+    }
+    return c;
+}
+
+// Top eigenvector of the symmetric tridiagonal q x q matrix (alpha, beta),
+// q <= 8, by one warp: the largest eigenvalue by 33-way multisection of the
+// Gershgorin interval on Sturm counts, then two steps of inverse iteration
+// (tridiagonal elimination) on lane 0.  y: q entries (not normalised).
+__device__ void tridiag_top(const float* alpha, const float* beta, int q, float* y)
+{
+    const int lane = threadIdx.x & 31;
+    float lo = 3.4e38f, hi = -3.4e38f;
+    for (int i = 0; i < q; ++i) {
+        const float r = (i > 0 ? fabsf(beta[i - 1]) : 0.f) + (i + 1 < q ? fabsf(beta[i]) : 0.f);
+        lo = fminf(lo, alpha[i] - r);
+        hi = fmaxf(hi, alpha[i] + r);
+    }
+    hi += 1e-6f * (fabsf(hi) + fabsf(lo)) + 1e-30f;
+    for (int it = 0; it < 8; ++it) {
+        const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+        const bool above = sturm_below(alpha, beta, q, x) == q;  // x above every eigenvalue
+        const uint32_t m = __ballot_sync(KNNG_FULL_MASK, above);
+        const int first = m ? __ffs(m) - 1 : 32;
+        const float nhi = first < 32 ? lo + (hi - lo) * (float)(first + 1) / 33.f : hi;
+        const float nlo = lo + (hi - lo) * (float)first / 33.f;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) {
+        const float lam = 0.5f * (lo + hi);
+        float v[8], dd[8], cc[8];
+        for (int i = 0; i < q; ++i) v[i] = 1.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            // solve (T - lam I) z = v by elimination without pivoting
+            for (int i = 0; i < q; ++i) {
+                float piv = alpha[i] - lam - (i > 0 ? beta[i - 1] * cc[i - 1] : 0.f);
+                if (fabsf(piv) < 1e-30f) piv = 1e-30f;
+                cc[i] = i + 1 < q ? beta[i] / piv : 0.f;
+                dd[i] = (v[i] - (i > 0 ? beta[i - 1] * dd[i - 1] : 0.f)) / piv;
+            }
+            for (int i = q - 1; i >= 0; --i) v[i] = dd[i] - (i + 1 < q ? cc[i] * v[i + 1] : 0.f);
+            float nn = 0.f;
+            for (int i = 0; i < q; ++i) nn = fmaxf(nn, fabsf(v[i]));
+            for (int i = 0; i < q; ++i) v[i] /= nn;
+        }
+        for (int i = 0; i < q; ++i) y[i] = v[i];
+    }
+    __syncwarp();
+}
+
+// Sums of cnt per-thread values over the block (fixed order); red holds
+// (threads / 32) * kPcaSteps + 8 floats.
+template <int N>
+__device__ __forceinline__ void pca_block_sums(float (&v)[N], int cnt, float* red)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(KNNG_FULL_MASK, v, o);
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    float s = 0.f;
-    for (int i = 0; i < kPcaThreads / 32; ++i) s += red[i];
-    return s;
-}
-
-// Largest eigenpair of the symmetric q x q matrix T (q <= 8), cyclic Jacobi.
-__device__ void jacobi_top(double (&T)[kPcaSteps][kPcaSteps], int q, double* y)
-{
-    double Vm[kPcaSteps][kPcaSteps];
-    for (int i = 0; i < q; ++i)
-        for (int j = 0; j < q; ++j) Vm[i][j] = i == j ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        double off = 0.0;
-        for (int i = 0; i < q; ++i)
-            for (int j = i + 1; j < q; ++j) off += T[i][j] * T[i][j];
-        if (off < 1e-300) break;
-        for (int p = 0; p < q; ++p)
-            for (int r = p + 1; r < q; ++r) {
-                if (T[p][r] == 0.0) continue;
-                const double theta = (T[r][r] - T[p][p]) / (2.0 * T[p][r]);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < q; ++k) {  // columns p, r
-                    const double a = T[k][p], b = T[k][r];
-                    T[k][p] = c * a - s * b;
-                    T[k][r] = s * a + c * b;
-                }
-                for (int k = 0; k < q; ++k) {  // rows p, r
-                    const double a = T[p][k], b = T[r][k];
-                    T[p][k] = c * a - s * b;
-                    T[r][k] = s * a + c * b;
-                }
-                for (int k = 0; k < q; ++k) {
-                    const double a = Vm[k][p], b = Vm[k][r];
-                    Vm[k][p] = c * a - s * b;
-                    Vm[k][r] = s * a + c * b;
-                }
-            }
+    for (int i = 0; i < N; ++i) {
+        if (i < cnt) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) v[i] += __shfl_xor_sync(KNNG_FULL_MASK, v[i], o);
+        }
     }
-    int top = 0;
-    for (int i = 1; i < q; ++i)
-        if (T[i][i] > T[top][top]) top = i;
-    for (int i = 0; i < q; ++i) y[i] = Vm[i][top];
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < cnt) red[w * N + i] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i < cnt) {
+            float s = 0.f;
+            for (int ww = 0; ww < kPcaThreads / 32; ++ww) s += red[ww * N + i];
+            v[i] = s;
+        }
+    }
 }
 
 template <class Loader>
@@ -116,8 +154,7 @@ __device__ void pca_node(const Loader& L, int64_t n, const SplitNode& nd, const 
     float* red = u + 128;                   // 8 warp partials (+ spare)
     __shared__ int rows[128];
     __shared__ float alpha[kPcaSteps], beta[kPcaSteps];
-    __shared__ int qsteps;
-    __shared__ double ysh[kPcaSteps];
+    __shared__ float ysh[kPcaSteps];
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
 
     // 1. sample
@@ -135,9 +172,17 @@ __device__ void pca_node(const Loader& L, int64_t n, const SplitNode& nd, const 
     }
     __syncthreads();
     // 2. rows, mean, centring
-    for (int e = tid; e < s * d; e += kPcaThreads) {
-        const int r = e / d, j = e - (e / d) * d;
-        A[(size_t)r * dp + j] = L.load1(rows[r], j);
+    if (L.all_vec()) {
+        const int d4 = d >> 2;
+        for (int e = tid; e < s * d4; e += kPcaThreads) {
+            const int r = e / d4, j = 4 * (e - (e / d4) * d4);
+            *reinterpret_cast<float4*>(A + (size_t)r * dp + j) = L.load4v(rows[r], j);
+        }
+    } else {
+        for (int e = tid; e < s * d; e += kPcaThreads) {
+            const int r = e / d, j = e - (e / d) * d;
+            A[(size_t)r * dp + j] = L.load1(rows[r], j);
+        }
     }
     __syncthreads();
     for (int j = tid; j < d; j += kPcaThreads) {
@@ -151,17 +196,18 @@ __device__ void pca_node(const Loader& L, int64_t n, const SplitNode& nd, const 
         A[(size_t)r * dp + j] -= mu[j];
     }
     // start vector: the node's random direction, normalised
-    float part = 0.f;
+    float v1[1] = {0.f};
     for (int j = tid; j < d; j += kPcaThreads) {
         const float x = dir[j];
         V[j] = x;
-        part = fmaf(x, x, part);
+        v1[0] = fmaf(x, x, v1[0]);
     }
-    const float nv = sqrtf(pca_block_sum(part, red));
+    pca_block_sums(v1, 1, red);
+    const float nv = sqrtf(v1[0]);
     for (int j = tid; j < d; j += kPcaThreads) V[j] /= nv;
     __syncthreads();
 
-    // 3. Lanczos
+    // 3. Lanczos with full reorthogonalisation
     const int steps = d < kPcaSteps ? d : kPcaSteps;
     float amax = 0.f;
     int q = 0;
@@ -176,16 +222,16 @@ __device__ void pca_node(const Loader& L, int64_t n, const SplitNode& nd, const 
             if (lane == 0) u[r] = acc;
         }
         __syncthreads();
-        // w = A^T u / s
+        // w = A^T u / s, and alpha = w . v_j
+        v1[0] = 0.f;
         for (int c = tid; c < d; c += kPcaThreads) {
             float acc = 0.f;
             for (int r = 0; r < s; ++r) acc = fmaf(A[(size_t)r * dp + c], u[r], acc);
             w[c] = acc / (float)s;
+            v1[0] = fmaf(w[c], vj[c], v1[0]);
         }
-        __syncthreads();
-        part = 0.f;
-        for (int c = tid; c < d; c += kPcaThreads) part = fmaf(w[c], vj[c], part);
-        const float a = pca_block_sum(part, red);
+        pca_block_sums(v1, 1, red);
+        const float a = v1[0];
         amax = fmaxf(amax, a);
         const float bprev = j > 0 ? beta[j - 1] : 0.f;
         for (int c = tid; c < d; c += kPcaThreads) {
@@ -193,24 +239,29 @@ __device__ void pca_node(const Loader& L, int64_t n, const SplitNode& nd, const 
             if (j > 0) x -= bprev * V[(size_t)(j - 1) * dp + c];
             w[c] = x;
         }
-        __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
             float coef[kPcaSteps];
-            for (int i = 0; i <= j; ++i) {
-                part = 0.f;
-                for (int c = tid; c < d; c += kPcaThreads) part = fmaf(V[(size_t)i * dp + c], w[c], part);
-                coef[i] = pca_block_sum(part, red);
+#pragma unroll
+            for (int i = 0; i < kPcaSteps; ++i) coef[i] = 0.f;
+            for (int c = tid; c < d; c += kPcaThreads) {
+                const float wc = w[c];
+#pragma unroll
+                for (int i = 0; i < kPcaSteps; ++i)
+                    if (i <= j) coef[i] = fmaf(V[(size_t)i * dp + c], wc, coef[i]);
             }
+            pca_block_sums(coef, j + 1, red);
             for (int c = tid; c < d; c += kPcaThreads) {
                 float x = w[c];
-                for (int i = 0; i <= j; ++i) x -= coef[i] * V[(size_t)i * dp + c];
+#pragma unroll
+                for (int i = 0; i < kPcaSteps; ++i)
+                    if (i <= j) x -= coef[i] * V[(size_t)i * dp + c];
                 w[c] = x;
             }
-            __syncthreads();
         }
-        part = 0.f;
-        for (int c = tid; c < d; c += kPcaThreads) part = fmaf(w[c], w[c], part);
-        const float b = sqrtf(pca_block_sum(part, red));
+        v1[0] = 0.f;
+        for (int c = tid; c < d; c += kPcaThreads) v1[0] = fmaf(w[c], w[c], v1[0]);
+        pca_block_sums(v1, 1, red);
+        const float b = sqrtf(v1[0]);
         if (tid == 0) {
             alpha[j] = a;
             beta[j] = b;
@@ -221,28 +272,18 @@ __device__ void pca_node(const Loader& L, int64_t n, const SplitNode& nd, const 
         __syncthreads();
     }
     __syncthreads();
-    // 4. tridiagonal eigenvector, Ritz vector
-    if (tid == 0) {
-        double Tm[kPcaSteps][kPcaSteps];
-        for (int i = 0; i < q; ++i)
-            for (int k = 0; k < q; ++k) Tm[i][k] = 0.0;
-        for (int i = 0; i < q; ++i) Tm[i][i] = alpha[i];
-        for (int i = 0; i + 1 < q; ++i) Tm[i][i + 1] = Tm[i + 1][i] = beta[i];
-        double y[kPcaSteps];
-        jacobi_top(Tm, q, y);
-        for (int i = 0; i < q; ++i) ysh[i] = y[i];
-        qsteps = q;
-    }
+    // 4. tridiagonal eigenvector (one warp), Ritz vector
+    if (wp == 0) tridiag_top(alpha, beta, q, ysh);
     __syncthreads();
-    q = qsteps;
-    part = 0.f;
+    v1[0] = 0.f;
     for (int c = tid; c < d; c += kPcaThreads) {
-        double x = 0.0;
-        for (int i = 0; i < q; ++i) x += ysh[i] * (double)V[(size_t)i * dp + c];
-        w[c] = (float)x;
-        part = fmaf(w[c], w[c], part);
+        float x = 0.f;
+        for (int i = 0; i < q; ++i) x = fmaf(ysh[i], V[(size_t)i * dp + c], x);
+        w[c] = x;
+        v1[0] = fmaf(x, x, v1[0]);
     }
-    const float nrm = sqrtf(pca_block_sum(part, red));
+    pca_block_sums(v1, 1, red);
+    const float nrm = sqrtf(v1[0]);
     // sign: the largest-magnitude entry positive (ties: the lowest index)
     float best = -1.f;
     int bi = 0x7FFFFFFF;

@@ -124,32 +124,40 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         // i = e*k + f = lane + 32*step, advanced without division
         int e = lane / k, f = lane - (lane / k) * k;
         const int de = 32 / k, df = 32 - (32 / k) * k;
-        for (int i0 = 0; i0 < kk; i0 += 32) {
-            int32_t o = -1;
-            if (i0 + lane < kk) {
-                const int32_t q = own[e];
-                if (q >= 0 && q != p) {
-                    const bool qnew = (pf >> e) & 1ull;
-                    const bool cnew = flags_in ? ((own_fl[e] >> f) & 1ull) : true;
-                    if (qnew || cnew) o = ids_in[(int64_t)q * k + f];
-                    if (o >= n) o = -1;
+        constexpr int G = 4;  // list loads in flight per lane before the hash inserts
+        for (int i0 = 0; i0 < kk; i0 += 32 * G) {
+            int32_t o[G];
+#pragma unroll
+            for (int gi = 0; gi < G; ++gi) {
+                o[gi] = -1;
+                if (i0 + 32 * gi + lane < kk) {
+                    const int32_t q = own[e];
+                    if (q >= 0 && q != p) {
+                        const bool qnew = (pf >> e) & 1ull;
+                        const bool cnew = flags_in ? ((own_fl[e] >> f) & 1ull) : true;
+                        if (qnew || cnew) o[gi] = ids_in[(int64_t)q * k + f];
+                    }
                 }
+                e += de;
+                f += df;
+                if (f >= k) { f -= k; ++e; }
             }
-            const bool ins = o >= 0 && hash_insert(tab, (uint32_t)hshift, hmask, o);
-            const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
-            if (ins) cid[cnt + __popc(b & lanemask_lt())] = o;
-            cnt += __popc(b);
-            e += de;
-            f += df;
-            if (f >= k) { f -= k; ++e; }
+#pragma unroll
+            for (int gi = 0; gi < G; ++gi) {
+                const int32_t oo = o[gi] < n ? o[gi] : -1;
+                const bool ins = oo >= 0 && hash_insert(tab, (uint32_t)hshift, hmask, oo);
+                const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
+                if (ins) cid[cnt + __popc(b & lanemask_lt())] = oo;
+                cnt += __popc(b);
+            }
         }
         __syncwarp();
         // score the new candidates, 32 at a time
-        for (int c0 = nknown; c0 < cnt; c0 += 16) {
-            const int nb = min(16, cnt - c0);
+        for (int c0 = nknown; c0 < cnt; c0 += 32) {
+            const int nb = min(32, cnt - c0);
             float dd;
-            if (kDT == kDtF32 && bytes) dd = warp_canon_dist16(Lb, p, cid + c0, nb);
-            else dd = warp_canon_dist16(L, p, cid + c0, nb);
+            if (kDT == kDtF32 && bytes) dd = warp_canon_dist32(Lb, p, cid + c0, nb);
+            else dd = warp_canon_dist32(L, p, cid + c0, nb);
             if (lane < nb) cd[c0 + lane] = dd;
         }
         __syncwarp();

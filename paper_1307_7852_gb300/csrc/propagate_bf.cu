@@ -86,11 +86,11 @@ __global__ void __launch_bounds__(256, 2) propagate_bf_kernel(RowLoader<kDT> L, 
             if (fresh && pos < budget) vid[pos] = o;
             const int end = min(cnt + __popc(b), budget);
             __syncwarp();
-            for (int c0 = cnt; c0 < end; c0 += 16) {
-                const int nb = min(16, end - c0);
+            for (int c0 = cnt; c0 < end; c0 += 32) {
+                const int nb = min(32, end - c0);
                 float dd;
-                if (kDT == kDtF32 && bytes) dd = warp_canon_dist16(Lb, p, vid + c0, nb);
-                else dd = warp_canon_dist16(L, p, vid + c0, nb);
+                if (kDT == kDtF32 && bytes) dd = warp_canon_dist32(Lb, p, vid + c0, nb);
+                else dd = warp_canon_dist32(L, p, vid + c0, nb);
                 if (lane < nb) vkey[c0 + lane] = pack_key(dd, (uint32_t)vid[c0 + lane]);
             }
             cnt = end;
