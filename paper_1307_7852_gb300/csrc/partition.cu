@@ -322,22 +322,89 @@ __device__ __forceinline__ void project_body(const Loader& L, int64_t n, int T, 
 }
 
 // Float rows whose byte copy is exact (*xb_bad == 0, see XDesc) are read from
-// the copy: the same float values, a quarter of the bytes.
+// the copy: the same float values, a quarter of the bytes.  With
+// bytes_elsewhere set, such a build is left to project_bytes_kernel.
 template <int kDT, bool kLearned>
 __global__ void __launch_bounds__(256) project_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
-                                                      const int* __restrict__ xb_bad, int64_t n, int T,
-                                                      const float* __restrict__ dirs, int S, int d_pad,
-                                                      const int32_t* __restrict__ node_of,
+                                                      const int* __restrict__ xb_bad, bool bytes_elsewhere,
+                                                      int64_t n, int T, const float* __restrict__ dirs, int S,
+                                                      int d_pad, const int32_t* __restrict__ node_of,
                                                       const int32_t* __restrict__ pos_of,
                                                       uint32_t* __restrict__ keys, LevelFeat lv)
 {
     if constexpr (kDT == kDtF32) {
         if (xb_bad && *xb_bad == 0) {
+            if (bytes_elsewhere) return;
             project_body<kLearned>(Lb, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
             return;
         }
     }
     project_body<kLearned>(L, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
+}
+
+// Node-major projection of byte rows (16-byte aligned, rows padded to
+// multiples of 16 bytes): one thread per (tree, position).  Threads of a
+// warp take consecutive positions, i.e. mostly the same node, so the
+// direction is one broadcast load per 16 bytes while every thread gathers
+// its own row (d bytes).  The thread forms the 32 lane partials of the
+// canonical order (lane l: j = 128c + 4l + e, fmaf) and the pairwise rounds
+// 16, 8, 4, 2, 1 itself, so the value is the one of the warp-cooperative
+// projection bit for bit.  Unless bytes_given, it runs only when the byte
+// copy of float rows is exact (*xb_bad == 0).
+__global__ void __launch_bounds__(256) project_bytes_kernel(RowLoader<kDtU8> Lb, const int* __restrict__ xb_bad,
+                                                            bool bytes_given, int64_t n, int T,
+                                                            const float* __restrict__ dirs, int S, int d_pad,
+                                                            const int32_t* __restrict__ cur,
+                                                            const int32_t* __restrict__ node_of,
+                                                            uint32_t* __restrict__ keys)
+{
+    if (!bytes_given && (!xb_bad || *xb_bad != 0)) return;
+    const int d = Lb.d;
+    const int64_t total = (int64_t)T * n;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(g / n);
+        const int32_t id = cur[g];
+        const int sn = node_of[(int64_t)t * n + id];
+        if (sn < 0) continue;  // a leaf of an earlier level
+        const float* a = dirs + ((int64_t)t * S + sn) * d_pad;
+        const uint8_t* row = static_cast<const uint8_t*>(Lb.X) + Lb.row_off(id);
+        float acc[32];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) acc[l] = 0.f;
+        for (int c0 = 0; c0 < d; c0 += 128) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int jb = c0 + 16 * q;  // bytes jb .. jb + 15: lanes 4q .. 4q + 3
+                if (jb < d) {
+                    const uint4 w = __ldg(reinterpret_cast<const uint4*>(row + jb));
+                    const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int j = jb + 4 * h;
+                        const float4 av = __ldg(reinterpret_cast<const float4*>(a + j));
+                        const float4 xv = bytes_to_float4(wv[h]);
+                        float& s = acc[4 * q + h];
+                        if (j + 3 < d) {
+                            s = fmaf(xv.x, av.x, s);
+                            s = fmaf(xv.y, av.y, s);
+                            s = fmaf(xv.z, av.z, s);
+                            s = fmaf(xv.w, av.w, s);
+                        } else {
+                            if (j < d) s = fmaf(xv.x, av.x, s);
+                            if (j + 1 < d) s = fmaf(xv.y, av.y, s);
+                            if (j + 2 < d) s = fmaf(xv.z, av.z, s);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+            for (int l = 0; l < o; ++l) acc[l] = acc[l] + acc[l + o];
+        keys[g] = ord_key(acc[0]);
+    }
 }
 
 // ---- block radix select (one block, keys in shared memory) ---------------
@@ -707,21 +774,36 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
             if (e != cudaSuccess) return e;
         }
         const int pgrid = grid_for(n * 32, 256, sms * 16);
-        auto project = [&](auto dt) {
-            constexpr int kDT = decltype(dt)::value;
-            RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
-            const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
-            if (learned)
-                project_kernel<kDT, true><<<pgrid, 256, 0, st>>>(rl, rb, x.xb_bad, n, T, dirs, S, d_pad, node_of, pos_of,
-                                                                 keys, lv);
-            else
-                project_kernel<kDT, false><<<pgrid, 256, 0, st>>>(rl, rb, x.xb_bad, n, T, dirs, S, d_pad, node_of, pos_of,
-                                                                  keys, lv);
-        };
-        if (x.dtype == kDtF16) project(std::integral_constant<int, kDtF16>{});
-        else if (x.dtype == kDtU8) project(std::integral_constant<int, kDtU8>{});
-        else project(std::integral_constant<int, kDtF32>{});
-        note_launches(1);
+        // byte rows with 16-byte aligned, padded rows go node-major: the
+        // internal exact byte copy of float rows (decided on the device), or
+        // byte input laid out that way
+        const bool copy_nm = !learned && x.dtype == kDtF32 && x.Xb != nullptr;
+        const bool u8_nm = !learned && x.dtype == kDtU8 && ((uintptr_t)x.X % 16 == 0) && (x.ld % 16 == 0) &&
+                           (x.d % 16 == 0);
+        const int bgrid = grid_for((int64_t)T * n, 256, sms * 16);
+        if (copy_nm || u8_nm) {
+            const RowLoader<kDtU8> rb = u8_nm ? RowLoader<kDtU8>{x.X, x.ld, x.d, true}
+                                              : RowLoader<kDtU8>{x.Xb, x.ldb, x.d, true};
+            project_bytes_kernel<<<bgrid, 256, 0, st>>>(rb, x.xb_bad, u8_nm, n, T, dirs, S, d_pad, cur, node_of, keys);
+            note_launches(1);
+        }
+        if (!u8_nm) {
+            auto project = [&](auto dt) {
+                constexpr int kDT = decltype(dt)::value;
+                RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
+                const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
+                if (learned)
+                    project_kernel<kDT, true><<<pgrid, 256, 0, st>>>(rl, rb, x.xb_bad, copy_nm, n, T, dirs, S, d_pad,
+                                                                     node_of, pos_of, keys, lv);
+                else
+                    project_kernel<kDT, false><<<pgrid, 256, 0, st>>>(rl, rb, x.xb_bad, copy_nm, n, T, dirs, S, d_pad,
+                                                                      node_of, pos_of, keys, lv);
+            };
+            if (x.dtype == kDtF16) project(std::integral_constant<int, kDtF16>{});
+            else if (x.dtype == kDtU8) project(std::integral_constant<int, kDtU8>{});
+            else project(std::integral_constant<int, kDtF32>{});
+            note_launches(1);
+        }
         // leaves of this level keep their positions: start from a copy
         cudaMemcpyAsync(nxt, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);
         if (L.nbig < S) {
