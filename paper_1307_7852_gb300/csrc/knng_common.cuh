@@ -614,6 +614,35 @@ __device__ __forceinline__ float warp_canon_dist16(const RowLoader<kDT>& L, int6
     return mine;
 }
 
+// Byte rows, 16-byte aligned with rows padded to a multiple of 16 bytes and
+// d <= 128 (so every distance is an exact integer): each lane scores its
+// own candidate b[lane] (lane < nb) against the query row q[8] (bytes of a,
+// loaded once by the caller with load_query_u8) -- no exchange between lanes.
+__device__ __forceinline__ void load_query_u8(const uint8_t* X, int64_t ld, int64_t a, int d, uint4 (&q)[8])
+{
+    const uint8_t* row = X + (uint64_t)(uint32_t)a * (uint32_t)ld;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        q[c] = 16 * c < d ? __ldg(reinterpret_cast<const uint4*>(row + 16 * c)) : make_uint4(0u, 0u, 0u, 0u);
+}
+__device__ __forceinline__ float lane_u8_dist(const uint8_t* X, int64_t ld, int d, const uint4 (&q)[8], int b)
+{
+    const uint8_t* row = X + (uint64_t)(uint32_t)b * (uint32_t)ld;
+    uint32_t acc = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (16 * c < d) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4*>(row + 16 * c));
+            uint32_t t;
+            t = __vabsdiffu4(q[c].x, x.x); acc = __dp4a(t, t, acc);
+            t = __vabsdiffu4(q[c].y, x.y); acc = __dp4a(t, t, acc);
+            t = __vabsdiffu4(q[c].z, x.z); acc = __dp4a(t, t, acc);
+            t = __vabsdiffu4(q[c].w, x.w); acc = __dp4a(t, t, acc);
+        }
+    }
+    return (float)acc;
+}
+
 // Canonical distances from a to b[0..nb) (nb <= 32): lane c < nb returns the
 // distance to b[c].  Byte rows with exact integer distances take one batch
 // of 32 (32 rows in flight per warp), other rows two batches of 16.
@@ -627,6 +656,43 @@ __device__ __forceinline__ float warp_canon_dist32(const RowLoader<kDT>& L, int6
     if (nb > 16) hi = warp_canon_dist16(L, a, b + 16, nb - 16);
     const float hi_l = __shfl_sync(KNNG_FULL_MASK, hi, lane & 15);
     return lane < 16 ? lo : hi_l;
+}
+
+// Rescoring of one row's candidate list (collective over one warp):
+// keys[i * stride], i < nc <= 64, hold (D~, local index j); every candidate
+// is rescored with the canonical FP32 distance between the original rows of
+// lid[self] and lid[j], and the k best by (D, id) go to oi/od (padding -1 /
+// +inf).  ws: kLeafWarpScratch bytes of the warp.
+template <int kDT>
+__device__ void leaf_rescore_list(const RowLoader<kDT>& L, const int32_t* lid, int self, const uint64_t* keys,
+                                  int stride, int nc, int k, unsigned char* ws, int32_t* oi, float* od)
+{
+    const int lane = threadIdx.x & 31;
+    int* cid = reinterpret_cast<int*>(ws);                   // 64 point ids
+    uint64_t* rk = reinterpret_cast<uint64_t*>(ws + 1024);   // 64 rescored keys
+    for (int c = lane; c < nc; c += 32) cid[c] = lid[(uint32_t)keys[(size_t)c * stride]];
+    __syncwarp();
+    const int gi = lid[self];
+    for (int c0 = 0; c0 < nc; c0 += 16) {
+        const int nb = min(16, nc - c0);
+        const float dd = warp_canon_dist16(L, gi, cid + c0, nb);
+        if (lane < nb) rk[c0 + lane] = pack_key(dd, (uint32_t)cid[c0 + lane]);
+    }
+    __syncwarp();
+    uint64_t v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) v[e] = lane * 2 + e < nc ? rk[lane * 2 + e] : kKeyMax;
+    warp_bitonic_sort<2>(v);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int i = lane * 2 + e;
+        if (i < k) {
+            const bool ok = i < nc;
+            oi[i] = ok ? (int32_t)(uint32_t)v[e] : -1;
+            od[i] = ok ? unord_key((uint32_t)(v[e] >> 32)) : __int_as_float(0x7f800000);
+        }
+    }
+    __syncwarp();
 }
 
 // Finishes one row of a leaf graph (collective over one warp): from the

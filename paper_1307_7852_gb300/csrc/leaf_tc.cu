@@ -65,9 +65,13 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec, const TcTile* tile
         G.RG = 128;
         while (G.RG > 32 && G.RG * G.ldD * 4 > 72 * 1024) G.RG >>= 1;
     }
-    G.pipe_bytes = std::max(G.S * G.stage_bytes, G.RG * G.ldD * 4);
+    // the pipeline region is reused after the MMAs: by the row-per-thread
+    // selection (kFastSmem), by the distance block of the warp-per-row path
+    // and, past both, by the warps' selection scratch
+    G.wsc_off = (std::max(G.RG * G.ldD * 4, 72 * 1024) + 15) & ~15;
+    G.pipe_bytes = std::max(std::max(G.S * G.stage_bytes, G.wsc_off + kTcWarps * kLeafWarpScratch), kFastSmem);
     G.pipe_bytes = (G.pipe_bytes + 1023) & ~1023;
-    G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + 16 + kTcWarps * kLeafWarpScratch + (2 * G.S + 1) * 8 + 16;
+    G.smem = 1024 + G.pipe_bytes + 3 * G.N_load * 4 + 16 + (2 * G.S + 1) * 8 + 16;
     return G;
 }
 

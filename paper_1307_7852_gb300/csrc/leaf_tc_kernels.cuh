@@ -123,8 +123,38 @@ struct TcGeom {
     int RG;          // epilogue rows per group
     int ldD;         // row stride of the distance block (floats)
     int pipe_bytes;
+    int wsc_off;     // offset of the warps' selection scratch in the pipeline region
     int smem;
 };
+
+// Bitonic sorting network on a thread's own registers (N a power of two;
+// every index is a compile-time constant after unrolling).
+template <class T, int N>
+__device__ __forceinline__ void reg_bitonic_sort(T (&v)[N])
+{
+#pragma unroll
+    for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & kk) == 0;
+                    const T a = v[i], b = v[l];
+                    const bool sw = up ? (b < a) : (a < b);
+                    v[i] = sw ? b : a;
+                    v[l] = sw ? a : b;
+                }
+            }
+        }
+    }
+}
+
+// Shared memory of the row-per-thread selection (reusing the pipeline):
+// sorted group minima [32][256] u32 (later the rows' merged lists [32][128]
+// u64) and candidate lists [32][256] u64.
+constexpr int kFastSmem = 32 * kTcThreads * 4 + 32 * kTcThreads * 8;
 
 template <int PREC, int PER, int kDT>
 __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -144,8 +174,8 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
     int32_t* lid = reinterpret_cast<int32_t*>(base + G.pipe_bytes);
     float* qn = reinterpret_cast<float*>(lid + G.N_load);
     float* qs = qn + G.N_load;
-    unsigned char* wsc = reinterpret_cast<unsigned char*>(((uintptr_t)(qs + G.N_load) + 15) & ~(uintptr_t)15);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wsc + kTcWarps * kLeafWarpScratch);
+    unsigned char* wsc = pipe + G.wsc_off;  // used only after the MMAs
+    uint64_t* bars = reinterpret_cast<uint64_t*>(((uintptr_t)(qs + G.N_load) + 15) & ~(uintptr_t)15);
     uint64_t* full = bars;
     uint64_t* empty = bars + G.S;
     uint64_t* done = bars + 2 * G.S;
@@ -256,42 +286,176 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // pipeline smem is reused below
     __syncthreads();
 
-    // ---- epilogue: TMEM -> distance block -> per-row selection ----------
+    // ---- epilogue -------------------------------------------------------
+    // Row per thread first: thread (quad, half) owns row 32 quad + lane and
+    // the column chunks 32 half + 64 i of it.  Pass 1 takes the minimum of
+    // the distance parts (high 32 bits of the keys) over the columns with
+    // the same position in their chunk (32 groups per thread), sorts them;
+    // the want-th smallest of the 64 minima of a row (both halves) bounds the
+    // row's answer.  Pass 2 lists the columns up to that bound (at most 32
+    // per thread), each thread sorts its list, and the half-0 thread merges
+    // the row's two lists.  Rows whose lists overflow, and all rows when more
+    // than 32 candidates are wanted, take the warp-per-row path below.
     if (!abort_flag) {
-        const int ldD = G.ldD;
         const int quad = w & 3, half = w >> 2;
-        for (int g0 = 0; g0 < 128 && r0 + g0 < m; g0 += G.RG) {
-            if (32 * quad >= g0 && 32 * quad < g0 + G.RG) {
-                const int lr = 32 * quad + lane;
-                const int il = min(r0 + lr, G.N_load - 1);
-                const float ni = qn[il], si = qs[il];
-                float* drow = Dblk + (size_t)(lr - g0) * ldD;
-                for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
-                    uint32_t r[32];
-                    tc::tmem_ld32(tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, r);
-                    tc::tmem_ld_wait();
+        const int lr = 32 * quad + lane;
+        const int iloc = r0 + lr;
+        const bool row_ok = iloc < m;
+        const int kw = exact_leaf ? k : kp;
+        const int want = min(kw, m - 1);
+        uint32_t* gsh = reinterpret_cast<uint32_t*>(pipe);                     // [32][256]
+        uint64_t* cand = reinterpret_cast<uint64_t*>(pipe + 32 * kTcThreads * 4);  // [32][256]
+        __shared__ int ccount[kTcThreads];
+        __shared__ unsigned char rowflag[128];
+        __shared__ int any_overflow;
+        const bool fast = want <= 32;
+        if (tid == 0) any_overflow = fast ? 0 : 1;
+        if (tid < 128) rowflag[tid] = fast ? 0 : 1;
+        __syncthreads();
+        const int il = min(iloc, G.N_load - 1);
+        const float ni = qn[il], si = qs[il];
+        const uint32_t trow = tbase + ((uint32_t)(32 * quad) << 16);
+        auto hi_of = [&](uint32_t raw, int j) -> uint32_t {
+            const int jj = min(j, G.N_load - 1);
+            const float sdot = __uint_as_float(raw);
+            float dv;
+            if (PREC == 1) dv = ni + qn[jj] - 2.f * sdot;
+            else dv = si * si * ni + qs[jj] * qs[jj] * qn[jj] - 2.f * si * qs[jj] * sdot;
+            const bool valid = row_ok && j < m && j != iloc;
+            return valid ? ord_key(dv) : 0xFFFFFFFFu;
+        };
+        if (fast) {
+            // pass 1: group minima
+            uint32_t gm[32];
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int j = min(c0 + e, G.N_load - 1);
-                        const float sdot = __uint_as_float(r[e]);
-                        float dv;
-                        if (PREC == 1) dv = ni + qn[j] - 2.f * sdot;
-                        else dv = si * si * ni + qs[j] * qs[j] * qn[j] - 2.f * si * qs[j] * sdot;
-                        drow[c0 + e] = dv;
+            for (int e = 0; e < 32; ++e) gm[e] = 0xFFFFFFFFu;
+            for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
+                uint32_t r[32];
+                tc::tmem_ld32(trow + (uint32_t)c0, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 32; ++e) gm[e] = min(gm[e], hi_of(r[e], c0 + e));
+            }
+            reg_bitonic_sort(gm);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) gsh[e * kTcThreads + tid] = gm[e];
+            __syncthreads();
+            // the want-th smallest of the row's 64 minima (two sorted lists)
+            const int ptid = tid ^ 128;
+            uint32_t tau = 0xFFFFFFFFu;
+            {
+                int ia = 0, ib = 0;
+                for (int s2 = 0; s2 < want; ++s2) {
+                    const uint32_t xa = ia < 32 ? gsh[ia * kTcThreads + tid] : 0xFFFFFFFFu;
+                    const uint32_t xb = ib < 32 ? gsh[ib * kTcThreads + ptid] : 0xFFFFFFFFu;
+                    if (xa <= xb) { tau = xa; ++ia; } else { tau = xb; ++ib; }
+                }
+            }
+            // pass 2: the candidates up to the bound
+            int c = 0;
+            for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
+                uint32_t r[32];
+                tc::tmem_ld32(trow + (uint32_t)c0, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const int j = c0 + e;
+                    const uint32_t h = hi_of(r[e], j);
+                    if (h != 0xFFFFFFFFu && h <= tau) {
+                        if (c < 32) cand[c * kTcThreads + tid] = ((uint64_t)h << 32) | (uint32_t)j;
+                        ++c;
                     }
                 }
             }
-            __syncthreads();
-            for (int rr = w; rr < G.RG && g0 + rr < 128; rr += kTcWarps) {
-                const int iloc = r0 + g0 + rr;
-                if (iloc >= m) break;
-                const float* drow = Dblk + (size_t)rr * ldD;
-                const int gi = lid[iloc];
-                leaf_row_finish<PER, kDT>(L, [&](int j) { return drow[j]; }, m, iloc, lid, k, exact_leaf ? k : kp,
-                                      wsc + (size_t)kLeafWarpScratch * w, out_ids + ((int64_t)t * n + gi) * k,
-                                      out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
+            if (c > 32 && row_ok) {
+                rowflag[lr] = 1;
+                any_overflow = 1;
+            }
+            ccount[tid] = min(c, 32);
+            {
+                uint64_t v[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] = e < c ? cand[e * kTcThreads + tid] : kKeyMax;
+                reg_bitonic_sort(v);
+#pragma unroll
+                for (int e = 0; e < 32; ++e) cand[e * kTcThreads + tid] = v[e];
             }
             __syncthreads();
+            // merge the row's two sorted lists; exact leaves write the output
+            uint64_t* rowlist = reinterpret_cast<uint64_t*>(gsh);  // [32][128], minima are dead
+            if (half == 0 && row_ok && !rowflag[lr]) {
+                const int ptid = tid ^ 128;
+                const int ca = ccount[tid], cb = ccount[ptid];
+                const int gi = lid[iloc];
+                int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
+                float* od = out_d + ((int64_t)t * n + gi) * k;
+                int ia = 0, ib = 0;
+                for (int s2 = 0; s2 < want; ++s2) {
+                    const uint64_t xa = ia < ca ? cand[ia * kTcThreads + tid] : kKeyMax;
+                    const uint64_t xb = ib < cb ? cand[ib * kTcThreads + ptid] : kKeyMax;
+                    const uint64_t x = xa < xb ? xa : xb;
+                    if (xa < xb) ++ia; else ++ib;
+                    if (exact_leaf) {
+                        oi[s2] = lid[(uint32_t)x];
+                        od[s2] = unord_key((uint32_t)(x >> 32));
+                    } else {
+                        rowlist[s2 * 128 + lr] = x;
+                    }
+                }
+                if (exact_leaf)
+                    for (int s2 = want; s2 < k; ++s2) {
+                        oi[s2] = -1;
+                        od[s2] = __int_as_float(0x7f800000);
+                    }
+            }
+            __syncthreads();
+            if (!exact_leaf) {
+                // rescore the listed candidates of each row, one warp per row
+                for (int rr = w; rr < 128; rr += kTcWarps) {
+                    const int il2 = r0 + rr;
+                    if (il2 >= m) break;
+                    if (rowflag[rr]) continue;
+                    const int gi = lid[il2];
+                    leaf_rescore_list(L, lid, il2, rowlist + rr, 128, want, k, wsc + (size_t)kLeafWarpScratch * w,
+                                      out_ids + ((int64_t)t * n + gi) * k, out_d + ((int64_t)t * n + gi) * k);
+                }
+            }
+            __syncthreads();
+        }
+        if (any_overflow) {
+            // warp-per-row path for the rows not done above
+            const int ldD = G.ldD;
+            for (int g0 = 0; g0 < 128 && r0 + g0 < m; g0 += G.RG) {
+                if (32 * quad >= g0 && 32 * quad < g0 + G.RG) {
+                    float* drow = Dblk + (size_t)(lr - g0) * ldD;
+                    for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
+                        uint32_t r[32];
+                        tc::tmem_ld32(trow + (uint32_t)c0, r);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int j = min(c0 + e, G.N_load - 1);
+                            const float sdot = __uint_as_float(r[e]);
+                            float dv;
+                            if (PREC == 1) dv = ni + qn[j] - 2.f * sdot;
+                            else dv = si * si * ni + qs[j] * qs[j] * qn[j] - 2.f * si * qs[j] * sdot;
+                            drow[c0 + e] = dv;
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int rr = w; rr < G.RG && g0 + rr < 128; rr += kTcWarps) {
+                    const int il2 = r0 + g0 + rr;
+                    if (il2 >= m) break;
+                    if (!rowflag[g0 + rr]) continue;
+                    const float* drow = Dblk + (size_t)rr * ldD;
+                    const int gi = lid[il2];
+                    leaf_row_finish<PER, kDT>(L, [&](int j) { return drow[j]; }, m, il2, lid, k, kw,
+                                              wsc + (size_t)kLeafWarpScratch * w, out_ids + ((int64_t)t * n + gi) * k,
+                                              out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
+                }
+                __syncthreads();
+            }
         }
     }
     tc::fence_before_sync();
