@@ -615,32 +615,46 @@ __device__ __forceinline__ float warp_canon_dist16(const RowLoader<kDT>& L, int6
 }
 
 // Byte rows, 16-byte aligned with rows padded to a multiple of 16 bytes and
-// d <= 128 (so every distance is an exact integer): each lane scores its
-// own candidate b[lane] (lane < nb) against the query row q[8] (bytes of a,
-// loaded once by the caller with load_query_u8) -- no exchange between lanes.
-__device__ __forceinline__ void load_query_u8(const uint8_t* X, int64_t ld, int64_t a, int d, uint4 (&q)[8])
+// d <= 128 (so every distance is an exact integer): eight lanes per
+// candidate, lane l taking bytes 16 (l mod 8) .. + 15 of its row, so one load
+// instruction fetches four whole rows.  load_query_u8 gives each lane its
+// 16 bytes of the query row; score_u8_g8 writes the distances from a to
+// b[0..nb) (nb <= 32) to out[0..nb) (shared memory).
+__device__ __forceinline__ uint4 load_query_u8(const uint8_t* X, int64_t ld, int64_t a, int d)
 {
+    const int c = threadIdx.x & 7;
     const uint8_t* row = X + (uint64_t)(uint32_t)a * (uint32_t)ld;
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-        q[c] = 16 * c < d ? __ldg(reinterpret_cast<const uint4*>(row + 16 * c)) : make_uint4(0u, 0u, 0u, 0u);
+    return 16 * c < d ? __ldg(reinterpret_cast<const uint4*>(row + 16 * c)) : make_uint4(0u, 0u, 0u, 0u);
 }
-__device__ __forceinline__ float lane_u8_dist(const uint8_t* X, int64_t ld, int d, const uint4 (&q)[8], int b)
+__device__ __forceinline__ void score_u8_g8(const uint8_t* X, int64_t ld, int d, uint4 q, const int* b, int nb,
+                                            float* out)
 {
-    const uint8_t* row = X + (uint64_t)(uint32_t)b * (uint32_t)ld;
-    uint32_t acc = 0u;
+    const int lane = threadIdx.x & 31;
+    const int c = lane & 7, g = lane >> 3;
+    const bool has = 16 * c < d;
+    uint4 x[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        if (16 * c < d) {
-            const uint4 x = __ldg(reinterpret_cast<const uint4*>(row + 16 * c));
-            uint32_t t;
-            t = __vabsdiffu4(q[c].x, x.x); acc = __dp4a(t, t, acc);
-            t = __vabsdiffu4(q[c].y, x.y); acc = __dp4a(t, t, acc);
-            t = __vabsdiffu4(q[c].z, x.z); acc = __dp4a(t, t, acc);
-            t = __vabsdiffu4(q[c].w, x.w); acc = __dp4a(t, t, acc);
+    for (int it = 0; it < 8; ++it) {
+        const int idx = 4 * it + g;
+        x[it] = make_uint4(0u, 0u, 0u, 0u);
+        if (idx < nb && has) {
+            const uint8_t* row = X + (uint64_t)(uint32_t)b[idx] * (uint32_t)ld;
+            x[it] = __ldg(reinterpret_cast<const uint4*>(row + 16 * c));
         }
     }
-    return (float)acc;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        uint32_t t, acc = 0u;
+        t = __vabsdiffu4(q.x, x[it].x); acc = __dp4a(t, t, acc);
+        t = __vabsdiffu4(q.y, x[it].y); acc = __dp4a(t, t, acc);
+        t = __vabsdiffu4(q.z, x[it].z); acc = __dp4a(t, t, acc);
+        t = __vabsdiffu4(q.w, x[it].w); acc = __dp4a(t, t, acc);
+        acc += __shfl_xor_sync(KNNG_FULL_MASK, acc, 4);
+        acc += __shfl_xor_sync(KNNG_FULL_MASK, acc, 2);
+        acc += __shfl_xor_sync(KNNG_FULL_MASK, acc, 1);
+        const int idx = 4 * it + g;
+        if (c == 0 && idx < nb) out[idx] = (float)acc;
+    }
 }
 
 // Canonical distances from a to b[0..nb) (nb <= 32): lane c < nb returns the

@@ -58,7 +58,8 @@ static PropLayout prop_layout(int k)
 
 template <int E, int kDT>
 __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
-                                 const int* __restrict__ xb_bad, PairOffers po, int64_t n, int k,
+                                 const int* __restrict__ xb_bad, const uint8_t* __restrict__ lane_X,
+                                 int64_t lane_ld, PairOffers po, int64_t n, int k,
                                  const int32_t* __restrict__ order,
                                  const int32_t* __restrict__ ids_in, const float* __restrict__ d_in,
                                  const unsigned long long* __restrict__ flags_in, int32_t* __restrict__ ids_out,
@@ -153,12 +154,19 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         }
         __syncwarp();
         // score the new candidates, 32 at a time
-        for (int c0 = nknown; c0 < cnt; c0 += 32) {
-            const int nb = min(32, cnt - c0);
-            float dd;
-            if (kDT == kDtF32 && bytes) dd = warp_canon_dist32(Lb, p, cid + c0, nb);
-            else dd = warp_canon_dist32(L, p, cid + c0, nb);
-            if (lane < nb) cd[c0 + lane] = dd;
+        if (lane_X && (kDT == kDtU8 || bytes)) {
+            // byte rows, d <= 128: eight lanes per candidate
+            const uint4 q = load_query_u8(lane_X, lane_ld, p, L.d);
+            for (int c0 = nknown; c0 < cnt; c0 += 32)
+                score_u8_g8(lane_X, lane_ld, L.d, q, cid + c0, min(32, cnt - c0), cd + c0);
+        } else {
+            for (int c0 = nknown; c0 < cnt; c0 += 32) {
+                const int nb = min(32, cnt - c0);
+                float dd;
+                if (kDT == kDtF32 && bytes) dd = warp_canon_dist32(Lb, p, cid + c0, nb);
+                else dd = warp_canon_dist32(L, p, cid + c0, nb);
+                if (lane < nb) cd[c0 + lane] = dd;
+            }
         }
         __syncwarp();
         if (po.tgt) {
@@ -269,7 +277,20 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     if (blocks > need) blocks = need;
     RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
     const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
-    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, po, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
+    // byte rows scored one candidate per lane: 16-byte aligned rows whose
+    // 16-byte blocks up to d stay inside the row (d <= 128)
+    const uint8_t* lane_X = nullptr;
+    int64_t lane_ld = 0;
+    if (x.d <= 128) {
+        if (kDT == kDtF32 && x.Xb) {
+            lane_X = x.Xb;
+            lane_ld = x.ldb;
+        } else if (kDT == kDtU8 && (uintptr_t)x.X % 16 == 0 && x.ld % 16 == 0 && x.d % 16 == 0) {
+            lane_X = static_cast<const uint8_t*>(x.X);
+            lane_ld = x.ld;
+        }
+    }
+    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, lane_X, lane_ld, po, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
                                                 PL.hshift, PL.cap, (int)PL.per_warp);
     note_launches(1);
     return cudaGetLastError();

@@ -108,3 +108,14 @@ def test_u8_host_entry_point_and_odd_d():
     oi, od = oracle.build_graph(X, 8, 3, 40, 2, 5)
     np.testing.assert_array_equal(hi, oi)
     np.testing.assert_array_equal(hd, od)
+
+
+@pytest.mark.parametrize("d", [100, 36, 200])
+def test_byte_copy_ragged_d(d):
+    # d not a multiple of 16: the copy's padding bytes must read as zeros in
+    # the 16-byte row loads of projection and propagation
+    X = synthetic.sift_like(4000, d, centers=20, seed=d)
+    gi, gd = knng().knng_build(dev(X), 10, 3, 64, 2, 3)
+    oi, od = oracle.build_graph(X, 10, 3, 64, 2, 3)
+    np.testing.assert_array_equal(host(gi), oi)
+    np.testing.assert_array_equal(host(gd), od)
