@@ -44,6 +44,11 @@ WORKLOADS = {
 }
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
 PROPAGATION = {"first_order": 0, "best_first": 1, "pairwise": 2}
+# DRAM bytes (read + write) per point of one launch, from ncu captures of the
+# current kernels on the 400k-point case of the sift1m configuration (leaf:
+# per point and tree; propagation: per point and round).
+TRAFFIC = {("sift1m", "bf16"): {"leaf_knn": (940.408064e6 + 550.368256e6) / (400_000 * 8),
+                                "propagate": (237.591808e6 + 66.906880e6) / 400_000}}
 METRIC = "points/sec to build the k-NN graph (recall@k reported on a 10k-point sample)"
 
 
@@ -517,10 +522,19 @@ def main():
         ach = merge_bytes / (stage_ms["merge"] / 1e3) / 1e9
         roof["merge"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                          "traffic": None, "algorithmic_bytes_per_launch": merge_bytes}
-        # the dominant kernel of the step carries the headline roofline object
+        # DRAM traffic per launch from the ncu captures of the current kernels
+        # (profiles/leaf_tc_propagate_sift400k.md: 400k points, scaled by the
+        # points a launch processes); other configurations have no capture
+        cap = TRAFFIC.get((args.workload if args.workload != "sift400k" else "sift1m", args.precision))
+        if cap and args.propagation == "first_order" and args.partitioner == "random" and args.metric_kind == "l2":
+            roof["leaf_knn"]["traffic"] = cap["leaf_knn"] * n * T
+            if "propagate" in roof:
+                roof["propagate"]["traffic"] = cap["propagate"] * n
+        # the kernel that takes the most time in a step carries the headline
+        # roofline object (its figures are per launch)
         stage_of = {"leaf_knn": stage_ms["leaf_knn"], "merge": stage_ms["merge"]}
         if R > 0:
-            stage_of["propagate"] = sum(stage_ms[f"propagate_r{r}"] for r in range(R)) / R
+            stage_of["propagate"] = sum(stage_ms[f"propagate_r{r}"] for r in range(R))
         dom = max(stage_of, key=stage_of.get)
         line["roofline"] = dict(roof[dom], kernel=dom, peak_source=src)
         line["roofline_all"] = roof
@@ -564,7 +578,8 @@ def main():
     # ---- the CPU oracle on a bounded sample (rank 0, N = 1 only)
     if not args.no_extras and not args.no_cpu_baseline and rank == 0 and world == 1 and args.partitioner == "random":
         import oracle
-        ns = min(args.cpu_sample, n)
+        # about 15 s of oracle work: fewer points for wider rows
+        ns = min(args.cpu_sample * 128 // max(d, 128), n)
         Xs = np.ascontiguousarray(X[:ns])
         t0 = time.perf_counter()
         oracle.build_graph(Xs, k, T, g, R, args.seed, metric=opts["metric"], prop=opts["propagation"],
