@@ -285,13 +285,22 @@ def run_learned(args):
 
     res = {}
     l0 = knng.knng_launch_counter()
+    # headline: per-level learned features (random directions where a
+    # feature is flat in the node), T=4
     ms, clk = timed(lambda: knng.knng_build_learned(net, Xd, k, 4, g, R, args.seed, prec, 2, ids=ids, dists=dists,
-                                                    h=h))
+                                                    h=h, partitioner=knng.PART_FEATURES))
     launches = (knng.knng_launch_counter() - l0) // (args.steps + args.warmup)
-    res["learned_T4"] = {"ms_per_step": ms, "recall": recall()}
-    for T in (8, 4):
+    res["learned_T4"] = {"ms_per_step": ms, "recall": recall(), "splits": "per-level learned features"}
+    for name, part in (("learned_embedding_random_T4", knng.PART_RANDOM), ("learned_embedding_pca_T4", knng.PART_PCA)):
+        ms_l, _ = timed(lambda: knng.knng_build_learned(net, Xd, k, 4, g, R, args.seed, prec, 2, ids=ids,
+                                                        dists=dists, h=h, partitioner=part))
+        res[name] = {"ms_per_step": ms_l, "recall": recall()}
+    for T in (8, 6, 4):
         ms_r, _ = timed(lambda: knng.knng_build(Xd, k, T, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h))
         res[f"random_T{T}"] = {"ms_per_step": ms_r, "recall": recall()}
+    ms_p, _ = timed(lambda: knng.knng_build(Xd, k, 4, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h,
+                                            partitioner=knng.PART_PCA))
+    res["pca_T4"] = {"ms_per_step": ms_p, "recall": recall()}
     for v in res.values():
         v["points_per_s"] = n / (v["ms_per_step"] / 1e3)
     line = {

@@ -65,6 +65,7 @@ extern "C" {
 
 #define KNNG_PART_RANDOM 0  /* Philox random directions (App. after Lemma 1)                  */
 #define KNNG_PART_PCA 1     /* random principal directions (Sec. 3.4): see knng_partition_pca */
+#define KNNG_PART_FEATURES 2 /* knng_build_learned only: per-level learned features              */
 
 /* Distance.  L2: the squared Euclidean distance.  COSINE: 1 - cos of the
  * angle between two rows (App. after Lemma 1: random projections partition
@@ -311,7 +312,16 @@ int knng_mlp_load(knng_mlp* m, const char* path);
 /* Features of every point: Z (device, FP32 [n][d_out]), BF16 inference. */
 int knng_mlp_forward(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                      float* Z, void* stream);
-/* knng_build with learned splits (the network's d_in must equal d). */
+/* knng_build with learned splits (the network's d_in must equal d).
+ * p->partitioner selects how the network's outputs z (d_out per point,
+ * BF16 inference) split the points: KNNG_PART_RANDOM -- the random
+ * partition trees of knng_build on the points z (a random direction per
+ * node in the learned space, median split); KNNG_PART_PCA -- principal-
+ * direction trees on z; KNNG_PART_FEATURES -- level l < d_out of tree t
+ * splits at the median of one output (a per-tree Philox permutation of the
+ * outputs), while that output still varies inside the node, and random
+ * directions in the input space elsewhere.  Leaf graphs, merge and
+ * propagation use X. */
 int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                        const knng_params* p, int32_t* ids, float* dists, void* stream);
 

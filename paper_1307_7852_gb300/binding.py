@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libknng.so")
 KNNG_OK = 0
 DTYPE_F32, DTYPE_F16, DTYPE_U8 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
-PART_RANDOM, PART_PCA = 0, 1
+PART_RANDOM, PART_PCA, PART_FEATURES = 0, 1, 2
 METRIC_L2, METRIC_COSINE = 0, 1
 PROP_FIRST_ORDER, PROP_BEST_FIRST, PROP_PAIRWISE = 0, 1, 2
 
@@ -592,14 +592,14 @@ def knng_mlp_forward(mlp: Mlp, X, Z=None, stream=None, h: Handle = None):
 
 def knng_build_learned(mlp: Mlp, X, k, T, leaf_size, prop_rounds, seed, precision=PREC_FP32, rescore_mult=2,
                        ids=None, dists=None, stream=None, h: Handle = None, propagation: int = PROP_FIRST_ORDER,
-                       budget: int = 0, r_stop: float = 0.0):
+                       budget: int = 0, r_stop: float = 0.0, partitioner: int = PART_RANDOM):
     torch = _torch()
     xp, dt, n, d, ld = _xdesc(X)
     h = h or handle(X.device.index or 0)
     ids = _out((n, k), torch.int32, X.device, ids)
     dists = _out((n, k), torch.float32, X.device, dists)
     p = make_params(k, T, leaf_size, prop_rounds, seed, precision, rescore_mult, propagation=propagation,
-                    budget=budget, r_stop=r_stop)
+                    budget=budget, r_stop=r_stop, partitioner=partitioner)
     h.check(lib().knng_build_learned(h.ptr, mlp.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
                                      _stream(X.device, stream)), "knng_build_learned")
     return ids, dists

@@ -259,7 +259,7 @@ int check_params(knng_handle* h, const knng_params* p, int64_t n)
 // ar.base == nullptr it only measures them.
 int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc& x_in, const knng_params& p,
                    int32_t* ids, float* dists, Arena& a, cudaStream_t st, bool events,
-                   const LearnedFeat* lf = nullptr, bool byte_copy = false)
+                   const LearnedFeat* lf = nullptr, bool byte_copy = false, const XDesc* xpart = nullptr)
 {
     XDesc x = x_in;
     const int64_t n = x.n;
@@ -306,7 +306,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
     const size_t fixed = a.off;
     int r;
     if (!a.base) {
-        run_partition(x, P, dp, T, p.seed, nullptr, a, st, lf);
+        run_partition(xpart ? *xpart : x, P, dp, T, p.seed, nullptr, a, st, lf);
         const size_t part_end = a.off;
         a.off = fixed;
         if ((r = leaf_stage(h, P, dp, x, T, nullptr, k, p.precision, p.rescore_mult, nullptr, nullptr, a, st)))
@@ -332,7 +332,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
     }
     int cur = 0;  // bi[cur] / bd[cur]: the merged graph when R > 0
     if (!adaptive) {
-        e = run_partition(x, P, dp, T, p.seed, perm, a, st, lf, 0, &pca);
+        e = run_partition(xpart ? *xpart : x, P, dp, T, p.seed, perm, a, st, lf, 0, &pca);
         if (e != cudaSuccess) return cuda_fail(h, e, "partition");
         mark(1);
         const size_t part_end = a.off;
@@ -356,7 +356,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         for (int t0 = 0; t0 < T && !stop; t0 += kChunk) {
             const int tc = std::min(kChunk, T - t0);
             const size_t base = a.off;
-            e = run_partition(x, P, dp, tc, p.seed, perm + (size_t)t0 * n, a, st, lf, t0, &pca);
+            e = run_partition(xpart ? *xpart : x, P, dp, tc, p.seed, perm + (size_t)t0 * n, a, st, lf, t0, &pca);
             if (e != cudaSuccess) return cuda_fail(h, e, "partition");
             const size_t part_end = a.off;
             a.off = base;
@@ -1147,7 +1147,13 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     if (r) return r;
     if (!p) return fail(h, KNNG_ERR_INVALID_ARG, "params is NULL");
     knng_params q = *p;
-    q.partitioner = KNNG_PART_RANDOM;  // the random directions serve the levels past the features
+    // KNNG_PART_FEATURES: per-level learned features (random directions past
+    // them); KNNG_PART_RANDOM / KNNG_PART_PCA: random or principal-direction
+    // trees in the learned embedding
+    const int mode = q.partitioner;
+    if (mode != KNNG_PART_FEATURES && mode != KNNG_PART_RANDOM && mode != KNNG_PART_PCA)
+        return fail(h, KNNG_ERR_INVALID_ARG, "partitioner %d", mode);
+    q.partitioner = mode == KNNG_PART_PCA ? KNNG_PART_PCA : KNNG_PART_RANDOM;
     if ((r = check_params(h, &q, n))) return r;
     MlpModel* M = mlp_model(m);
     if (!M || !ids || !dists) return fail(h, KNNG_ERR_INVALID_ARG, "NULL network or output");
@@ -1161,11 +1167,15 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     LearnedFeat lf;
     lf.C = M->C;
     learned_feature_order(q.seed, q.T, M->C, lf);
+    const bool feat = mode == KNNG_PART_FEATURES;
+    XDesc xz{nullptr, KNNG_DTYPE_F32, n, M->C, M->C, true};  // the embedding as the partition's points
     Arena m0;
     m0.take<float>((size_t)n * M->C);
     m0.take<uint32_t>(2 * (size_t)M->C);
     m0.take<float>((size_t)M->C);
-    if ((r = build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, m0, st, true, &lf, true))) return r;
+    if ((r = build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, m0, st, true, feat ? &lf : nullptr, true,
+                            feat ? nullptr : &xz)))
+        return r;
     if ((r = ensure_ws(h, m0.off, st))) return r;
     Arena a;
     a.base = h->ws;
@@ -1177,9 +1187,11 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     const bool rec = (int)h->stage_ev.size() >= 5 + q.prop_rounds;
     if (rec) cudaEventRecord(h->stage_ev[4 + q.prop_rounds], st);  // start of inference
     cudaError_t e = run_mlp_forward(*M, x, Z, h->dev_err, st);
-    if (e == cudaSuccess) e = run_feature_range(Z, n, M->C, mm, frange, st);
+    if (e == cudaSuccess && feat) e = run_feature_range(Z, n, M->C, mm, frange, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "network inference");
-    return build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, a, st, true, &lf, true);
+    xz.X = Z;
+    return build_pipeline(h, h->plan, h->dplan, x, q, ids, dists, a, st, true, feat ? &lf : nullptr, true,
+                          feat ? nullptr : &xz);
 }
 
 int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,

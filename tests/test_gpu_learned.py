@@ -86,21 +86,55 @@ def _recall(X, ids, k, sample):
     return float(np.mean([len(set(gi[r]) & set(e[r])) / k for r in range(len(sample))]))
 
 
-def test_learned_splits_gain_over_random_at_equal_trees():
+@pytest.fixture(scope="module")
+def trained():
     k = knng()
     n, d, kk = 60000, 96, 20
     X = synthetic.sphere_f16(n, d, centers=256, std=0.05, seed=11)
-    Xd = torch.from_numpy(X).cuda()
     # training graph: the method itself, random directions, on a subsample
     sub = torch.from_numpy(np.ascontiguousarray(X[: n // 2])).cuda()
     gi, _ = k.knng_build(sub, kk, 8, 256, 1, 7)
     net = k.Mlp(d, 256, 16, seed=2)
     net.train(sub, gi, 600, batch_edges=4096, lr=2e-3, seed=3)
+    return X, net
+
+
+@pytest.mark.parametrize("mode", ["embedding_random", "features"])
+def test_learned_splits_gain_over_random_at_equal_trees(trained, mode):
+    k = knng()
+    X, net = trained
+    n, kk = X.shape[0], 20
+    Xd = torch.from_numpy(X).cuda()
+    part = k.PART_RANDOM if mode == "embedding_random" else k.PART_FEATURES
     sample = synthetic.sample_ids(n, 2000, 5)
     T = 2
     r_rand = _recall(X, k.knng_build(Xd, kk, T, 256, 0, 21)[0], kk, sample)
-    r_lrn = _recall(X, k.knng_build_learned(net, Xd, kk, T, 256, 0, 21)[0], kk, sample)
-    ids, dd = k.knng_build_learned(net, Xd, kk, T, 256, 0, 21)
+    ids, dd = k.knng_build_learned(net, Xd, kk, T, 256, 0, 21, partitioner=part)
+    r_lrn = _recall(X, ids, kk, sample)
+    print(f"recall T=2, no propagation: random {r_rand:.4f}, learned ({mode}) {r_lrn:.4f}")
     ids = ids.cpu().numpy()
     assert np.all((ids >= -1) & (ids < n))
     assert r_lrn > r_rand, (r_lrn, r_rand)
+
+
+def test_learned_embedding_build_matches_oracle_stagewise(trained):
+    # the embedding trees are the random partition of the points z = f(x)
+    # (the GPU's BF16 inference), the lists those of the rows x
+    k = knng()
+    X, net = trained
+    X = np.ascontiguousarray(X[:8000])
+    Xd = torch.from_numpy(X).cuda()
+    Z = k.knng_mlp_forward(net, Xd).cpu().numpy()
+    T, g, kk, seed = 3, 64, 10, 4
+    gi, gd = k.knng_build_learned(net, Xd, kk, T, g, 1, seed)
+    Xf = X.astype(np.float32)
+    lists = np.empty((T, 8000, kk), dtype=np.int32)
+    for t in range(T):
+        perm, off = oracle.partition(Z, seed, t, g)
+        np.testing.assert_array_equal(k.knng_partition(torch.from_numpy(Z).cuda(), T, g, seed)[t].cpu().numpy(),
+                                      perm)
+        lists[t], _ = oracle.leaf_knn(Xf, perm, off, kk)
+    oi, od = oracle.merge(Xf, lists, kk)
+    oi, od = oracle.propagate(Xf, oi, kk)
+    gi = gi.cpu().numpy()
+    assert np.mean(gi == oi) > 0.99
