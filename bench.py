@@ -291,7 +291,8 @@ def run_learned(args):
                                                     h=h, partitioner=knng.PART_FEATURES))
     launches = (knng.knng_launch_counter() - l0) // (args.steps + args.warmup)
     res["learned_T4"] = {"ms_per_step": ms, "recall": recall(), "splits": "per-level learned features"}
-    for name, part in (("learned_embedding_random_T4", knng.PART_RANDOM), ("learned_embedding_pca_T4", knng.PART_PCA)):
+    for name, part in (("learned_features_pca_T4", knng.PART_FEATURES_PCA),
+                       ("learned_embedding_random_T4", knng.PART_RANDOM), ("learned_embedding_pca_T4", knng.PART_PCA)):
         ms_l, _ = timed(lambda: knng.knng_build_learned(net, Xd, k, 4, g, R, args.seed, prec, 2, ids=ids,
                                                         dists=dists, h=h, partitioner=part))
         res[name] = {"ms_per_step": ms_l, "recall": recall()}

@@ -66,6 +66,7 @@ extern "C" {
 #define KNNG_PART_RANDOM 0  /* Philox random directions (App. after Lemma 1)                  */
 #define KNNG_PART_PCA 1     /* random principal directions (Sec. 3.4): see knng_partition_pca */
 #define KNNG_PART_FEATURES 2 /* knng_build_learned only: per-level learned features              */
+#define KNNG_PART_FEATURES_PCA 3 /* the same with principal directions where a feature is flat   */
 
 /* Distance.  L2: the squared Euclidean distance.  COSINE: 1 - cos of the
  * angle between two rows (App. after Lemma 1: random projections partition
@@ -320,8 +321,9 @@ int knng_mlp_forward(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, 
  * direction trees on z; KNNG_PART_FEATURES -- level l < d_out of tree t
  * splits at the median of one output (a per-tree Philox permutation of the
  * outputs), while that output still varies inside the node, and random
- * directions in the input space elsewhere.  Leaf graphs, merge and
- * propagation use X. */
+ * directions in the input space elsewhere; KNNG_PART_FEATURES_PCA -- the
+ * same with principal directions of the input (knng_partition_pca) in place
+ * of the random ones.  Leaf graphs, merge and propagation use X. */
 int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                        const knng_params* p, int32_t* ids, float* dists, void* stream);
 

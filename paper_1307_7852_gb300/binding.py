@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libknng.so")
 KNNG_OK = 0
 DTYPE_F32, DTYPE_F16, DTYPE_U8 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8E4M3 = 0, 1, 2
-PART_RANDOM, PART_PCA, PART_FEATURES = 0, 1, 2
+PART_RANDOM, PART_PCA, PART_FEATURES, PART_FEATURES_PCA = 0, 1, 2, 3
 METRIC_L2, METRIC_COSINE = 0, 1
 PROP_FIRST_ORDER, PROP_BEST_FIRST, PROP_PAIRWISE = 0, 1, 2
 

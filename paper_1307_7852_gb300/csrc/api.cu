@@ -1151,9 +1151,10 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     // them); KNNG_PART_RANDOM / KNNG_PART_PCA: random or principal-direction
     // trees in the learned embedding
     const int mode = q.partitioner;
-    if (mode != KNNG_PART_FEATURES && mode != KNNG_PART_RANDOM && mode != KNNG_PART_PCA)
+    if (mode != KNNG_PART_FEATURES && mode != KNNG_PART_FEATURES_PCA && mode != KNNG_PART_RANDOM &&
+        mode != KNNG_PART_PCA)
         return fail(h, KNNG_ERR_INVALID_ARG, "partitioner %d", mode);
-    q.partitioner = mode == KNNG_PART_PCA ? KNNG_PART_PCA : KNNG_PART_RANDOM;
+    q.partitioner = (mode == KNNG_PART_PCA || mode == KNNG_PART_FEATURES_PCA) ? KNNG_PART_PCA : KNNG_PART_RANDOM;
     if ((r = check_params(h, &q, n))) return r;
     MlpModel* M = mlp_model(m);
     if (!M || !ids || !dists) return fail(h, KNNG_ERR_INVALID_ARG, "NULL network or output");
@@ -1167,7 +1168,7 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
     LearnedFeat lf;
     lf.C = M->C;
     learned_feature_order(q.seed, q.T, M->C, lf);
-    const bool feat = mode == KNNG_PART_FEATURES;
+    const bool feat = mode == KNNG_PART_FEATURES || mode == KNNG_PART_FEATURES_PCA;
     XDesc xz{nullptr, KNNG_DTYPE_F32, n, M->C, M->C, true};  // the embedding as the partition's points
     Arena m0;
     m0.take<float>((size_t)n * M->C);

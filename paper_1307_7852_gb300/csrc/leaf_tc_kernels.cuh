@@ -49,11 +49,10 @@ constexpr int kTcCand = 128;
 //     sum of the Gram is an integer below 2^24, exact in FP32, so the
 //     candidate distance |x|^2 + |y|^2 - 2 x.y equals the true squared
 //     distance, which is also what the canonical FP32 distance returns.
-template <int PREC, int kDT>
-__global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kDT> L, int64_t rows,
-                                                           const int32_t* __restrict__ perm, int dq,
-                                                           void* __restrict__ out, float* __restrict__ nrm,
-                                                           float* __restrict__ scl, uint8_t* __restrict__ exact)
+template <int PREC, class Loader>
+__device__ __forceinline__ void gather_quant_body(const Loader& L, int64_t rows, const int32_t* __restrict__ perm,
+                                                  int dq, void* __restrict__ out, float* __restrict__ nrm,
+                                                  float* __restrict__ scl, uint8_t* __restrict__ exact)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -107,6 +106,23 @@ __global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kDT> L, int
             exact[r] = (PREC == 1 && ex && s < 8388608.0f) ? 1 : 0;
         }
     }
+}
+
+// Float rows whose byte copy is exact (*xb_bad == 0) are read from the copy.
+template <int PREC, int kDT>
+__global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
+                                                           const int* __restrict__ xb_bad, int64_t rows,
+                                                           const int32_t* __restrict__ perm, int dq,
+                                                           void* __restrict__ out, float* __restrict__ nrm,
+                                                           float* __restrict__ scl, uint8_t* __restrict__ exact)
+{
+    if constexpr (kDT == kDtF32) {
+        if (xb_bad && *xb_bad == 0) {
+            gather_quant_body<PREC>(Lb, rows, perm, dq, out, nrm, scl, exact);
+            return;
+        }
+    }
+    gather_quant_body<PREC>(L, rows, perm, dq, out, nrm, scl, exact);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,8 +517,11 @@ cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const 
     const int64_t rows = (int64_t)T * x.n;
     const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);
     RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
-    if (prec == 1) gather_quant_kernel<1, kDT><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
-    else gather_quant_kernel<2, kDT><<<gblocks, 256, 0, st>>>(rl, rows, perm, dq, Xq, qn, qs, qx);
+    const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
+    if (prec == 1)
+        gather_quant_kernel<1, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx);
+    else
+        gather_quant_kernel<2, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         int nsel = 0;
         uint64_t v[E];
         if (cnt <= 512 && want <= 64) {
-            nsel = warp_topk_sorted<16>(key, cnt, want, keys, keys + 64, hist);
+            nsel = cnt <= 256 ? warp_topk_sorted<8>(key, cnt, want, keys, keys + 64, hist)
+                              : warp_topk_sorted<16>(key, cnt, want, keys, keys + 64, hist);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int i = lane * E + e;
