@@ -44,7 +44,7 @@ extern "C" {
 /* ---- status codes ---------------------------------------------------- */
 #define KNNG_OK 0
 #define KNNG_ERR_INVALID_ARG (-1) /* a size, pointer or parameter is out of range */
-#define KNNG_ERR_UNSUPPORTED (-2) /* valid request this build does not serve     */
+#define KNNG_ERR_UNSUPPORTED (-2) /* valid request the library does not serve     */
 #define KNNG_ERR_OOM (-3)         /* device workspace allocation failed          */
 #define KNNG_ERR_CUDA (-4)        /* a CUDA runtime call or launch failed        */
 #define KNNG_ERR_TIMEOUT (-5)     /* a bounded device wait gave up               */

@@ -13,8 +13,8 @@
  * (see orc_project).  Compile with -ffp-contract=off so that the compiler
  * fuses nothing that is not written as fmaf.
  *
- * Where the paper is silent, the readings below are used (each is listed in
- * the design doc of the repository):
+ * Where the paper is silent, the readings below are used (the CUDA library
+ * follows the same ones):
  *   - rho is the squared Euclidean distance (ranks like the Euclidean
  *     distance of Def. 1; the square root is not taken).
  *   - Ties are broken by point id: lists are ordered by (D, id) ascending.
@@ -29,7 +29,11 @@
  *     is "at most g").
  *   - Propagation (Sec. 3.2) is the first-order form analysed in Theorem 1:
  *     one synchronous round replaces every list by the k best of its own
- *     members and its neighbours' members.
+ *     members and its neighbours' members.  The best-first form with a visit
+ *     budget (Sec. 3.2) and pairwise updating (Sec. 3.4) are synchronous
+ *     passes too (orc_propagate_best_first, orc_propagate_pairwise).
+ *   - The cosine distance is 1 - cos, computed as |u - v|^2 / 2 between the
+ *     rows scaled to unit length in FP32 (orc_normalize_rows).
  */
 #include <math.h>
 #include <stdint.h>

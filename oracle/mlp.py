@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE (see oracle/__init__.py): the plain NumPy statement of
 what the CUDA training kernels compute, used to check their gradients.
 
 The paper has no learned partitioner; this is the reading used by the
-library (listed in the design doc).  Network (FP32 weights on the GPU):
+library.  Network (FP32 weights on the GPU):
 
     A = X W1^T + b1          (N x H)
     Hh = GELU(A)             GELU(a) = a/2 (1 + erf(a / sqrt 2))
