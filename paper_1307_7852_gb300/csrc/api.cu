@@ -68,6 +68,8 @@ struct knng_handle {
     std::string err;
     int div_used = 0;            // divisions used by the last build
     std::vector<float> div_rates;  // their effective rates r_m (adaptive builds)
+    char* staging = nullptr;     // device copies of knng_build_host's buffers (grow-only)
+    size_t staging_size = 0;
 };
 
 namespace {
@@ -483,6 +485,7 @@ int knng_destroy(knng_handle* h)
         if (h->ws) cudaFree(h->ws);
         if (h->plan_dev) cudaFree(h->plan_dev);
         if (h->dev_err) cudaFree(h->dev_err);
+        if (h->staging) cudaFree(h->staging);
         BatchCache& B = h->batch;
         if (B.exec) cudaGraphExecDestroy(B.exec);
         if (B.graph) cudaGraphDestroy(B.graph);
@@ -1207,16 +1210,25 @@ int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int
     const size_t es = dtype_size(dtype);
     const size_t xbytes = (size_t)((n - 1) * ld + d) * es;
     const size_t nk = (size_t)n * p->k;
-    void* dx = nullptr;
-    void* dout = nullptr;
-    cudaError_t e = cudaMallocAsync(&dx, xbytes, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&dout, nk * 8, st);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        if (dx) cudaFreeAsync(dx, st);
-        return fail(h, KNNG_ERR_OOM, "staging buffers");
+    // device copies of X and of the graph, kept by the handle between calls
+    const size_t xpad = (xbytes + 255) & ~(size_t)255;
+    const size_t need = xpad + nk * 8;
+    cudaError_t e = cudaSuccess;
+    if (need > h->staging_size) {
+        if (h->staging) cudaFreeAsync(h->staging, st);
+        h->staging = nullptr;
+        h->staging_size = 0;
+        void* q = nullptr;
+        e = cudaMallocAsync(&q, need, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, KNNG_ERR_OOM, "staging buffers");
+        }
+        h->staging = static_cast<char*>(q);
+        h->staging_size = need;
     }
-    int32_t* di = static_cast<int32_t*>(dout);
+    void* dx = h->staging;
+    int32_t* di = reinterpret_cast<int32_t*>(h->staging + xpad);
     float* dd = reinterpret_cast<float*>(di + nk);
     int r = KNNG_OK;
     e = cudaMemcpyAsync(dx, X, xbytes, cudaMemcpyHostToDevice, st);
@@ -1227,8 +1239,6 @@ int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int
         if (e == cudaSuccess) e = cudaMemcpyAsync(dists, dd, nk * 4, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) r = cuda_fail(h, e, "copy graph to host");
     }
-    cudaFreeAsync(dx, st);
-    cudaFreeAsync(dout, st);
     const int rs = knng_sync(h, stream);
     return r ? r : rs;
 }

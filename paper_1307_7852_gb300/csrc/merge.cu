@@ -17,11 +17,8 @@ __global__ void __launch_bounds__(128) merge_kernel(int64_t n, int T, int k,
                                                     const float* __restrict__ d_in,
                                                     int32_t* __restrict__ ids, float* __restrict__ dists)
 {
-    // the ids written so far, per thread (column threadIdx.x of [kMaxK][128])
-    __shared__ int32_t seen[kMaxK * 128];
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
-    int32_t* mine = seen + threadIdx.x;
     int h[TMAX];
     uint64_t cur[TMAX];
 #pragma unroll
@@ -57,9 +54,8 @@ __global__ void __launch_bounds__(128) merge_kernel(int64_t n, int T, int k,
         const int32_t id = (int32_t)(uint32_t)best;
         if (id == (int32_t)p) continue;
         bool dup = false;
-        for (int e = 0; e < cnt; ++e) dup |= (mine[e * 128] == id);
+        for (int e = 0; e < cnt; ++e) dup |= (oi[e] == id);
         if (dup) continue;
-        mine[cnt * 128] = id;
         oi[cnt] = id;
         od[cnt] = unord_key((uint32_t)(best >> 32));
         ++cnt;
