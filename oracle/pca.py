@@ -13,9 +13,11 @@ the readings used here (the kernel takes the same ones):
   word r mod 4 of Philox4x32-10 with counter (t, level | 2^30, v, r // 4) and
   key = seed (with replacement).  s_cap = clamp(floor(40960 / d), 8, 128).
 * covariance of the sample, C = A^T A / s with A the centred rows.
-* Lanczos with full reorthogonalisation from the node's random direction
-  (the one the random partitioner would use, normalised), at most
-  q = min(8, d) steps, stopping once beta_j <= 1e-4 * max_i alpha_i.
+* Lanczos with full reorthogonalisation (each C v_j is orthogonalised
+  against every earlier basis vector by one classical Gram-Schmidt pass; its
+  coefficient on v_j is alpha_j) from the node's random direction (the one
+  the random partitioner would use, normalised), at most q = min(8, d)
+  steps, stopping once beta_j <= 1e-4 * max_i alpha_i.
 * the Ritz vector of the largest eigenvalue of the tridiagonal matrix,
   normalised, with its largest-magnitude entry made positive (ties: the
   lowest index).
@@ -60,12 +62,13 @@ def lanczos_top(C_mul, v0: np.ndarray, steps: int):
     amax = 0.0
     for j in range(steps):
         w = C_mul(V[j])
-        a = float(w @ V[j])
+        # one classical Gram-Schmidt pass against v_0 .. v_j: the coefficient
+        # on v_j is alpha_j; the pass also removes the three-term part
+        coef = V[:j + 1] @ w
+        a = float(coef[j])
         alpha.append(a)
         amax = max(amax, a)
-        w = w - a * V[j] - (beta[-1] * V[j - 1] if j > 0 else 0.0)
-        for _ in range(2):  # classical Gram-Schmidt, twice
-            w = w - V[:j + 1].T @ (V[:j + 1] @ w)
+        w = w - V[:j + 1].T @ coef
         b = float(np.linalg.norm(w))
         if j == steps - 1 or b <= 1e-4 * amax:
             break

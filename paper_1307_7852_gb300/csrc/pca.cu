@@ -8,9 +8,10 @@
 //     counter (tree, level | 2^30, node, r / 4)); members are read in the
 //     node's ascending-id order; s_cap = clamp(floor(40960 / d), 8, 128);
 //  2. the sampled rows, centred, in shared memory (FP32);
-//  3. Lanczos with full reorthogonalisation (Gram-Schmidt twice) on
-//     C = A^T A / s from the node's random direction, at most min(8, d)
-//     steps, stopping once beta_j <= 1e-4 * max alpha;
+//  3. Lanczos with full reorthogonalisation (one classical Gram-Schmidt
+//     pass of C v_j against every earlier basis vector, whose coefficient
+//     on v_j is alpha_j) on C = A^T A / s from the node's random direction,
+//     at most min(8, d) steps, stopping once beta_j <= 1e-4 * max alpha;
 //  4. the top eigenvector of the tridiagonal matrix (one warp: Sturm
 //     multisection for the eigenvalue, inverse iteration for the vector),
 //     the Ritz vector, normalised, its largest entry made positive (ties:
@@ -222,44 +223,36 @@ __device__ void pca_node(const Loader& L, int64_t n, const SplitNode& nd, const 
             if (lane == 0) u[r] = acc;
         }
         __syncthreads();
-        // w = A^T u / s, and alpha = w . v_j
-        v1[0] = 0.f;
+        // w = A^T u / s; one classical Gram-Schmidt pass against v_0 .. v_j
+        // (full reorthogonalisation) gives alpha_j, the coefficient of v_j,
+        // and removes the three-term recurrence's part with the rest
+        float coef[kPcaSteps];
+#pragma unroll
+        for (int i = 0; i < kPcaSteps; ++i) coef[i] = 0.f;
         for (int c = tid; c < d; c += kPcaThreads) {
             float acc = 0.f;
             for (int r = 0; r < s; ++r) acc = fmaf(A[(size_t)r * dp + c], u[r], acc);
-            w[c] = acc / (float)s;
-            v1[0] = fmaf(w[c], vj[c], v1[0]);
+            const float wc = acc / (float)s;
+            w[c] = wc;
+#pragma unroll
+            for (int i = 0; i < kPcaSteps; ++i)
+                if (i <= j) coef[i] = fmaf(V[(size_t)i * dp + c], wc, coef[i]);
         }
-        pca_block_sums(v1, 1, red);
-        const float a = v1[0];
+        pca_block_sums(coef, j + 1, red);
+        float a = 0.f;
+#pragma unroll
+        for (int i = 0; i < kPcaSteps; ++i)
+            if (i == j) a = coef[i];
         amax = fmaxf(amax, a);
-        const float bprev = j > 0 ? beta[j - 1] : 0.f;
-        for (int c = tid; c < d; c += kPcaThreads) {
-            float x = w[c] - a * vj[c];
-            if (j > 0) x -= bprev * V[(size_t)(j - 1) * dp + c];
-            w[c] = x;
-        }
-        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-            float coef[kPcaSteps];
-#pragma unroll
-            for (int i = 0; i < kPcaSteps; ++i) coef[i] = 0.f;
-            for (int c = tid; c < d; c += kPcaThreads) {
-                const float wc = w[c];
-#pragma unroll
-                for (int i = 0; i < kPcaSteps; ++i)
-                    if (i <= j) coef[i] = fmaf(V[(size_t)i * dp + c], wc, coef[i]);
-            }
-            pca_block_sums(coef, j + 1, red);
-            for (int c = tid; c < d; c += kPcaThreads) {
-                float x = w[c];
-#pragma unroll
-                for (int i = 0; i < kPcaSteps; ++i)
-                    if (i <= j) x -= coef[i] * V[(size_t)i * dp + c];
-                w[c] = x;
-            }
-        }
         v1[0] = 0.f;
-        for (int c = tid; c < d; c += kPcaThreads) v1[0] = fmaf(w[c], w[c], v1[0]);
+        for (int c = tid; c < d; c += kPcaThreads) {
+            float x = w[c];
+#pragma unroll
+            for (int i = 0; i < kPcaSteps; ++i)
+                if (i <= j) x -= coef[i] * V[(size_t)i * dp + c];
+            w[c] = x;
+            v1[0] = fmaf(x, x, v1[0]);
+        }
         pca_block_sums(v1, 1, red);
         const float b = sqrtf(v1[0]);
         if (tid == 0) {
