@@ -73,6 +73,7 @@ def _load():
             lib.orc_leaf_knn_quant.argtypes = [P, i64, i32, i64, P, P, P, i64, i32, i32, P, P]
             lib.orc_merge.argtypes = [P, i64, i32, i64, i32, i32, P, P, P]
             lib.orc_propagate.argtypes = [P, i64, i32, i64, i32, P, P, P]
+            lib.orc_propagate_rows.argtypes = [P, i64, i32, i64, i32, P, P, i64, P, P]
             lib.orc_knn_exact.argtypes = [P, i64, i32, i64, i32, P, i64, P, P]
             lib.orc_pair_dist.argtypes = [P, i32, i64, P, P, i64, P]
             lib.orc_normalize_rows.argtypes = [P, i64, i32, i64, P]
@@ -258,6 +259,18 @@ def propagate(X, ids_in, k: int):
     ids = np.empty((n, k), dtype=np.int32)
     dists = np.empty((n, k), dtype=np.float32)
     lib.orc_propagate(_ptr(X), n, d, d, k, _ptr(ids_in), _ptr(ids), _ptr(dists))
+    return ids, dists
+
+
+def propagate_rows(X, ids_in, k: int, rows):
+    """One first-order round for the given points only: [len(rows), k]."""
+    X = _as_f32(X)
+    n, d = X.shape
+    ids_in = np.ascontiguousarray(ids_in, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    ids = np.empty((rows.shape[0], k), dtype=np.int32)
+    dists = np.empty((rows.shape[0], k), dtype=np.float32)
+    _load().orc_propagate_rows(_ptr(X), n, d, d, k, _ptr(ids_in), _ptr(rows), rows.shape[0], _ptr(ids), _ptr(dists))
     return ids, dists
 
 

@@ -414,37 +414,55 @@ int orc_merge(const float* X, int64_t n, int d, int64_t ld, int T, int k, const 
 /* without p; the new list is the k best candidates by (D, id).  All lists   */
 /* are read from the input graph (a synchronous round).                     */
 /* ------------------------------------------------------------------------ */
+/* First-order candidates of p (its list and its neighbours' lists, without
+ * p, deduplicated) and the k best of them by (D, id). */
+static void propagate_point(const float* X, int64_t n, int d, int64_t ld, int k, const int32_t* in_ids,
+                            int64_t p, int32_t* ids, float* dists)
+{
+    int64_t cap = (int64_t)k + (int64_t)k * k;
+    int32_t* u = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
+    int64_t cnt = 0;
+    for (int e = 0; e < k; ++e) {
+        int32_t q = in_ids[p * k + e];
+        if (q < 0) continue;
+        if (q != p) u[cnt++] = q;
+        for (int f = 0; f < k; ++f) {
+            int32_t o = in_ids[(int64_t)q * k + f];
+            if (o < 0 || o == p) continue;
+            u[cnt++] = o;
+        }
+    }
+    qsort(u, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    cand_t* c = (cand_t*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(cand_t));
+    int64_t m = 0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        if (e > 0 && u[e] == u[e - 1]) continue;
+        c[m].id = u[e];
+        c[m].D = sqdist64(X + p * ld, X + (int64_t)u[e] * ld, d);
+        ++m;
+    }
+    emit_topk(c, m, k, ids, dists);
+    free(c);
+    free(u);
+    (void)n;
+}
+
 int orc_propagate(const float* X, int64_t n, int d, int64_t ld, int k, const int32_t* in_ids,
                   int32_t* ids, float* dists)
 {
 #pragma omp parallel for schedule(dynamic, 256)
-    for (int64_t p = 0; p < n; ++p) {
-        int64_t cap = (int64_t)k + (int64_t)k * k;
-        int32_t* u = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
-        int64_t cnt = 0;
-        for (int e = 0; e < k; ++e) {
-            int32_t q = in_ids[p * k + e];
-            if (q < 0) continue;
-            if (q != p) u[cnt++] = q;
-            for (int f = 0; f < k; ++f) {
-                int32_t o = in_ids[(int64_t)q * k + f];
-                if (o < 0 || o == p) continue;
-                u[cnt++] = o;
-            }
-        }
-        qsort(u, (size_t)cnt, sizeof(int32_t), cmp_i32);
-        cand_t* c = (cand_t*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(cand_t));
-        int64_t m = 0;
-        for (int64_t e = 0; e < cnt; ++e) {
-            if (e > 0 && u[e] == u[e - 1]) continue;
-            c[m].id = u[e];
-            c[m].D = sqdist64(X + p * ld, X + (int64_t)u[e] * ld, d);
-            ++m;
-        }
-        emit_topk(c, m, k, ids + p * k, dists + p * k);
-        free(c);
-        free(u);
-    }
+    for (int64_t p = 0; p < n; ++p) propagate_point(X, n, d, ld, k, in_ids, p, ids + p * k, dists + p * k);
+    return 0;
+}
+
+/* The same round for the points rows[0 .. nrows) only: row r of ids/dists
+ * ([nrows][k]) is the new list of point rows[r]. */
+int orc_propagate_rows(const float* X, int64_t n, int d, int64_t ld, int k, const int32_t* in_ids,
+                       const int32_t* rows, int64_t nrows, int32_t* ids, float* dists)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < nrows; ++r)
+        propagate_point(X, n, d, ld, k, in_ids, rows[r], ids + r * k, dists + r * k);
     return 0;
 }
 

@@ -449,3 +449,13 @@ def test_cosine_graph_is_scale_invariant():
     b = oracle.build_graph(S, 8, 2, 48, 1, 4, metric=oracle.METRIC_COSINE)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_propagate_rows_is_the_round_on_those_rows():
+    X = synthetic.sift_like(3000, 32, centers=8, seed=1)
+    ids, _ = oracle.build_graph(X, 8, 2, 40, 0, 3)
+    full = oracle.propagate(X, ids, 8)
+    rows = np.array([5, 17, 2999, 0, 1500])
+    part = oracle.propagate_rows(X, ids, 8, rows)
+    np.testing.assert_array_equal(part[0], full[0][rows])
+    np.testing.assert_array_equal(part[1], full[1][rows])
