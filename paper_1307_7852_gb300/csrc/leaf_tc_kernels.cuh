@@ -340,6 +340,27 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
             const bool valid = row_ok && j < m && j != iloc;
             return valid ? ord_key(dv) : 0xFFFFFFFFu;
         };
+        // the distance parts of one chunk of 32 columns (BF16): the norms of
+        // the columns read as float4; only the self column and, in the last
+        // chunk, columns past the leaf are invalid (rows past the leaf are
+        // never output, so their values do not matter)
+        auto chunk_hi = [&](const uint32_t (&r)[32], int c0, uint32_t (&h)[32]) {
+            const bool tail = c0 + 32 > m;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 q = *reinterpret_cast<const float4*>(qn + c0 + 4 * i);
+                const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    const int e = 4 * i + e2;
+                    const float dv = ni + qv[e2] - 2.f * __uint_as_float(r[e]);
+                    uint32_t x = ord_key(dv);
+                    x = (c0 + e == iloc) ? 0xFFFFFFFFu : x;
+                    if (tail) x = (c0 + e < m) ? x : 0xFFFFFFFFu;
+                    h[e] = x;
+                }
+            }
+        };
         if (fast) {
             // pass 1: group minima
             uint32_t gm[32];
@@ -349,8 +370,15 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 uint32_t r[32];
                 tc::tmem_ld32(trow + (uint32_t)c0, r);
                 tc::tmem_ld_wait();
+                if (PREC == 1) {
+                    uint32_t h[32];
+                    chunk_hi(r, c0, h);
 #pragma unroll
-                for (int e = 0; e < 32; ++e) gm[e] = min(gm[e], hi_of(r[e], c0 + e));
+                    for (int e = 0; e < 32; ++e) gm[e] = min(gm[e], h[e]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) gm[e] = min(gm[e], hi_of(r[e], c0 + e));
+                }
             }
             reg_bitonic_sort(gm);
 #pragma unroll
@@ -373,12 +401,17 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 uint32_t r[32];
                 tc::tmem_ld32(trow + (uint32_t)c0, r);
                 tc::tmem_ld_wait();
+                uint32_t h[32];
+                if (PREC == 1) {
+                    chunk_hi(r, c0, h);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) h[e] = hi_of(r[e], c0 + e);
+                }
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
-                    const int j = c0 + e;
-                    const uint32_t h = hi_of(r[e], j);
-                    if (h != 0xFFFFFFFFu && h <= tau) {
-                        if (c < 32) cand[c * kTcThreads + tid] = ((uint64_t)h << 32) | (uint32_t)j;
+                    if (h[e] != 0xFFFFFFFFu && h[e] <= tau) {
+                        if (c < 32) cand[c * kTcThreads + tid] = ((uint64_t)h[e] << 32) | (uint32_t)(c0 + e);
                         ++c;
                     }
                 }
