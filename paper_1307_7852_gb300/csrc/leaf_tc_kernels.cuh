@@ -308,9 +308,9 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
     // the distance parts (high 32 bits of the keys) over the columns with
     // the same position in their chunk (32 groups per thread), sorts them;
     // the want-th smallest of the 64 minima of a row (both halves) bounds the
-    // row's answer.  Pass 2 lists the columns up to that bound (at most 32
-    // per thread), each thread sorts its list, and the half-0 thread merges
-    // the row's two lists.  Rows whose lists overflow, and all rows when more
+    // row's answer.  Pass 2 lists the columns up to that bound, and the
+    // half-0 thread sorts the union of the row's two lists (at most 32) with
+    // a register network.  Rows whose lists overflow, and all rows when more
     // than 32 candidates are wanted, take the warp-per-row path below.
     if (!abort_flag) {
         const int quad = w & 3, half = w >> 2;
@@ -421,41 +421,44 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 any_overflow = 1;
             }
             ccount[tid] = min(c, 32);
-            {
-                uint64_t v[32];
-#pragma unroll
-                for (int e = 0; e < 32; ++e) v[e] = e < c ? cand[e * kTcThreads + tid] : kKeyMax;
-                reg_bitonic_sort(v);
-#pragma unroll
-                for (int e = 0; e < 32; ++e) cand[e * kTcThreads + tid] = v[e];
-            }
             __syncthreads();
-            // merge the row's two sorted lists; exact leaves write the output
+            // the half-0 thread of a row sorts the union of the row's two
+            // lists (a register network) and writes the exact leaves' output
+            // (or the list to rescore); a union of more than 32 overflows
             uint64_t* rowlist = reinterpret_cast<uint64_t*>(gsh);  // [32][128], minima are dead
             if (half == 0 && row_ok && !rowflag[lr]) {
                 const int ptid = tid ^ 128;
                 const int ca = ccount[tid], cb = ccount[ptid];
-                const int gi = lid[iloc];
-                int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
-                float* od = out_d + ((int64_t)t * n + gi) * k;
-                int ia = 0, ib = 0;
-                for (int s2 = 0; s2 < want; ++s2) {
-                    const uint64_t xa = ia < ca ? cand[ia * kTcThreads + tid] : kKeyMax;
-                    const uint64_t xb = ib < cb ? cand[ib * kTcThreads + ptid] : kKeyMax;
-                    const uint64_t x = xa < xb ? xa : xb;
-                    if (xa < xb) ++ia; else ++ib;
+                if (ca + cb > 32) {
+                    rowflag[lr] = 1;
+                    any_overflow = 1;
+                } else {
+                    uint64_t v[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        v[e] = e < ca ? cand[e * kTcThreads + tid]
+                                      : (e - ca < cb ? cand[(e - ca) * kTcThreads + ptid] : kKeyMax);
+                    reg_bitonic_sort(v);
                     if (exact_leaf) {
-                        oi[s2] = lid[(uint32_t)x];
-                        od[s2] = unord_key((uint32_t)(x >> 32));
+                        const int gi = lid[iloc];
+                        int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
+                        float* od = out_d + ((int64_t)t * n + gi) * k;
+#pragma unroll
+                        for (int s2 = 0; s2 < 32; ++s2)
+                            if (s2 < want) {
+                                oi[s2] = lid[(uint32_t)v[s2]];
+                                od[s2] = unord_key((uint32_t)(v[s2] >> 32));
+                            }
+                        for (int s2 = want; s2 < k; ++s2) {
+                            oi[s2] = -1;
+                            od[s2] = __int_as_float(0x7f800000);
+                        }
                     } else {
-                        rowlist[s2 * 128 + lr] = x;
+#pragma unroll
+                        for (int s2 = 0; s2 < 32; ++s2)
+                            if (s2 < want) rowlist[s2 * 128 + lr] = v[s2];
                     }
                 }
-                if (exact_leaf)
-                    for (int s2 = want; s2 < k; ++s2) {
-                        oi[s2] = -1;
-                        od[s2] = __int_as_float(0x7f800000);
-                    }
             }
             __syncthreads();
             if (!exact_leaf) {
