@@ -168,8 +168,9 @@ __device__ __forceinline__ void reg_bitonic_sort(T (&v)[N])
 }
 
 // Shared memory of the row-per-thread selection (reusing the pipeline):
-// sorted group minima [32][256] u32 (later the rows' merged lists [32][128]
-// u64) and candidate lists [32][256] u64.
+// sorted group minima [32][256] u32 (later the halves' sorted runs
+// [2][16][128] u64) and candidate lists [32][256] u64 (later the rows'
+// merged lists [32][128] u64).
 constexpr int kFastSmem = 32 * kTcThreads * 4 + 32 * kTcThreads * 8;
 
 template <int PREC, int PER, int kDT>
@@ -384,16 +385,23 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
 #pragma unroll
             for (int e = 0; e < 32; ++e) gsh[e * kTcThreads + tid] = gm[e];
             __syncthreads();
-            // the want-th smallest of the row's 64 minima (two sorted lists)
+            // the want-th smallest of the row's 64 minima (two sorted lists
+            // A, B): binary search for the number i of them taken from A, the
+            // smallest i with A[i] >= B[want - i - 1]
             const int ptid = tid ^ 128;
-            uint32_t tau = 0xFFFFFFFFu;
+            uint32_t tau;
             {
-                int ia = 0, ib = 0;
-                for (int s2 = 0; s2 < want; ++s2) {
-                    const uint32_t xa = ia < 32 ? gsh[ia * kTcThreads + tid] : 0xFFFFFFFFu;
-                    const uint32_t xb = ib < 32 ? gsh[ib * kTcThreads + ptid] : 0xFFFFFFFFu;
-                    if (xa <= xb) { tau = xa; ++ia; } else { tau = xb; ++ib; }
+                int lo = max(0, want - 32), hi = min(want, 32);
+                while (lo < hi) {
+                    const int i = (lo + hi) >> 1;
+                    const uint32_t a = gsh[i * kTcThreads + tid];  // i < hi <= 32
+                    const uint32_t b = gsh[(want - i - 1) * kTcThreads + ptid];
+                    if (a >= b) hi = i;
+                    else lo = i + 1;
                 }
+                const uint32_t ta = lo > 0 ? gsh[(lo - 1) * kTcThreads + tid] : 0u;
+                const uint32_t tb = want - lo > 0 ? gsh[(want - lo - 1) * kTcThreads + ptid] : 0u;
+                tau = max(ta, tb);
             }
             // pass 2: the candidates up to the bound
             int c = 0;
@@ -422,42 +430,81 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
             }
             ccount[tid] = min(c, 32);
             __syncthreads();
-            // the half-0 thread of a row sorts the union of the row's two
-            // lists (a register network) and writes the exact leaves' output
-            // (or the list to rescore); a union of more than 32 overflows
-            uint64_t* rowlist = reinterpret_cast<uint64_t*>(gsh);  // [32][128], minima are dead
-            if (half == 0 && row_ok && !rowflag[lr]) {
-                const int ptid = tid ^ 128;
-                const int ca = ccount[tid], cb = ccount[ptid];
-                if (ca + cb > 32) {
-                    rowflag[lr] = 1;
-                    any_overflow = 1;
+            // the union of the row's two lists (slots: list A, then list B),
+            // at most 32 (more overflows): each half sorts 16 slots with a
+            // register network; then the half-0 thread merges the two sorted
+            // runs forward into ranks 0..15 and the half-1 thread backward
+            // into ranks 31..16 (the keys are distinct: no ties to order),
+            // and both write the exact leaves' output (or the list to
+            // rescore)
+            const int rtA = tid & 127, rtB = rtA | 128;  // the row's two threads
+            const int ca = ccount[rtA], cb = ccount[rtB];
+            const bool sel = row_ok && !rowflag[lr] && ca + cb <= 32;
+            uint64_t* srt = reinterpret_cast<uint64_t*>(gsh);  // [2][16][128], minima are dead
+            if (sel) {
+                uint64_t v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int u = 16 * half + e;
+                    v[e] = u < ca ? cand[u * kTcThreads + rtA]
+                                  : (u - ca < cb ? cand[(u - ca) * kTcThreads + rtB] : kKeyMax);
+                }
+                reg_bitonic_sort(v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) srt[(16 * half + e) * 128 + lr] = v[e];
+            } else if (row_ok && half == 0 && !rowflag[lr]) {
+                rowflag[lr] = 1;
+                any_overflow = 1;
+            }
+            __syncthreads();
+            uint64_t* rowlist = reinterpret_cast<uint64_t*>(cand);  // [32][128], the lists are dead
+            if (sel) {
+                const uint64_t* S0 = srt + lr;
+                const uint64_t* S1 = srt + 16 * 128 + lr;
+                uint64_t v[16];
+                if (half == 0) {
+                    int i = 0, j = 0;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const uint64_t a = i < 16 ? S0[i * 128] : kKeyMax;
+                        const uint64_t b = j < 16 ? S1[j * 128] : kKeyMax;
+                        const bool ta = a <= b;
+                        v[e] = ta ? a : b;
+                        i += ta ? 1 : 0;
+                        j += ta ? 0 : 1;
+                    }
                 } else {
-                    uint64_t v[32];
+                    int i = 15, j = 15;
 #pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        v[e] = e < ca ? cand[e * kTcThreads + tid]
-                                      : (e - ca < cb ? cand[(e - ca) * kTcThreads + ptid] : kKeyMax);
-                    reg_bitonic_sort(v);
-                    if (exact_leaf) {
-                        const int gi = lid[iloc];
-                        int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
-                        float* od = out_d + ((int64_t)t * n + gi) * k;
+                    for (int e = 15; e >= 0; --e) {
+                        const uint64_t a = i >= 0 ? S0[i * 128] : 0ull;
+                        const uint64_t b = j >= 0 ? S1[j * 128] : 0ull;
+                        const bool ta = a > b;
+                        v[e] = ta ? a : b;
+                        i -= ta ? 1 : 0;
+                        j -= ta ? 0 : 1;
+                    }
+                }
+                const int r0s = 16 * half;  // rank of v[0]
+                if (exact_leaf) {
+                    const int gi = lid[iloc];
+                    int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
+                    float* od = out_d + ((int64_t)t * n + gi) * k;
 #pragma unroll
-                        for (int s2 = 0; s2 < 32; ++s2)
-                            if (s2 < want) {
-                                oi[s2] = lid[(uint32_t)v[s2]];
-                                od[s2] = unord_key((uint32_t)(v[s2] >> 32));
-                            }
+                    for (int e = 0; e < 16; ++e)
+                        if (r0s + e < want) {
+                            oi[r0s + e] = lid[(uint32_t)v[e]];
+                            od[r0s + e] = unord_key((uint32_t)(v[e] >> 32));
+                        }
+                    if (half == 0)
                         for (int s2 = want; s2 < k; ++s2) {
                             oi[s2] = -1;
                             od[s2] = __int_as_float(0x7f800000);
                         }
-                    } else {
+                } else {
 #pragma unroll
-                        for (int s2 = 0; s2 < 32; ++s2)
-                            if (s2 < want) rowlist[s2 * 128 + lr] = v[s2];
-                    }
+                    for (int e = 0; e < 16; ++e)
+                        if (r0s + e < want) rowlist[(r0s + e) * 128 + lr] = v[e];
                 }
             }
             __syncthreads();

@@ -134,7 +134,7 @@ void make_tree_plan(int64_t n, int g, TreePlan& P)
 // Kernels
 // ---------------------------------------------------------------------------
 __global__ void init_perm_kernel(int64_t n, int T, int first_node, int32_t* perm, int32_t* pos_of,
-                                 int32_t* node_of)
+                                 int32_t* node_of, int32_t* node_pos)
 {
     const int64_t total = (int64_t)T * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -143,16 +143,23 @@ __global__ void init_perm_kernel(int64_t n, int T, int first_node, int32_t* perm
         perm[e] = i;
         pos_of[e] = i;
         node_of[e] = first_node;
+        node_pos[e] = first_node;
     }
 }
 
 // Points of the root node s of level 0 start in node s (other points are in
-// roots that are already leaves and keep node -1).
-__global__ void init_root_nodes_kernel(int64_t n, const SplitNode* __restrict__ nodes, int32_t* node_of)
+// roots that are already leaves and keep node -1).  At level 0 positions are
+// ids, so the map by id and the map by position start equal.
+__global__ void init_root_nodes_kernel(int64_t n, const SplitNode* __restrict__ nodes, int32_t* node_of,
+                                       int32_t* node_pos)
 {
     const SplitNode nd = nodes[blockIdx.x];
     int32_t* row = node_of + (int64_t)blockIdx.y * n;
-    for (int e = threadIdx.x; e < nd.size; e += blockDim.x) row[nd.off + e] = (int32_t)blockIdx.x;
+    int32_t* prow = node_pos + (int64_t)blockIdx.y * n;
+    for (int e = threadIdx.x; e < nd.size; e += blockDim.x) {
+        row[nd.off + e] = (int32_t)blockIdx.x;
+        prow[nd.off + e] = (int32_t)blockIdx.x;
+    }
 }
 
 // dirs[t][s][0..d_pad): direction of split node s of this level in tree
@@ -342,68 +349,169 @@ __global__ void __launch_bounds__(256) project_kernel(RowLoader<kDT> L, RowLoade
     project_body<kLearned>(L, n, T, dirs, S, d_pad, node_of, pos_of, keys, lv);
 }
 
-// Node-major projection of byte rows (16-byte aligned, rows padded to
-// multiples of 16 bytes): one thread per (tree, position).  Threads of a
-// warp take consecutive positions, i.e. mostly the same node, so the
-// direction is one broadcast load per 16 bytes while every thread gathers
-// its own row (d bytes).  The thread forms the 32 lane partials of the
-// canonical order (lane l: j = 128c + 4l + e, fmaf) and the pairwise rounds
-// 16, 8, 4, 2, 1 itself, so the value is the one of the warp-cooperative
-// projection bit for bit.  Unless bytes_given, it runs only when the byte
-// copy of float rows is exact (*xb_bad == 0).
-__global__ void __launch_bounds__(256) project_bytes_kernel(RowLoader<kDtU8> Lb, const int* __restrict__ xb_bad,
-                                                            bool bytes_given, int64_t n, int T,
-                                                            const float* __restrict__ dirs, int S, int d_pad,
-                                                            const int32_t* __restrict__ cur,
-                                                            const int32_t* __restrict__ node_of,
-                                                            uint32_t* __restrict__ keys)
+// Exact floats of the four bytes of w: the byte permute assembles 2^23 + b
+// (the exponent of 2^23 with b in the low mantissa bits) and one packed add
+// takes 2^23 off two of them at a time; both steps are exact.  This keeps
+// the conversion off the integer-to-float unit, which runs at a quarter of
+// the FMA rate.
+__device__ __forceinline__ void bytes_exact4(uint32_t w, float& x0, float& x1, float& x2, float& x3)
 {
+    const float2 off = make_float2(-8388608.0f, -8388608.0f);
+    const float2 lo = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u)),
+                                             __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541u))),
+                                 off);
+    const float2 hi = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7542u)),
+                                             __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7543u))),
+                                 off);
+    x0 = lo.x;
+    x1 = lo.y;
+    x2 = hi.x;
+    x3 = hi.y;
+}
+
+// Lane partial of the canonical order over one 4-byte word: s plus
+// x[j..j+3] . a[j..j+3] by four fmaf in j order.
+__device__ __forceinline__ float word_partial(uint32_t w, const float4& a, float s)
+{
+    float x0, x1, x2, x3;
+    bytes_exact4(w, x0, x1, x2, x3);
+    s = fmaf(x0, a.x, s);
+    s = fmaf(x1, a.y, s);
+    s = fmaf(x2, a.z, s);
+    return fmaf(x3, a.w, s);
+}
+
+// Rows of at most 128 bytes (one canonical chunk): the value of lane
+// partial L after the pairwise rounds down to distance O (O = 32: the
+// partial itself), evaluated depth-first so that few sums are live at once.
+// Partial L covers bytes 4L .. 4L + 3; words past the row (L >= nw) and
+// direction entries past d contribute nothing (the row's padding bytes and
+// the direction's padding entries are zeros, and adding +0 * 0 to a partial,
+// which is never -0, leaves it unchanged).
+template <int L, int O, bool kFull>
+struct ProjTree {
+    static __device__ __forceinline__ float eval(const uint32_t (&w)[32], const float* __restrict__ a, int nw,
+                                                 int d)
+    {
+        return ProjTree<L, 2 * O, kFull>::eval(w, a, nw, d) + ProjTree<L + O, 2 * O, kFull>::eval(w, a, nw, d);
+    }
+};
+template <int L, bool kFull>
+struct ProjTree<L, 32, kFull> {
+    static __device__ __forceinline__ float eval(const uint32_t (&w)[32], const float* __restrict__ a, int nw,
+                                                 int d)
+    {
+        if (kFull) return word_partial(w[L], __ldg(reinterpret_cast<const float4*>(a + 4 * L)), 0.0f);
+        if (L >= nw || 4 * L >= d) return 0.0f;
+        return word_partial(w[L], __ldg(reinterpret_cast<const float4*>(a + 4 * L)), 0.0f);
+    }
+};
+
+// Node-major projection of byte rows (16-byte aligned, rows padded to
+// multiples of 16 bytes with zeros, or byte input of such rows): one thread
+// per (tree, position), a warp on 32 consecutive positions, which mostly
+// share their node, so a direction load is one broadcast.  The thread forms
+// the 32 lane partials of the canonical order (lane l: j = 128c + 4l + e,
+// fmaf) and the pairwise rounds 16, 8, 4, 2, 1 itself, so the value is the
+// one of the warp-cooperative projection bit for bit.  Rows of at most 128
+// bytes (kOneChunk) are fetched by the warp eight lanes to a row (one
+// 128-byte line per four lanes' loads instead of one line per lane and
+// load) into shared memory, and each thread then sums its row depth-first;
+// longer rows are gathered by their threads.  The node comes from the map
+// by position.  Unless bytes_given, it runs only when the byte copy of
+// float rows is exact (*xb_bad == 0).
+template <bool kOneChunk, bool kFull>
+__global__ void __launch_bounds__(256, 4) project_bytes_kernel(RowLoader<kDtU8> Lb, const int* __restrict__ xb_bad,
+                                                               bool bytes_given, int64_t n, int T,
+                                                               const float* __restrict__ dirs, int S, int d_pad,
+                                                               const int32_t* __restrict__ cur,
+                                                               const int32_t* __restrict__ node_pos,
+                                                               uint32_t* __restrict__ keys)
+{
+    // rows staged per warp: 32 rows of 8 16-byte words, stride 9 words (the
+    // 16-byte accesses of eight lanes fall in distinct banks)
+    __shared__ uint4 srow[8][32][9];
     if (!bytes_given && (!xb_bad || *xb_bad != 0)) return;
     const int d = Lb.d;
+    const int nq = (d + 15) >> 4;  // 16-byte words of a row
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int64_t total = (int64_t)T * n;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(g / n);
-        const int32_t id = cur[g];
-        const int sn = node_of[(int64_t)t * n + id];
-        if (sn < 0) continue;  // a leaf of an earlier level
-        const float* a = dirs + ((int64_t)t * S + sn) * d_pad;
-        const uint8_t* row = static_cast<const uint8_t*>(Lb.X) + Lb.row_off(id);
-        float acc[32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int t = (int)(g / n);
+    int64_t i = g - (int64_t)t * n;  // position within tree t (g = t n + i)
+    const uint8_t* X = static_cast<const uint8_t*>(Lb.X);
+    for (; g - lane < total; g += stride) {  // whole warps iterate together
+        const bool valid = g < total;
+        const int tt = t;
+        i += stride;
+        while (i >= n && t < T) {
+            i -= n;
+            ++t;
+        }
+        const int32_t id = valid ? cur[g] : 0;
+        const int sn = valid ? node_pos[g] : -1;  // -1: a leaf of an earlier level
+        float v = 0.f;
+        if constexpr (kOneChunk) {
+            // the warp's rows, eight lanes to a row
+            const int q = lane & 7;
 #pragma unroll
-        for (int l = 0; l < 32; ++l) acc[l] = 0.f;
-        for (int c0 = 0; c0 < d; c0 += 128) {
+            for (int r = 0; r < 8; ++r) {
+                const int rr = 4 * r + (lane >> 3);
+                const int32_t idr = __shfl_sync(KNNG_FULL_MASK, id, rr);
+                const int snr = __shfl_sync(KNNG_FULL_MASK, sn, rr);
+                uint4 u = make_uint4(0u, 0u, 0u, 0u);
+                if (snr >= 0 && (kFull || q < nq))
+                    u = __ldg(reinterpret_cast<const uint4*>(X + Lb.row_off(idr) + 16 * q));
+                srow[wq][rr][q] = u;
+            }
+            __syncwarp();
+            if (sn >= 0) {
+                uint32_t w[32];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int jb = c0 + 16 * q;  // bytes jb .. jb + 15: lanes 4q .. 4q + 3
-                if (jb < d) {
-                    const uint4 w = __ldg(reinterpret_cast<const uint4*>(row + jb));
-                    const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+                for (int c = 0; c < 8; ++c) {
+                    const uint4 u = srow[wq][lane][c];
+                    w[4 * c + 0] = u.x;
+                    w[4 * c + 1] = u.y;
+                    w[4 * c + 2] = u.z;
+                    w[4 * c + 3] = u.w;
+                }
+                const float* a = dirs + ((int64_t)tt * S + sn) * d_pad;
+                v = ProjTree<0, 1, kFull>::eval(w, a, 4 * nq, d);
+            }
+            __syncwarp();  // the rows are read before the next batch lands
+        } else {
+            if (sn >= 0) {
+                const uint8_t* row = X + Lb.row_off(id);
+                const float* a = dirs + ((int64_t)tt * S + sn) * d_pad;
+                float acc[32];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int j = jb + 4 * h;
-                        const float4 av = __ldg(reinterpret_cast<const float4*>(a + j));
-                        const float4 xv = bytes_to_float4(wv[h]);
-                        float& s = acc[4 * q + h];
-                        if (j + 3 < d) {
-                            s = fmaf(xv.x, av.x, s);
-                            s = fmaf(xv.y, av.y, s);
-                            s = fmaf(xv.z, av.z, s);
-                            s = fmaf(xv.w, av.w, s);
-                        } else {
-                            if (j < d) s = fmaf(xv.x, av.x, s);
-                            if (j + 1 < d) s = fmaf(xv.y, av.y, s);
-                            if (j + 2 < d) s = fmaf(xv.z, av.z, s);
+                for (int l = 0; l < 32; ++l) acc[l] = 0.f;
+                for (int c0 = 0; c0 < d; c0 += 128) {
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq) {
+                        const int jb = c0 + 16 * qq;  // bytes jb .. jb + 15: lanes 4qq .. 4qq + 3
+                        if (jb < d) {
+                            const uint4 u = __ldg(reinterpret_cast<const uint4*>(row + jb));
+                            const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const int j = jb + 4 * h;
+                                if (j < d)
+                                    acc[4 * qq + h] = word_partial(
+                                        wv[h], __ldg(reinterpret_cast<const float4*>(a + j)), acc[4 * qq + h]);
+                            }
                         }
                     }
                 }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+                    for (int l = 0; l < o; ++l) acc[l] = acc[l] + acc[l + o];
+                v = acc[0];
             }
         }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1)
-#pragma unroll
-            for (int l = 0; l < o; ++l) acc[l] = acc[l] + acc[l + o];
-        keys[g] = ord_key(acc[0]);
+        if (sn >= 0) keys[g] = ord_key(v);
     }
 }
 
@@ -493,31 +601,59 @@ __device__ int block_excl_scan(int v, int* sh, int* total)
 }
 
 // Stable two-way scatter of elements [0, len) of a slice (keys in shared
-// memory), contiguous runs per thread.  lbase/rbase: destination of the
-// slice's first left / right element.
+// memory) in rounds of NT consecutive elements: a block-wide count of the
+// left elements before each one gives its destination, so a warp's left and
+// right elements land in two contiguous runs.  lbase/rbase: destination of
+// the slice's first left / right element.  The node of every destination
+// position is written to node_pos; the maps by id (pos_of, node_of) only
+// when a later projection reads them (id_maps).
 template <int NT>
 __device__ void stable_scatter(const unsigned long long* k64, int len, unsigned long long thr,
                                int32_t lbase, int32_t rbase, int32_t childL, int32_t childR,
-                               int32_t* perm_nxt, int32_t* pos_of, int32_t* node_of, int* sh)
+                               int32_t* perm_nxt, int32_t* node_pos, int32_t* pos_of, int32_t* node_of,
+                               bool id_maps, int* sh)
 {
-    const int tid = threadIdx.x;
-    const int per = (len + NT - 1) / NT;
-    const int e0 = min(len, tid * per), e1 = min(len, e0 + per);
-    int cl = 0;
-    for (int e = e0; e < e1; ++e) cl += (k64[e] <= thr);
-    int total;
-    const int lb = block_excl_scan<NT>(cl, sh, &total);
-    int lp = lbase + lb, rp = rbase + (e0 - lb);
-    for (int e = e0; e < e1; ++e) {
-        const unsigned long long kv = k64[e];
-        const int32_t id = (int32_t)(uint32_t)kv;
-        int32_t dst, child;
-        if (kv <= thr) { dst = lp++; child = childL; }
-        else { dst = rp++; child = childR; }
-        perm_nxt[dst] = id;
-        pos_of[id] = dst;
-        node_of[id] = child;
+    constexpr int NW = NT / 32;
+    static_assert(NW <= 16, "two rounds of warp counts share sh[0..31]");
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int before = 0;  // left elements of the earlier rounds
+    for (int base = 0, r = 0; base < len; base += NT, r ^= 1) {
+        const int e = base + tid;
+        const unsigned long long kv = e < len ? k64[e] : ~0ull;
+        const bool left = e < len && kv <= thr;
+        const uint32_t b = __ballot_sync(KNNG_FULL_MASK, left);
+        // the counts alternate between two halves of sh: one barrier a round
+        if (lane == 0) sh[16 * r + w] = __popc(b);
+        __syncthreads();
+        int pre = 0, tot = 0;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const int c = sh[16 * r + i];
+            pre += i < w ? c : 0;
+            tot += c;
+        }
+        if (e < len) {
+            const int lrank = before + pre + __popc(b & lanemask_lt());
+            const int32_t id = (int32_t)(uint32_t)kv;
+            const int32_t dst = left ? lbase + lrank : rbase + (e - lrank);
+            const int32_t child = left ? childL : childR;
+            perm_nxt[dst] = id;
+            node_pos[dst] = child;
+            if (id_maps) {
+                pos_of[id] = dst;
+                node_of[id] = child;
+            }
+        }
+        before += tot;
     }
+}
+
+// Whether this level's scatter keeps the maps by id: 1 always, 0 never,
+// 2 when the float rows' byte copy is not exact (*xb_bad != 0: the next
+// level then projects by id).
+__device__ __forceinline__ bool want_id_maps(int id_mode, const int* xb_bad)
+{
+    return id_mode == 1 || (id_mode == 2 && xb_bad && *xb_bad != 0);
 }
 
 // One block per (split node, tree), node <= kSmallCap points.
@@ -525,8 +661,8 @@ template <int NT>
 __global__ void __launch_bounds__(NT) split_small_kernel(int64_t n, const SplitNode* __restrict__ nodes,
                                                          const uint32_t* __restrict__ keys,
                                                          const int32_t* __restrict__ perm_cur,
-                                                         int32_t* perm_nxt, int32_t* pos_of,
-                                                         int32_t* node_of)
+                                                         int32_t* perm_nxt, int32_t* node_pos, int32_t* pos_of,
+                                                         int32_t* node_of, int id_mode, const int* xb_bad)
 {
     extern __shared__ unsigned long long k64[];
     __shared__ uint32_t hist[256];
@@ -540,7 +676,7 @@ __global__ void __launch_bounds__(NT) split_small_kernel(int64_t n, const SplitN
     __syncthreads();
     const unsigned long long thr = block_select<NT>(k64, m, m / 2, hist, bcast);
     stable_scatter<NT>(k64, m, thr, nd.off, nd.off + m / 2, nd.childL, nd.childR, perm_nxt + row,
-                       pos_of + row, node_of + row, sh);
+                       node_pos + row, pos_of + row, node_of + row, want_id_maps(id_mode, xb_bad), sh);
 }
 
 // ---- multi-block split of large nodes ------------------------------------
@@ -680,7 +816,8 @@ __global__ void __launch_bounds__(NT) big_scatter_kernel(int64_t n, int S, int n
                                                          const int32_t* __restrict__ perm_cur,
                                                          const SelState* __restrict__ st,
                                                          const int32_t* __restrict__ lbase_arr,
-                                                         int32_t* perm_nxt, int32_t* pos_of, int32_t* node_of)
+                                                         int32_t* perm_nxt, int32_t* node_pos, int32_t* pos_of,
+                                                         int32_t* node_of, int id_mode, const int* xb_bad)
 {
     __shared__ unsigned long long k64[kChunk];
     __shared__ int sh[33];
@@ -695,7 +832,8 @@ __global__ void __launch_bounds__(NT) big_scatter_kernel(int64_t n, int S, int n
     const int32_t lb = lbase_arr[(int64_t)t * nchunks + blockIdx.x];
     const int32_t before = c.start - nd.off;
     stable_scatter<NT>(k64, c.len, thr, nd.off + lb, nd.off + nd.size / 2 + (before - lb), nd.childL,
-                       nd.childR, perm_nxt + row, pos_of + row, node_of + row, sh);
+                       nd.childR, perm_nxt + row, node_pos + row, pos_of + row, node_of + row,
+                       want_id_maps(id_mode, xb_bad), sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -720,6 +858,7 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
     int32_t* perm_b = ar.take<int32_t>((size_t)T * n);
     int32_t* pos_of = ar.take<int32_t>((size_t)T * n);
     int32_t* node_of = ar.take<int32_t>((size_t)T * n);
+    int32_t* node_pos = ar.take<int32_t>((size_t)T * n);
     uint32_t* keys = ar.take<uint32_t>((size_t)T * n);
     float* dirs = ar.take<float>((size_t)T * S_max * d_pad);
     const int S_big = std::max(P.max_big_nodes, 1);
@@ -736,10 +875,14 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
 
     const int sms = num_sms();
     const int gcap = sms * 32;
-    init_perm_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, -1, perm_a, pos_of, node_of);
+    // byte input laid out for the node-major projection (16-byte aligned,
+    // padded rows)
+    const bool u8_nm_ok =
+        x.dtype == kDtU8 && ((uintptr_t)x.X % 16 == 0) && (x.ld % 16 == 0) && (x.d % 16 == 0);
+    init_perm_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, -1, perm_a, pos_of, node_of, node_pos);
     note_launches(1);
     if (!P.levels.empty()) {
-        init_root_nodes_kernel<<<dim3(P.levels[0].nnodes, T), 256, 0, st>>>(n, dp.nodes, node_of);
+        init_root_nodes_kernel<<<dim3(P.levels[0].nnodes, T), 256, 0, st>>>(n, dp.nodes, node_of, node_pos);
         note_launches(1);
     }
     int32_t* cur = perm_a;
@@ -778,13 +921,20 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         // internal exact byte copy of float rows (decided on the device), or
         // byte input laid out that way
         const bool copy_nm = !learned && x.dtype == kDtF32 && x.Xb != nullptr;
-        const bool u8_nm = !learned && x.dtype == kDtU8 && ((uintptr_t)x.X % 16 == 0) && (x.ld % 16 == 0) &&
-                           (x.d % 16 == 0);
+        const bool u8_nm = !learned && u8_nm_ok;
         const int bgrid = grid_for((int64_t)T * n, 256, sms * 16);
         if (copy_nm || u8_nm) {
             const RowLoader<kDtU8> rb = u8_nm ? RowLoader<kDtU8>{x.X, x.ld, x.d, true}
                                               : RowLoader<kDtU8>{x.Xb, x.ldb, x.d, true};
-            project_bytes_kernel<<<bgrid, 256, 0, st>>>(rb, x.xb_bad, u8_nm, n, T, dirs, S, d_pad, cur, node_of, keys);
+            if (x.d == 128)
+                project_bytes_kernel<true, true><<<bgrid, 256, 0, st>>>(rb, x.xb_bad, u8_nm, n, T, dirs, S, d_pad, cur,
+                                                                        node_pos, keys);
+            else if (((x.d + 15) & ~15) <= 128)
+                project_bytes_kernel<true, false><<<bgrid, 256, 0, st>>>(rb, x.xb_bad, u8_nm, n, T, dirs, S, d_pad,
+                                                                         cur, node_pos, keys);
+            else
+                project_bytes_kernel<false, false><<<bgrid, 256, 0, st>>>(rb, x.xb_bad, u8_nm, n, T, dirs, S, d_pad,
+                                                                          cur, node_pos, keys);
             note_launches(1);
         }
         if (!u8_nm) {
@@ -804,8 +954,19 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
             else project(std::integral_constant<int, kDtF32>{});
             note_launches(1);
         }
-        // leaves of this level keep their positions: start from a copy
-        cudaMemcpyAsync(nxt, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);
+        // which maps by id the scatter keeps: the next level's projection
+        // reads them unless it goes node-major (byte rows), and none follows
+        // the last level
+        int id_mode = 1;
+        if (lvl + 1 >= P.levels.size()) id_mode = 0;
+        else if (lf && lf->Z && (int)lvl + 1 < lf->C) id_mode = 1;
+        else if (u8_nm_ok) id_mode = 0;
+        else if (x.dtype == kDtF32 && x.Xb != nullptr) id_mode = 2;
+        // leaves of this level keep their positions: start from a copy,
+        // unless the level's split nodes cover every position
+        int64_t covered = 0;
+        for (int s = 0; s < S; ++s) covered += P.nodes[L.node_base + s].size;
+        if (covered < n) cudaMemcpyAsync(nxt, cur, sizeof(int32_t) * (size_t)T * n, cudaMemcpyDeviceToDevice, st);
         if (L.nbig < S) {
             constexpr int NT = 512;
             const size_t smem = sizeof(unsigned long long) * (size_t)L.max_small;
@@ -816,8 +977,8 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
                 if (e != cudaSuccess) return e;
                 attr = true;
             }
-            split_small_kernel<NT><<<dim3(S - L.nbig, T), NT, smem, st>>>(n, nodes + L.nbig, keys, cur, nxt, pos_of,
-                                                                         node_of);
+            split_small_kernel<NT><<<dim3(S - L.nbig, T), NT, smem, st>>>(n, nodes + L.nbig, keys, cur, nxt, node_pos,
+                                                                         pos_of, node_of, id_mode, x.xb_bad);
             note_launches(1);
         }
         if (L.nbig > 0) {
@@ -839,7 +1000,7 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
             big_base_kernel<<<(SB * T + 127) / 128, 128, 0, st>>>(SB, T, NC, chunks, cnt);
             note_launches(1);
             big_scatter_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, SB, NC, chunks, nodes, keys, cur, sel, cnt, nxt,
-                                                               pos_of, node_of);
+                                                               node_pos, pos_of, node_of, id_mode, x.xb_bad);
             note_launches(1);
         }
         std::swap(cur, nxt);
