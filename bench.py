@@ -47,7 +47,7 @@ PROPAGATION = {"first_order": 0, "best_first": 1, "pairwise": 2}
 # DRAM bytes (read + write) per point of one launch, from ncu captures of the
 # current kernels on the 400k-point case of the sift1m configuration (leaf:
 # per point and tree; propagation: per point and round).
-TRAFFIC = {("sift1m", "bf16"): {"leaf_knn": (947.662848e6 + 556.315904e6) / (400_000 * 8),
+TRAFFIC = {("sift1m", "bf16"): {"leaf_knn": (948.755968e6 + 560.620288e6) / (400_000 * 8),
                                 "propagate": (237.841920e6 + 67.076864e6) / 400_000}}
 METRIC = "points/sec to build the k-NN graph (recall@k reported on a 10k-point sample)"
 

@@ -108,17 +108,105 @@ __device__ __forceinline__ void gather_quant_body(const Loader& L, int64_t rows,
     }
 }
 
-// Float rows whose byte copy is exact (*xb_bad == 0) are read from the copy.
+// Byte rows to bfloat16 (16-byte aligned rows padded with zeros to
+// multiples of 16 bytes, d <= 256): a group of LPR lanes per row, 16 bytes a
+// lane, two rows in flight per group.  A byte b becomes the float 2^23 + b
+// by a byte permute, 2^23 comes off with a packed subtract, and the pair
+// rounds to bfloat16 exactly (b < 2^8).  The squared norm is the exact
+// integer sum of b^2 (dp4a), below 2^24, so it equals the FP32 sum of any
+// order; every row of bytes is exact when that norm is below 2^23.
+template <int LPR>
+__device__ __forceinline__ void gather_bytes_bf16(const RowLoader<kDtU8>& Lb, int64_t rows,
+                                                  const int32_t* __restrict__ perm, int dq,
+                                                  __nv_bfloat16* __restrict__ out, float* __restrict__ nrm,
+                                                  uint8_t* __restrict__ exact)
+{
+    const int lane = threadIdx.x & 31, q = lane % LPR;
+    const unsigned gmask = LPR == 32 ? 0xFFFFFFFFu : (((1u << LPR) - 1u) << (lane - q));
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / LPR;
+    const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR;
+    const int d16 = (Lb.d + 15) & ~15;
+    const bool has = 16 * q < d16, put = 16 * q < dq;
+    const uint8_t* X = static_cast<const uint8_t*>(Lb.X);
+    const float2 off = make_float2(-8388608.0f, -8388608.0f);
+    auto cvt = [&](uint32_t w, uint32_t& lo, uint32_t& hi) {
+        const float2 a = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u)),
+                                                __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541u))),
+                                    off);
+        const float2 b = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7542u)),
+                                                __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7543u))),
+                                    off);
+        const __nv_bfloat162 ha = __floats2bfloat162_rn(a.x, a.y), hb = __floats2bfloat162_rn(b.x, b.y);
+        lo = *reinterpret_cast<const uint32_t*>(&ha);
+        hi = *reinterpret_cast<const uint32_t*>(&hb);
+    };
+    for (int64_t r0 = grp; r0 < rows; r0 += 2 * ngrp) {
+        const int64_t r1 = r0 + ngrp;
+        const bool two = r1 < rows;
+        const int32_t id0 = perm[r0];
+        const int32_t id1 = two ? perm[r1] : id0;
+        uint4 u[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+        if (has) {
+            u[0] = __ldg(reinterpret_cast<const uint4*>(X + Lb.row_off(id0) + 16 * q));
+            u[1] = __ldg(reinterpret_cast<const uint4*>(X + Lb.row_off(id1) + 16 * q));
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t r = e ? r1 : r0;
+            uint32_t acc = 0u;
+            acc = __dp4a(u[e].x, u[e].x, acc);
+            acc = __dp4a(u[e].y, u[e].y, acc);
+            acc = __dp4a(u[e].z, u[e].z, acc);
+            acc = __dp4a(u[e].w, u[e].w, acc);
+            uint4 o0, o1;
+            cvt(u[e].x, o0.x, o0.y);
+            cvt(u[e].y, o0.z, o0.w);
+            cvt(u[e].z, o1.x, o1.y);
+            cvt(u[e].w, o1.z, o1.w);
+#pragma unroll
+            for (int sh = LPR / 2; sh >= 1; sh >>= 1) acc += __shfl_xor_sync(gmask, acc, sh, LPR);
+            if (e == 0 || two) {
+                if (put) {
+                    uint4* dst = reinterpret_cast<uint4*>(out + r * dq + 16 * q);
+                    dst[0] = o0;
+                    dst[1] = o1;
+                }
+                if (q == 0) {
+                    nrm[r] = (float)acc;
+                    exact[r] = acc < 8388608u ? 1 : 0;
+                }
+            }
+        }
+    }
+}
+
+// Float rows whose byte copy is exact (*xb_bad == 0) are read from the copy;
+// for bfloat16, rows of bytes (the copy, or aligned byte input) of at most
+// 256 entries take the byte conversion above.
 template <int PREC, int kDT>
 __global__ void __launch_bounds__(256) gather_quant_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
                                                            const int* __restrict__ xb_bad, int64_t rows,
                                                            const int32_t* __restrict__ perm, int dq,
                                                            void* __restrict__ out, float* __restrict__ nrm,
-                                                           float* __restrict__ scl, uint8_t* __restrict__ exact)
+                                                           float* __restrict__ scl, uint8_t* __restrict__ exact,
+                                                           bool u8_aligned)
 {
+    auto bytes_bf16 = [&](const RowLoader<kDtU8>& B) {
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
+        if (dq <= 64) gather_bytes_bf16<4>(B, rows, perm, dq, o, nrm, exact);
+        else if (dq <= 128) gather_bytes_bf16<8>(B, rows, perm, dq, o, nrm, exact);
+        else gather_bytes_bf16<16>(B, rows, perm, dq, o, nrm, exact);
+    };
     if constexpr (kDT == kDtF32) {
         if (xb_bad && *xb_bad == 0) {
-            gather_quant_body<PREC>(Lb, rows, perm, dq, out, nrm, scl, exact);
+            if (PREC == 1 && Lb.d <= 256) bytes_bf16(Lb);
+            else gather_quant_body<PREC>(Lb, rows, perm, dq, out, nrm, scl, exact);
+            return;
+        }
+    }
+    if constexpr (kDT == kDtU8) {
+        if (PREC == 1 && u8_aligned && L.d <= 256) {
+            bytes_bf16(L);
             return;
         }
     }
@@ -601,10 +689,15 @@ cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const 
     const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);
     RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
     const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
+    // byte input laid out for 16-byte row loads
+    const bool u8_aligned =
+        x.dtype == kDtU8 && ((uintptr_t)x.X % 16 == 0) && (x.ld % 16 == 0) && (x.d % 16 == 0);
     if (prec == 1)
-        gather_quant_kernel<1, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx);
+        gather_quant_kernel<1, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx,
+                                                             u8_aligned);
     else
-        gather_quant_kernel<2, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx);
+        gather_quant_kernel<2, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx,
+                                                             u8_aligned);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -1,79 +1,143 @@
 // Combination of the T base graphs (Sec. 3.1 of arXiv:1307.7852): every
 // point unites its T adjacency lists and keeps the k nearest.
 //
-// One thread per point.  The T input rows are each ordered by (dist, id),
-// so a T-way merge on the packed 64-bit key (ord(dist) << 32 | id) visits the
-// union in output order; equal keys (the same neighbour found by several
-// trees) advance together, and a neighbour seen again with a different
-// distance is dropped by the id check against the rows already written.
+// A group of GS lanes per point (GS the power of two >= T), lane j walking
+// tree j's row.  The T input rows are each ordered by (dist, id), so a T-way
+// merge on the packed 64-bit key (ord(dist) << 32 | id) visits the union in
+// output order: every step takes the group minimum of the lanes' heads and
+// advances the lanes holding it (the same neighbour found by several trees
+// has equal keys, so its copies go together); a neighbour seen again with
+// a different distance is dropped by the id check against the entries
+// already taken, and p itself is skipped.  A warp's rows (32 / GS points,
+// contiguous for every tree) are staged in shared memory with coalesced
+// loads; output slot s of a point is held by lane s % GS of its group.
 #include "knng_common.cuh"
 #include "knng_internal.h"
 
 namespace knng {
 
-template <int TMAX>
-__global__ void __launch_bounds__(128) merge_kernel(int64_t n, int T, int k,
-                                                    const int32_t* __restrict__ ids_in,
-                                                    const float* __restrict__ d_in,
-                                                    int32_t* __restrict__ ids, float* __restrict__ dists)
+constexpr int kMergeThreads = 128;
+
+template <int GS, int R>
+__global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, int k,
+                                                              const int32_t* __restrict__ ids_in,
+                                                              const float* __restrict__ d_in,
+                                                              int32_t* __restrict__ ids, float* __restrict__ dists)
 {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int h[TMAX];
-    uint64_t cur[TMAX];
-#pragma unroll
-    for (int t = 0; t < TMAX; ++t) {
-        h[t] = 0;
-        cur[t] = kKeyMax;
-        if (t < T) {
-            const int64_t r = ((int64_t)t * n + p) * k;
-            const int32_t id = ids_in[r];
-            if (id >= 0) cur[t] = pack_key(d_in[r], (uint32_t)id);
-        }
-    }
-    int32_t* oi = ids + p * k;
-    float* od = dists + p * k;
-    int cnt = 0;
-    while (cnt < k) {
-        uint64_t best = kKeyMax;
-#pragma unroll
-        for (int t = 0; t < TMAX; ++t) best = cur[t] < best ? cur[t] : best;
-        if (best == kKeyMax) break;
-#pragma unroll
-        for (int t = 0; t < TMAX; ++t) {
-            if (cur[t] == best) {
-                ++h[t];
-                cur[t] = kKeyMax;
-                if (h[t] < k) {
-                    const int64_t r = ((int64_t)t * n + p) * k + h[t];
-                    const int32_t id = ids_in[r];
-                    if (id >= 0) cur[t] = pack_key(d_in[r], (uint32_t)id);
+    constexpr int PPW = 32 / GS;  // points per warp
+    constexpr int NW = kMergeThreads / 32;
+    extern __shared__ unsigned long long mstage[];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int grp = lane / GS, j = lane % GS;
+    const int ks = k | 1;  // odd row stride (in keys): 64-bit accesses of a half warp avoid bank conflicts
+    unsigned long long* wk = mstage + (size_t)wq * 32 * ks;  // [PPW][GS][ks]
+    const unsigned gmask = GS == 32 ? 0xFFFFFFFFu : (((1u << GS) - 1u) << (grp * GS));
+    const int64_t step = (int64_t)gridDim.x * NW * PPW;
+    for (int64_t wbase = ((int64_t)blockIdx.x * NW + wq) * PPW; wbase < n; wbase += step) {
+        const int np = (int)(n - wbase < PPW ? n - wbase : PPW);
+        // stage: for every tree the rows of the warp's points are contiguous;
+        // entry e = pp k + h of them, advanced by 32 without division
+        const int dpp = 32 / k, dh = 32 - (32 / k) * k;
+        for (int t = 0; t < T; ++t) {
+            const int64_t src = ((int64_t)t * n + wbase) * k;
+            int pp = lane / k, h = lane - (lane / k) * k;
+            for (int e = lane; e < np * k; e += 32) {
+                const int32_t id = ids_in[src + e];
+                wk[(pp * GS + t) * ks + h] = id >= 0 ? pack_key(d_in[src + e], (uint32_t)id) : kKeyMax;
+                pp += dpp;
+                h += dh;
+                if (h >= k) {
+                    h -= k;
+                    ++pp;
                 }
             }
         }
-        const int32_t id = (int32_t)(uint32_t)best;
-        if (id == (int32_t)p) continue;
-        bool dup = false;
-        for (int e = 0; e < cnt; ++e) dup |= (oi[e] == id);
-        if (dup) continue;
-        oi[cnt] = id;
-        od[cnt] = unord_key((uint32_t)(best >> 32));
-        ++cnt;
+        __syncwarp();
+        const int64_t p = wbase + grp;
+        const bool live = grp < np;
+        const unsigned long long* row = wk + (grp * GS + j) * ks;
+        int h = 0;
+        // a row ends at its first empty entry (kKeyMax); trees j >= T are empty
+        unsigned long long key = (live && j < T) ? row[0] : kKeyMax;
+        unsigned long long o[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) o[r] = kKeyMax;
+        int cnt = 0;
+        bool done = !live || k == 0;
+        while (__any_sync(KNNG_FULL_MASK, !done)) {
+            unsigned long long best = key;
+#pragma unroll
+            for (int off = GS / 2; off >= 1; off >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(KNNG_FULL_MASK, best, off, GS);
+                best = other < best ? other : best;
+            }
+            if (!done) {  // uniform over the group
+                if (best == kKeyMax) {
+                    done = true;
+                } else {
+                    if (key == best) {
+                        ++h;
+                        key = h < k ? row[h] : kKeyMax;
+                    }
+                    const int32_t id = (int32_t)(uint32_t)best;
+                    bool dup = false;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) dup |= (GS * r + j < cnt) && ((int32_t)(uint32_t)o[r] == id);
+                    dup = __any_sync(gmask, dup) || id == (int32_t)p;
+                    if (!dup) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            if (GS * r + j == cnt) o[r] = best;
+                        ++cnt;
+                        done = cnt == k;
+                    }
+                }
+            }
+        }
+        if (live) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int s2 = GS * r + j;
+                if (s2 < k) {
+                    const bool ok = s2 < cnt;
+                    ids[p * k + s2] = ok ? (int32_t)(uint32_t)o[r] : -1;
+                    dists[p * k + s2] = ok ? unord_key((uint32_t)(o[r] >> 32)) : __int_as_float(0x7f800000);
+                }
+            }
+        }
+        __syncwarp();  // the staged rows are read before the next batch lands
     }
-    for (int e = cnt; e < k; ++e) {
-        oi[e] = -1;
-        od[e] = __int_as_float(0x7f800000);
+}
+
+template <int GS, int R>
+static cudaError_t launch_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in, int32_t* ids,
+                                float* dists, cudaStream_t st)
+{
+    static bool attr = false;  // one per instantiation
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(merge_kernel<GS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((kMergeThreads / 32) * 32 * (kMaxK | 1) * sizeof(unsigned long long)));
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
+    const size_t smem = (size_t)(kMergeThreads / 32) * 32 * (k | 1) * sizeof(unsigned long long);
+    const int64_t per_block = (int64_t)(kMergeThreads / 32) * (32 / GS);
+    const int64_t want = (n + per_block - 1) / per_block;
+    const int grid = (int)(want < (1 << 20) ? want : (1 << 20));
+    merge_kernel<GS, R><<<grid, kMergeThreads, smem, st>>>(n, T, k, ids_in, d_in, ids, dists);
+    return cudaSuccess;
 }
 
 cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
                       int32_t* ids, float* dists, cudaStream_t st)
 {
-    const int grid = (int)((n + 127) / 128);
-    if (T <= 4) merge_kernel<4><<<grid, 128, 0, st>>>(n, T, k, ids_in, d_in, ids, dists);
-    else if (T <= 8) merge_kernel<8><<<grid, 128, 0, st>>>(n, T, k, ids_in, d_in, ids, dists);
-    else if (T <= 16) merge_kernel<16><<<grid, 128, 0, st>>>(n, T, k, ids_in, d_in, ids, dists);
-    else merge_kernel<32><<<grid, 128, 0, st>>>(n, T, k, ids_in, d_in, ids, dists);
+    cudaError_t e;
+    if (T <= 8) e = k <= 32 ? launch_merge<8, 4>(n, T, k, ids_in, d_in, ids, dists, st)
+                            : launch_merge<8, 8>(n, T, k, ids_in, d_in, ids, dists, st);
+    else if (T <= 16) e = launch_merge<16, 4>(n, T, k, ids_in, d_in, ids, dists, st);
+    else e = launch_merge<32, 2>(n, T, k, ids_in, d_in, ids, dists, st);
+    if (e != cudaSuccess) return e;
     note_launches(1);
     return cudaGetLastError();
 }
