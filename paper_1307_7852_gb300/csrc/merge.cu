@@ -63,6 +63,9 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
 #pragma unroll
         for (int r = 0; r < R; ++r) o[r] = kKeyMax;
         int cnt = 0;
+        // ids taken so far, as one bit of a 64-bit filter (the same in every
+        // lane of the group): the full id check runs only on a hit
+        unsigned long long taken = 0ull;
         bool done = !live || k == 0;
         while (__any_sync(KNNG_FULL_MASK, !done)) {
             unsigned long long best = key;
@@ -80,14 +83,18 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
                         key = h < k ? row[h] : kKeyMax;
                     }
                     const int32_t id = (int32_t)(uint32_t)best;
-                    bool dup = false;
+                    const unsigned long long bit = 1ull << (((uint32_t)id * 0x9E3779B1u) >> 26);
+                    bool dup = id == (int32_t)p;
+                    if (!dup && (taken & bit)) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) dup |= (GS * r + j < cnt) && ((int32_t)(uint32_t)o[r] == id);
-                    dup = __any_sync(gmask, dup) || id == (int32_t)p;
+                        for (int r = 0; r < R; ++r) dup |= (GS * r + j < cnt) && ((int32_t)(uint32_t)o[r] == id);
+                        dup = __any_sync(gmask, dup);
+                    }
                     if (!dup) {
 #pragma unroll
                         for (int r = 0; r < R; ++r)
                             if (GS * r + j == cnt) o[r] = best;
+                        taken |= bit;
                         ++cnt;
                         done = cnt == k;
                     }

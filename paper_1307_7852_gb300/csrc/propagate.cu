@@ -204,6 +204,65 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
             }
         }
         auto key = [&](int idx) -> uint64_t { return pack_key(cd[idx], (uint32_t)cid[idx]); };
+        // p's own list full (k distinct ids) and ordered by key: its k-th key
+        // bounds the answer, so only the candidates below it can enter (few,
+        // usually), and the new list is the merge of the two ordered runs.
+        // Each output's rank is its position in its run plus the number of
+        // keys of the other run below it (all keys are distinct).
+        if (k <= 32 && nknown == k) {
+            const uint64_t mk = lane < k ? key(lane) : kKeyMax;
+            const uint64_t prev = __shfl_up_sync(KNNG_FULL_MASK, mk, 1);
+            if (__all_sync(KNNG_FULL_MASK, lane == 0 || lane >= k || prev < mk)) {
+                const uint64_t thr = __shfl_sync(KNNG_FULL_MASK, mk, k - 1);
+                uint64_t* sv = keys + 64;  // the candidates below thr
+                int ns = 0;
+                for (int c0 = nknown; c0 < cnt; c0 += 32) {
+                    const int i = c0 + lane;
+                    const uint64_t kv = i < cnt ? key(i) : kKeyMax;
+                    const bool below = kv < thr;
+                    const uint32_t b = __ballot_sync(KNNG_FULL_MASK, below);
+                    const int at = ns + __popc(b & lanemask_lt());
+                    if (below && at < 32) sv[at] = kv;
+                    ns += __popc(b);
+                }
+                if (ns <= 32) {
+                    __syncwarp();
+                    unsigned long long fl = 0;
+                    const uint64_t x = lane < ns ? sv[lane] : kKeyMax;
+                    int rx = 0, rm = lane;
+                    for (int j = 0; j < ns; ++j) {
+                        const uint64_t y = sv[j];
+                        rx += y < x ? 1 : 0;
+                        rm += y < mk ? 1 : 0;
+                    }
+                    if (lane < ns) {
+                        int lo = 0, hi = k;  // own keys below x
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (key(mid) < x) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        rx += lo;
+                        if (rx < k) {
+                            ids_out[(int64_t)p * k + rx] = (int32_t)(uint32_t)x;
+                            d_out[(int64_t)p * k + rx] = unord_key((uint32_t)(x >> 32));
+                            fl |= 1ull << rx;
+                        }
+                    }
+                    if (lane < k && rm < k) {
+                        ids_out[(int64_t)p * k + rm] = (int32_t)(uint32_t)mk;
+                        d_out[(int64_t)p * k + rm] = unord_key((uint32_t)(mk >> 32));
+                    }
+                    if (flags_out) {
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) fl |= __shfl_xor_sync(KNNG_FULL_MASK, fl, o);
+                        if (lane == 0) flags_out[p] = fl;
+                    }
+                    __syncwarp();
+                    continue;
+                }
+            }
+        }
         const int want = min(k, cnt);
         int nsel = 0;
         uint64_t v[E];
