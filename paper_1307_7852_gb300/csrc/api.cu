@@ -215,18 +215,24 @@ int check_k(knng_handle* h, int32_t k, int32_t g)
 
 // Leaf graphs of all trees.  With ar.base == nullptr only measures the
 // scratch the stage needs.
+// all_exact (nullable): left nonzero only when every leaf list is the exact
+// k best of its leaf (tensor-core path with exact leaves).
 int leaf_stage(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc& x, int T, const int32_t* perm,
-               int k, int prec, int mult, int32_t* ids, float* dists, Arena& ar, cudaStream_t st)
+               int k, int prec, int mult, int32_t* ids, float* dists, Arena& ar, cudaStream_t st,
+               int* all_exact = nullptr)
 {
     cudaError_t e;
     const int kp = std::min(mult * k, 128);
     if (prec == KNNG_PREC_FP32) {
         if (!ar.base) return KNNG_OK;
-        e = run_leaf_knn_f32(x, P, dp, T, perm, k, kp, ids, dists, st);
+        e = all_exact ? cudaMemsetAsync(all_exact, 0, sizeof(int), st) : cudaSuccess;
+        if (e == cudaSuccess) e = run_leaf_knn_f32(x, P, dp, T, perm, k, kp, ids, dists, st);
     } else if (prec == KNNG_PREC_BF16 || prec == KNNG_PREC_FP8E4M3) {
         const auto it = h->tune.find(tc_key(P, x.d, prec));
         const TcTile* tile = it == h->tune.end() ? nullptr : &it->second;
-        e = run_leaf_knn_tc(x, P, dp, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st, tile);
+        e = (all_exact && ar.base) ? cudaMemsetAsync(all_exact, 0x01, sizeof(int), st) : cudaSuccess;
+        if (e == cudaSuccess)
+            e = run_leaf_knn_tc(x, P, dp, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st, tile, all_exact);
     } else {
         return fail(h, KNNG_ERR_INVALID_ARG, "precision %d", prec);
     }
@@ -299,6 +305,10 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         xb_bad = a.take<int>(1);
     }
     unsigned long long* rate_cnt = a.take<unsigned long long>(2);
+    // the merge's tree masks for the first first-order round (T <= 8)
+    const bool tmasks = !(p.r_stop > 0.f) && R > 0 && T <= 8 && p.propagation == KNNG_PROP_FIRST_ORDER;
+    uint8_t* tmask = tmasks ? a.take<uint8_t>(nk) : nullptr;
+    int* all_exact = tmasks ? a.take<int>(1) : nullptr;
     PcaOpt pca;
     pca.on = p.partitioner == KNNG_PART_PCA;
     if (pca.on && x.d > 1024) return fail(h, KNNG_ERR_UNSUPPORTED, "principal directions support d <= 1024");
@@ -339,12 +349,13 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         mark(1);
         const size_t part_end = a.off;
         a.off = fixed;  // the partition scratch is dead: the leaf stage reuses it
-        if ((r = leaf_stage(h, P, dp, x, T, perm, k, p.precision, p.rescore_mult, li, ld_, a, st))) return r;
+        if ((r = leaf_stage(h, P, dp, x, T, perm, k, p.precision, p.rescore_mult, li, ld_, a, st, all_exact)))
+            return r;
         a.off = std::max(part_end, a.off);
         mark(2);
         int32_t* mi = R == 0 ? ids : bi[0];
         float* md = R == 0 ? dists : bd[0];
-        e = run_merge(n, T, k, li, ld_, mi, md, st);
+        e = run_merge(n, T, k, li, ld_, mi, md, st, tmask, all_exact);
         if (e != cudaSuccess) return cuda_fail(h, e, "merge");
         mark(3);
     } else {
@@ -416,7 +427,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         else if (p.propagation == KNNG_PROP_PAIRWISE)
             e = run_propagate_pairwise(x, k, perm, si, sd, sf, oi, od, of, pw, h->dev_err, st);
         else
-            e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st);
+            e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st, nullptr, rd == 0 ? tmask : nullptr);
         if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
         cur ^= 1;
         mark(4 + rd);

@@ -176,12 +176,17 @@ TcKey tc_key(const TreePlan& P, int d, int prec);
 // Candidate tiles for a shape (valid for its shared-memory budget).
 std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec);
 
+// all_exact (nullable): cleared by every leaf whose distances are not all
+// exact (its list is then not the exact k best of the leaf).
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
                             int k, int kp, int prec, int32_t* ids, float* dists, int* err, Arena& ar,
-                            cudaStream_t st, const TcTile* tile = nullptr);
+                            cudaStream_t st, const TcTile* tile = nullptr, int* all_exact = nullptr);
 
+// tmask (nullable, T <= 8): per output entry, the trees whose lists held
+// it, when *all_exact != 0 (every leaf list exact); zeros otherwise.
 cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
-                      int32_t* ids, float* dists, cudaStream_t st);
+                      int32_t* ids, float* dists, cudaStream_t st, uint8_t* tmask = nullptr,
+                      const int* all_exact = nullptr);
 // One more division into the running graph: lists (ia, da) and (ib, db) ->
 // the k best of both; counts[0] += entries not in a, counts[1] += entries.
 cudaError_t run_merge_add(int64_t n, int k, const int32_t* ia, const float* da, const int32_t* ib, const float* db,
@@ -190,9 +195,6 @@ cudaError_t run_merge_add(int64_t n, int k, const int32_t* ia, const float* da, 
 cudaError_t run_propagate_best_first(const XDesc& x, int k, int budget, const int32_t* order, const int32_t* ids_in,
                                      int32_t* ids, float* dists, cudaStream_t st);
 
-// One synchronous propagation round.  flags_in (nullable = every entry new)
-// marks, per point, the list entries that were not in the previous round's
-// list; flags_out (nullable) receives the same for the output lists.
 // Byte copy of float rows (see XDesc::Xb); *bad is set when an entry is not
 // an integer in [0, 255].  *bad must be 0 on entry.
 cudaError_t run_byte_copy(const XDesc& x, uint8_t* Xb, int64_t ldb, int* bad, cudaStream_t st);
@@ -214,9 +216,16 @@ struct PairOffers {
     int* err = nullptr;
 };
 
+// One synchronous propagation round.  flags_in (nullable = every entry new)
+// marks, per point, the list entries that were not in the previous round's
+// list; flags_out (nullable) receives the same for the output lists.
+// tmask_in (nullable): the merge's tree masks of the input lists (exact
+// leaves only); a neighbour's entry that shares a tree with p's entry for
+// that neighbour is skipped.
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
-                          unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers = nullptr);
+                          unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers = nullptr,
+                          const uint8_t* tmask_in = nullptr);
 
 // Scratch of a pairwise round: offers (cap entries), per-target counts and
 // offsets, forward lists.  pairwise_bytes() sizes it.

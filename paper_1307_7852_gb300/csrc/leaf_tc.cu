@@ -16,13 +16,13 @@ namespace knng {
 
 extern template cudaError_t leaf_tc_run<kDtF32>(int, const CUtensorMap&, const XDesc&, const TreePlan&, const DevPlan&,
                                                 int, const int32_t*, int, void*, float*, float*, uint8_t*, int, int,
-                                                const TcGeom&, int32_t*, float*, int*, cudaStream_t);
+                                                const TcGeom&, int32_t*, float*, int*, int*, cudaStream_t);
 extern template cudaError_t leaf_tc_run<kDtF16>(int, const CUtensorMap&, const XDesc&, const TreePlan&, const DevPlan&,
                                                 int, const int32_t*, int, void*, float*, float*, uint8_t*, int, int,
-                                                const TcGeom&, int32_t*, float*, int*, cudaStream_t);
+                                                const TcGeom&, int32_t*, float*, int*, int*, cudaStream_t);
 extern template cudaError_t leaf_tc_run<kDtU8>(int, const CUtensorMap&, const XDesc&, const TreePlan&, const DevPlan&,
                                                int, const int32_t*, int, void*, float*, float*, uint8_t*, int, int,
-                                               const TcGeom&, int32_t*, float*, int*, cudaStream_t);
+                                               const TcGeom&, int32_t*, float*, int*, int*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -97,7 +97,7 @@ std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec)
 
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
                             int k, int kp, int prec, int32_t* ids, float* dists, int* err, Arena& ar,
-                            cudaStream_t st, const TcTile* tile)
+                            cudaStream_t st, const TcTile* tile, int* all_exact)
 {
     const int elem = prec == 1 ? 2 : 1;
     const int slice = 128 / elem;
@@ -125,10 +125,10 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
     if (x.dtype == kDtF16)
-        return leaf_tc_run<kDtF16>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, st);
+        return leaf_tc_run<kDtF16>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
     if (x.dtype == kDtU8)
-        return leaf_tc_run<kDtU8>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, st);
-    return leaf_tc_run<kDtF32>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, st);
+        return leaf_tc_run<kDtU8>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
+    return leaf_tc_run<kDtF32>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
 }
 
 }  // namespace knng

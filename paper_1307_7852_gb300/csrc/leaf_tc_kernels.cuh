@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                                                                 const float* __restrict__ qscl,
                                                                 const uint8_t* __restrict__ qexact, int k, int kp,
                                                                 TcGeom G, int32_t* __restrict__ out_ids,
-                                                                float* __restrict__ out_d, int* err)
+                                                                float* __restrict__ out_d, int* err, int* all_exact)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
     tc::fence_before_sync();
     // the whole leaf is exact: candidate distances are final, no rescoring
     const bool exact_leaf = __syncthreads_and(ex) != 0;
+    if (tid == 0 && all_exact && !exact_leaf) atomicAnd(all_exact, 0);
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
 template <int PREC, int PER, int kDT>
 static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                              const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
-                             const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
+                             const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, cudaStream_t st)
 {
     auto kern = leaf_tc_kernel<PREC, PER, kDT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
@@ -662,7 +663,7 @@ static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreeP
     const int nleaves = (int)P.leaf_off.size() - 1;
     const int RB = (P.max_leaf + 127) / 128;
     kern<<<dim3(nleaves * RB, T), kTcThreads, G.smem, st>>>(map, rl, x.n, perm, dp.leaf_off, nleaves, qn, qs, qx, k, kp,
-                                                            G, ids, dists, err);
+                                                            G, ids, dists, err, all_exact);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -670,12 +671,12 @@ static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreeP
 template <int PREC, int kDT>
 static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                                const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
-                               const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
+                               const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, cudaStream_t st)
 {
     // keys per lane in the row selection: leaves of up to 32 * PER points
-    if (P.max_leaf <= 128) return launch_tc<PREC, 4, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
-    if (P.max_leaf <= 256) return launch_tc<PREC, 8, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
-    return launch_tc<PREC, 16, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    if (P.max_leaf <= 128) return launch_tc<PREC, 4, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
+    if (P.max_leaf <= 256) return launch_tc<PREC, 8, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
+    return launch_tc<PREC, 16, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
 }
 
 // Gather + quantise the leaf-ordered copy, then the leaf kernel, for one
@@ -683,7 +684,7 @@ static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const Tre
 template <int kDT>
 cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                         const int32_t* perm, int dq, void* Xq, float* qn, float* qs, uint8_t* qx, int k, int kp,
-                        const TcGeom& G, int32_t* ids, float* dists, int* err, cudaStream_t st)
+                        const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, cudaStream_t st)
 {
     const int64_t rows = (int64_t)T * x.n;
     const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);
@@ -701,8 +702,8 @@ cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const 
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (prec == 1) return dispatch_tc<1, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
-    return dispatch_tc<2, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, st);
+    if (prec == 1) return dispatch_tc<1, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
+    return dispatch_tc<2, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
 }
 
 }  // namespace knng

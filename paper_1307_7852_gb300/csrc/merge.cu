@@ -11,6 +11,8 @@
 // already taken, and p itself is skipped.  A warp's rows (32 / GS points,
 // contiguous for every tree) are staged in shared memory with coalesced
 // loads; output slot s of a point is held by lane s % GS of its group.
+// With eight lanes a group also records, per output entry, the trees whose
+// rows held it (the lanes that advanced on it).
 #include "knng_common.cuh"
 #include "knng_internal.h"
 
@@ -22,7 +24,9 @@ template <int GS, int R>
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, int k,
                                                               const int32_t* __restrict__ ids_in,
                                                               const float* __restrict__ d_in,
-                                                              int32_t* __restrict__ ids, float* __restrict__ dists)
+                                                              int32_t* __restrict__ ids, float* __restrict__ dists,
+                                                              uint8_t* __restrict__ tmask,
+                                                              const int* __restrict__ all_exact)
 {
     constexpr int PPW = 32 / GS;  // points per warp
     constexpr int NW = kMergeThreads / 32;
@@ -33,6 +37,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
     unsigned long long* wk = mstage + (size_t)wq * 32 * ks;  // [PPW][GS][ks]
     const unsigned gmask = GS == 32 ? 0xFFFFFFFFu : (((1u << GS) - 1u) << (grp * GS));
     const int64_t step = (int64_t)gridDim.x * NW * PPW;
+    // tree masks (GS == 8) only when every leaf list was exact
+    const bool masks = GS == 8 && tmask && all_exact && *all_exact != 0;
     for (int64_t wbase = ((int64_t)blockIdx.x * NW + wq) * PPW; wbase < n; wbase += step) {
         const int np = (int)(n - wbase < PPW ? n - wbase : PPW);
         // stage: for every tree the rows of the warp's points are contiguous;
@@ -60,8 +66,12 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
         // a row ends at its first empty entry (kKeyMax); trees j >= T are empty
         unsigned long long key = (live && j < T) ? row[0] : kKeyMax;
         unsigned long long o[R];
+        uint32_t om[R];  // trees of the held entries
 #pragma unroll
-        for (int r = 0; r < R; ++r) o[r] = kKeyMax;
+        for (int r = 0; r < R; ++r) {
+            o[r] = kKeyMax;
+            om[r] = 0u;
+        }
         int cnt = 0;
         // ids taken so far, as one bit of a 64-bit filter (the same in every
         // lane of the group): the full id check runs only on a hit
@@ -78,7 +88,10 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
                 if (best == kKeyMax) {
                     done = true;
                 } else {
-                    if (key == best) {
+                    const bool hit = key == best;
+                    uint32_t trees = 0u;
+                    if constexpr (GS == 8) trees = (__ballot_sync(gmask, hit) >> (grp * GS)) & 0xFFu;
+                    if (hit) {
                         ++h;
                         key = h < k ? row[h] : kKeyMax;
                     }
@@ -93,7 +106,10 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
                     if (!dup) {
 #pragma unroll
                         for (int r = 0; r < R; ++r)
-                            if (GS * r + j == cnt) o[r] = best;
+                            if (GS * r + j == cnt) {
+                                o[r] = best;
+                                om[r] = trees;
+                            }
                         taken |= bit;
                         ++cnt;
                         done = cnt == k;
@@ -109,6 +125,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
                     const bool ok = s2 < cnt;
                     ids[p * k + s2] = ok ? (int32_t)(uint32_t)o[r] : -1;
                     dists[p * k + s2] = ok ? unord_key((uint32_t)(o[r] >> 32)) : __int_as_float(0x7f800000);
+                    if (GS == 8 && tmask) tmask[p * k + s2] = (ok && masks) ? (uint8_t)om[r] : (uint8_t)0;
                 }
             }
         }
@@ -118,7 +135,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
 
 template <int GS, int R>
 static cudaError_t launch_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in, int32_t* ids,
-                                float* dists, cudaStream_t st)
+                                float* dists, uint8_t* tmask, const int* all_exact, cudaStream_t st)
 {
     static bool attr = false;  // one per instantiation
     if (!attr) {
@@ -132,18 +149,18 @@ static cudaError_t launch_merge(int64_t n, int T, int k, const int32_t* ids_in, 
     const int64_t per_block = (int64_t)(kMergeThreads / 32) * (32 / GS);
     const int64_t want = (n + per_block - 1) / per_block;
     const int grid = (int)(want < (1 << 20) ? want : (1 << 20));
-    merge_kernel<GS, R><<<grid, kMergeThreads, smem, st>>>(n, T, k, ids_in, d_in, ids, dists);
+    merge_kernel<GS, R><<<grid, kMergeThreads, smem, st>>>(n, T, k, ids_in, d_in, ids, dists, tmask, all_exact);
     return cudaSuccess;
 }
 
 cudaError_t run_merge(int64_t n, int T, int k, const int32_t* ids_in, const float* d_in,
-                      int32_t* ids, float* dists, cudaStream_t st)
+                      int32_t* ids, float* dists, cudaStream_t st, uint8_t* tmask, const int* all_exact)
 {
     cudaError_t e;
-    if (T <= 8) e = k <= 32 ? launch_merge<8, 4>(n, T, k, ids_in, d_in, ids, dists, st)
-                            : launch_merge<8, 8>(n, T, k, ids_in, d_in, ids, dists, st);
-    else if (T <= 16) e = launch_merge<16, 4>(n, T, k, ids_in, d_in, ids, dists, st);
-    else e = launch_merge<32, 2>(n, T, k, ids_in, d_in, ids, dists, st);
+    if (T <= 8) e = k <= 32 ? launch_merge<8, 4>(n, T, k, ids_in, d_in, ids, dists, tmask, all_exact, st)
+                            : launch_merge<8, 8>(n, T, k, ids_in, d_in, ids, dists, tmask, all_exact, st);
+    else if (T <= 16) e = launch_merge<16, 4>(n, T, k, ids_in, d_in, ids, dists, nullptr, nullptr, st);
+    else e = launch_merge<32, 2>(n, T, k, ids_in, d_in, ids, dists, nullptr, nullptr, st);
     if (e != cudaSuccess) return e;
     note_launches(1);
     return cudaGetLastError();

@@ -13,6 +13,12 @@
 //    already in p's previous list and c already in q's previous list.  Then c
 //    was a candidate of p in the previous round, so either c is in p's list
 //    or k listed points beat it, and it cannot enter the new list.
+//  * Skipping pairs that shared a leaf (exact, first round after the merge):
+//    when every leaf list was the exact k best of its leaf, the merge marks
+//    each entry with the trees whose lists held it.  If p's entry q and q's
+//    entry c share a tree t, then p, q and c were in one leaf of tree t, so c
+//    is in p's tree-t list or k points of that leaf beat it; either way c is
+//    in p's merged list or cannot enter the new one, and is skipped.
 //  * Scoring: 16 candidates at a time by warp_canon_dist16 (coalesced 16-byte
 //    row loads, 16 rows in flight per warp, bit-identical canonical FP32);
 //    float rows holding only bytes are scored on their exact byte copy in
@@ -47,11 +53,12 @@ static PropLayout prop_layout(int k)
     int lg = 0;
     while ((1 << lg) < H) ++lg;
     L.hshift = 32 - lg;
-    // tab[H] | cid[cap] | cd[cap] | hist[256] | sel[64] | own[64] | own_fl[64] (u64) | keys[192] (u64)
+    // tab[H] | cid[cap] | cd[cap] | hist[256] | sel[64] | own[64] | own_fl[64] (u64) | keys[192] (u64) |
+    // own_tm[64]
     L.cap = (L.cap + 1) & ~1;  // keeps own_fl 8-byte aligned
     L.per_warp = sizeof(int) * (size_t)H + (sizeof(int) + sizeof(float)) * (size_t)L.cap +
                  sizeof(uint32_t) * 256 + sizeof(int) * 64 + sizeof(int) * 64 + sizeof(unsigned long long) * 64 +
-                 sizeof(unsigned long long) * 192;
+                 sizeof(unsigned long long) * 192 + sizeof(int) * 64;
     L.per_warp = (L.per_warp + 15) & ~(size_t)15;
     return L;
 }
@@ -62,7 +69,8 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                                  int64_t lane_ld, PairOffers po, int64_t n, int k,
                                  const int32_t* __restrict__ order,
                                  const int32_t* __restrict__ ids_in, const float* __restrict__ d_in,
-                                 const unsigned long long* __restrict__ flags_in, int32_t* __restrict__ ids_out,
+                                 const unsigned long long* __restrict__ flags_in,
+                                 const uint8_t* __restrict__ tm_in, int32_t* __restrict__ ids_out,
                                  float* __restrict__ d_out, unsigned long long* __restrict__ flags_out, int H,
                                  int hshift, int cap, int per_warp_bytes)
 {
@@ -77,6 +85,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
     int* own = sel + 64;
     unsigned long long* own_fl = reinterpret_cast<unsigned long long*>(own + 64);
     uint64_t* keys = reinterpret_cast<uint64_t*>(own_fl + 64);
+    int* own_tm = reinterpret_cast<int*>(keys + 192);
     const uint32_t hmask = (uint32_t)H - 1;
     const int kk = k * k;
     // float rows with an exact byte copy: score on the copy (same values)
@@ -120,6 +129,9 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                 const int32_t q = own[e];
                 own_fl[e] = q >= 0 ? flags_in[q] : 0ull;
             }
+        // trees whose (exact) leaf lists held p's entries
+        if (tm_in)
+            for (int e = lane; e < k; e += 32) own_tm[e] = tm_in[(int64_t)p * k + e];
         __syncwarp();
         // the neighbours' lists, lanes over (neighbour e, slot f) with
         // i = e*k + f = lane + 32*step, advanced without division
@@ -136,7 +148,14 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                     if (q >= 0 && q != p) {
                         const bool qnew = (pf >> e) & 1ull;
                         const bool cnew = flags_in ? ((own_fl[e] >> f) & 1ull) : true;
-                        if (qnew || cnew) o[gi] = ids_in[(int64_t)q * k + f];
+                        if (qnew || cnew) {
+                            // c of q is useless when p, q and c shared an
+                            // exact leaf: c then is in p's merged list or
+                            // k listed points beat it
+                            int32_t c = ids_in[(int64_t)q * k + f];
+                            if (tm_in && (own_tm[e] & (int)tm_in[(int64_t)q * k + f])) c = -1;
+                            o[gi] = c;
+                        }
                     }
                 }
                 e += de;
@@ -319,7 +338,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
 template <int E, int kDT>
 static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                                const unsigned long long* fin, int32_t* ids, float* dists, unsigned long long* fout,
-                               const PairOffers& po, cudaStream_t st)
+                               const PairOffers& po, const uint8_t* tm, cudaStream_t st)
 {
     const PropLayout PL = prop_layout(k);
     int warps = (int)((200 * 1024) / PL.per_warp);
@@ -350,8 +369,8 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
             lane_ld = x.ld;
         }
     }
-    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, lane_X, lane_ld, po, x.n, k, order, ids_in, d_in, fin, ids, dists, fout, PL.H,
-                                                PL.hshift, PL.cap, (int)PL.per_warp);
+    kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, lane_X, lane_ld, po, x.n, k, order, ids_in, d_in, fin,
+                                                tm, ids, dists, fout, PL.H, PL.hshift, PL.cap, (int)PL.per_warp);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -359,22 +378,24 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
 template <int kDT>
 static cudaError_t prop_dispatch(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
                                  const float* d_in, const unsigned long long* fin, int32_t* ids, float* dists,
-                                 unsigned long long* fout, const PairOffers& po, cudaStream_t st)
+                                 unsigned long long* fout, const PairOffers& po, const uint8_t* tm,
+                                 cudaStream_t st)
 {
-    if (k <= 32) return launch_prop<1, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, st);
-    return launch_prop<2, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, st);
+    if (k <= 32) return launch_prop<1, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, tm, st);
+    return launch_prop<2, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, tm, st);
 }
 
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
-                          unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers)
+                          unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers,
+                          const uint8_t* tmask_in)
 {
     const PairOffers po = offers ? *offers : PairOffers{};
     if (x.dtype == kDtF16)
-        return prop_dispatch<kDtF16>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, st);
+        return prop_dispatch<kDtF16>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st);
     if (x.dtype == kDtU8)
-        return prop_dispatch<kDtU8>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, st);
-    return prop_dispatch<kDtF32>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, st);
+        return prop_dispatch<kDtU8>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st);
+    return prop_dispatch<kDtF32>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st);
 }
 
 }  // namespace knng
