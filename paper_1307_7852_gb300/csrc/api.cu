@@ -344,7 +344,7 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
     }
     int cur = 0;  // bi[cur] / bd[cur]: the merged graph when R > 0
     if (!adaptive) {
-        e = run_partition(xpart ? *xpart : x, P, dp, T, p.seed, perm, a, st, lf, 0, &pca);
+        e = run_partition(xpart ? *xpart : x, P, dp, T, p.seed, perm, a, st, lf, 0, &pca, h->dev_err);
         if (e != cudaSuccess) return cuda_fail(h, e, "partition");
         mark(1);
         const size_t part_end = a.off;
@@ -369,7 +369,8 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         for (int t0 = 0; t0 < T && !stop; t0 += kChunk) {
             const int tc = std::min(kChunk, T - t0);
             const size_t base = a.off;
-            e = run_partition(xpart ? *xpart : x, P, dp, tc, p.seed, perm + (size_t)t0 * n, a, st, lf, t0, &pca);
+            e = run_partition(xpart ? *xpart : x, P, dp, tc, p.seed, perm + (size_t)t0 * n, a, st, lf, t0, &pca,
+                              h->dev_err);
             if (e != cudaSuccess) return cuda_fail(h, e, "partition");
             const size_t part_end = a.off;
             a.off = base;
@@ -548,7 +549,7 @@ int knng_partition(knng_handle* h, const void* X, int32_t dtype, int64_t n, int3
     if ((r = ensure_ws(h, m.off, st))) return r;
     Arena a;
     a.base = h->ws;
-    cudaError_t e = run_partition(x, h->plan, h->dplan, T, seed, perm, a, st);
+    cudaError_t e = run_partition(x, h->plan, h->dplan, T, seed, perm, a, st, nullptr, 0, nullptr, h->dev_err);
     if (e != cudaSuccess) return cuda_fail(h, e, "partition");
     return KNNG_OK;
 }
@@ -583,7 +584,7 @@ int knng_partition_pca(knng_handle* h, const void* X, int32_t dtype, int64_t n, 
     if ((r = ensure_ws(h, m.off, st))) return r;
     Arena a;
     a.base = h->ws;
-    const cudaError_t e = run_partition(x, h->plan, h->dplan, T, seed, perm, a, st, nullptr, 0, &pca);
+    const cudaError_t e = run_partition(x, h->plan, h->dplan, T, seed, perm, a, st, nullptr, 0, &pca, h->dev_err);
     if (e != cudaSuccess) return cuda_fail(h, e, "partition");
     return KNNG_OK;
 }
@@ -1065,7 +1066,7 @@ int knng_autotune(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32
     int32_t* perm = a.take<int32_t>((size_t)T * n);
     int32_t* li = a.take<int32_t>((size_t)T * nk);
     float* ldd = a.take<float>((size_t)T * nk);
-    cudaError_t e = run_partition(x, h->plan, h->dplan, T, p->seed, perm, a, st);
+    cudaError_t e = run_partition(x, h->plan, h->dplan, T, p->seed, perm, a, st, nullptr, 0, nullptr, h->dev_err);
     if (e != cudaSuccess) return cuda_fail(h, e, "partition");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

@@ -149,7 +149,8 @@ cudaError_t run_pca_dirs(const XDesc& x, int T, int S, const SplitNode* nodes, c
 // Trees t0 .. t0 + T - 1 (perm_out[T][n]).
 cudaError_t run_partition(const XDesc& x, const TreePlan& plan, const DevPlan& dp, int T,
                           uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st,
-                          const LearnedFeat* lf = nullptr, int t0 = 0, const PcaOpt* pca = nullptr);
+                          const LearnedFeat* lf = nullptr, int t0 = 0, const PcaOpt* pca = nullptr,
+                          int* err = nullptr);
 
 cudaError_t run_leaf_knn_f32(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                              const int32_t* perm, int k, int kp, int32_t* ids, float* dists,

@@ -16,12 +16,16 @@
 //   4. scatter    -- stable partition of each node into its two children.
 // Stability makes every node's segment ascend by id, so the leaves come out
 // in canonical order without a final sort.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include <type_traits>
 
 #include "knng_common.cuh"
 #include "knng_internal.h"
+#include "tc_ptx.cuh"
 
 namespace knng {
 
@@ -150,15 +154,16 @@ __global__ void init_perm_kernel(int64_t n, int T, int first_node, int32_t* perm
 // Points of the root node s of level 0 start in node s (other points are in
 // roots that are already leaves and keep node -1).  At level 0 positions are
 // ids, so the map by id and the map by position start equal.
+// Block (x, s, t): slice x of root s in tree t.
 __global__ void init_root_nodes_kernel(int64_t n, const SplitNode* __restrict__ nodes, int32_t* node_of,
                                        int32_t* node_pos)
 {
-    const SplitNode nd = nodes[blockIdx.x];
-    int32_t* row = node_of + (int64_t)blockIdx.y * n;
-    int32_t* prow = node_pos + (int64_t)blockIdx.y * n;
-    for (int e = threadIdx.x; e < nd.size; e += blockDim.x) {
-        row[nd.off + e] = (int32_t)blockIdx.x;
-        prow[nd.off + e] = (int32_t)blockIdx.x;
+    const SplitNode nd = nodes[blockIdx.y];
+    int32_t* row = node_of + (int64_t)blockIdx.z * n;
+    int32_t* prow = node_pos + (int64_t)blockIdx.z * n;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nd.size; e += gridDim.x * blockDim.x) {
+        row[nd.off + e] = (int32_t)blockIdx.y;
+        prow[nd.off + e] = (int32_t)blockIdx.y;
     }
 }
 
@@ -515,6 +520,91 @@ __global__ void __launch_bounds__(256, 4) project_bytes_kernel(RowLoader<kDtU8> 
     }
 }
 
+// The same projection with the rows fetched by the tensor memory
+// accelerator (rows of at most 128 bytes): per warp, one lane gathers the
+// batch's 32 rows, four per gather4 copy, as 144-byte rows (bytes past the
+// tensor's rows read as zeros) into 128-byte aligned groups of four, and the
+// copies complete on the warp's mbarrier.  The waits are bounded: a warp
+// that gives up sets the error word, waits once more for its copies and
+// leaves.
+constexpr int kTmaRow = 144;    // bytes per gathered row
+constexpr int kTmaGroup = 640;  // bytes per group of four rows (128-byte aligned)
+constexpr long long kProjWait = 2000000000LL;  // ~1 s at GB300 clocks
+template <bool kFull>
+__global__ void __launch_bounds__(256, 4) project_bytes_tma_kernel(const __grid_constant__ CUtensorMap tmap, int d,
+                                                                   const int* __restrict__ xb_bad, bool bytes_given,
+                                                                   int64_t n, int T, const float* __restrict__ dirs,
+                                                                   int S, int d_pad, const int32_t* __restrict__ cur,
+                                                                   const int32_t* __restrict__ node_pos,
+                                                                   uint32_t* __restrict__ keys, int* err)
+{
+    __shared__ __align__(128) unsigned char srow[8][8 * kTmaGroup];
+    __shared__ int sid[8][32];
+    __shared__ __align__(8) uint64_t bar[8];
+    if (!bytes_given && (!xb_bad || *xb_bad != 0)) return;
+    const int nq = (d + 15) >> 4;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    unsigned char* buf = srow[wq];
+    if (lane == 0) {
+        tc::mbar_init(&bar[wq], 1);
+        tc::fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t phase = 0;
+    const int64_t total = (int64_t)T * n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int t = (int)(g / n);
+    int64_t i = g - (int64_t)t * n;  // position within tree t (g = t n + i)
+    for (; g - lane < total; g += stride) {  // whole warps iterate together
+        const bool valid = g < total;
+        const int tt = t;
+        i += stride;
+        while (i >= n && t < T) {
+            i -= n;
+            ++t;
+        }
+        const int32_t id = valid ? cur[g] : 0;
+        const int sn = valid ? node_pos[g] : -1;  // -1: a leaf of an earlier level
+        sid[wq][lane] = sn >= 0 ? id : 0;          // any row for a position without work
+        // the previous batch's rows are read (generic proxy) before the
+        // copies (async proxy) overwrite them
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            tc::mbar_arrive_expect_tx(&bar[wq], 32 * kTmaRow);
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                tc::tma_gather4_2d(buf + r * kTmaGroup, &tmap, &bar[wq], 0, sid[wq][4 * r], sid[wq][4 * r + 1],
+                                   sid[wq][4 * r + 2], sid[wq][4 * r + 3]);
+        }
+        const bool ok = __all_sync(KNNG_FULL_MASK, tc::mbar_wait(&bar[wq], phase, kProjWait));
+        if (!ok) {
+            if (lane == 0) {
+                if (err) atomicExch(err, 1);
+                tc::mbar_wait(&bar[wq], phase, kProjWait);
+            }
+            __syncwarp();
+            return;
+        }
+        phase ^= 1u;
+        if (sn >= 0) {
+            uint32_t w[32];
+            const uint4* rowp = reinterpret_cast<const uint4*>(buf + (lane >> 2) * kTmaGroup + (lane & 3) * kTmaRow);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const uint4 u = rowp[c];
+                w[4 * c + 0] = u.x;
+                w[4 * c + 1] = u.y;
+                w[4 * c + 2] = u.z;
+                w[4 * c + 3] = u.w;
+            }
+            const float* a = dirs + ((int64_t)tt * S + sn) * d_pad;
+            keys[g] = ord_key(ProjTree<0, 1, kFull>::eval(w, a, 4 * nq, d));
+        }
+    }
+}
+
 // ---- block radix select (one block, keys in shared memory) ---------------
 template <int NT>
 __device__ unsigned long long block_select(const unsigned long long* k64, int m, int want,
@@ -786,26 +876,34 @@ __global__ void __launch_bounds__(NT) big_count_kernel(int64_t n, int S, int nch
     if (threadIdx.x == 0) cnt[(int64_t)t * nchunks + blockIdx.x] = total;
 }
 
-// One thread per (node, tree): exclusive scan of the node's chunk counts
-// (in place: counts in, left-destination offsets out).  A node's chunks are
-// contiguous in the level's chunk list; the first is found by bisection.
-__global__ void big_base_kernel(int S, int T, int nchunks, const Chunk* __restrict__ chunks,
-                                int32_t* cnt_to_base)
+// One block per (node, tree): exclusive scan of the node's chunk counts
+// (in place: counts in, left-destination offsets out), NT chunks at a time.
+// A node's chunks are contiguous in the level's chunk list; its first and
+// its end are found by bisection.
+template <int NT>
+__global__ void __launch_bounds__(NT) big_base_kernel(int S, int nchunks, const Chunk* __restrict__ chunks,
+                                                      int32_t* cnt_to_base)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= S * T) return;
-    const int s = e % S, t = e / S;
-    int lo = 0, hi = nchunks;
-    while (lo < hi) {
-        const int mid = (lo + hi) / 2;
-        if (chunks[mid].node < s) lo = mid + 1; else hi = mid;
-    }
-    int run = 0;
+    __shared__ int sh[33];
+    const int s = blockIdx.x, t = blockIdx.y;
+    auto first_of = [&](int node) {
+        int lo = 0, hi = nchunks;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (chunks[mid].node < node) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+    const int c_beg = first_of(s), c_end = first_of(s + 1);
     int32_t* row = cnt_to_base + (int64_t)t * nchunks;
-    for (int c = lo; c < nchunks && chunks[c].node == s; ++c) {
-        const int v = row[c];
-        row[c] = run;
-        run += v;
+    int run = 0;
+    for (int c0 = c_beg; c0 < c_end; c0 += NT) {
+        const int c = c0 + threadIdx.x;
+        const int v = c < c_end ? row[c] : 0;
+        int total;
+        const int pre = block_excl_scan<NT>(v, sh, &total);
+        if (c < c_end) row[c] = run + pre;
+        run += total;
     }
 }
 
@@ -839,6 +937,32 @@ __global__ void __launch_bounds__(NT) big_scatter_kernel(int64_t n, int S, int n
 // ---------------------------------------------------------------------------
 // Host driver
 // ---------------------------------------------------------------------------
+// Tensor map of byte rows for the gather4 projection: n rows of ld bytes,
+// boxes of 144 bytes x one row.  False when the driver entry point or the
+// encoding is unavailable (the projection then loads the rows itself).
+static bool rows_tensor_map(CUtensorMap* map, const void* base, int64_t ld, int64_t n)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    if (!fn || (uintptr_t)base % 16 != 0 || ld % 16 != 0 || n >= ((int64_t)1 << 31)) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)ld, (cuuint64_t)n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)ld};
+    const cuuint32_t box[2] = {(cuuint32_t)kTmaRow, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static inline int grid_for(int64_t work, int per_block, int cap)
 {
     int64_t b = (work + per_block - 1) / per_block;
@@ -849,7 +973,7 @@ static inline int grid_for(int64_t work, int per_block, int cap)
 
 cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                           uint64_t seed, int32_t* perm_out, Arena& ar, cudaStream_t st, const LearnedFeat* lf,
-                          int t0, const PcaOpt* pca)
+                          int t0, const PcaOpt* pca, int* err)
 {
     const int64_t n = x.n;
     const int d_pad = (x.d + 3) & ~3;
@@ -879,10 +1003,22 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
     // padded rows)
     const bool u8_nm_ok =
         x.dtype == kDtU8 && ((uintptr_t)x.X % 16 == 0) && (x.ld % 16 == 0) && (x.d % 16 == 0);
+    // rows of at most 128 bytes for the node-major projection: gathered by
+    // the tensor memory accelerator when their tensor map encodes
+    CUtensorMap rows_map;
+    bool tma_rows = false;
+    if (((x.d + 15) & ~15) <= 128) {
+        if (u8_nm_ok) tma_rows = rows_tensor_map(&rows_map, x.X, x.ld, n);
+        else if (x.dtype == kDtF32 && x.Xb) tma_rows = rows_tensor_map(&rows_map, x.Xb, x.ldb, n);
+    }
     init_perm_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, -1, perm_a, pos_of, node_of, node_pos);
     note_launches(1);
     if (!P.levels.empty()) {
-        init_root_nodes_kernel<<<dim3(P.levels[0].nnodes, T), 256, 0, st>>>(n, dp.nodes, node_of, node_pos);
+        // slices of the roots, about 8 blocks per SM over all roots and trees
+        const int64_t roots = (int64_t)P.levels[0].nnodes * T;
+        const int slices = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8 / std::max<int64_t>(roots, 1),
+                                                                       (n + 255) / 256));
+        init_root_nodes_kernel<<<dim3(slices, P.levels[0].nnodes, T), 256, 0, st>>>(n, dp.nodes, node_of, node_pos);
         note_launches(1);
     }
     int32_t* cur = perm_a;
@@ -926,7 +1062,13 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
         if (copy_nm || u8_nm) {
             const RowLoader<kDtU8> rb = u8_nm ? RowLoader<kDtU8>{x.X, x.ld, x.d, true}
                                               : RowLoader<kDtU8>{x.Xb, x.ldb, x.d, true};
-            if (x.d == 128)
+            if (tma_rows && x.d == 128)
+                project_bytes_tma_kernel<true><<<bgrid, 256, 0, st>>>(rows_map, x.d, x.xb_bad, u8_nm, n, T, dirs, S,
+                                                                      d_pad, cur, node_pos, keys, err);
+            else if (tma_rows)
+                project_bytes_tma_kernel<false><<<bgrid, 256, 0, st>>>(rows_map, x.d, x.xb_bad, u8_nm, n, T, dirs, S,
+                                                                       d_pad, cur, node_pos, keys, err);
+            else if (x.d == 128)
                 project_bytes_kernel<true, true><<<bgrid, 256, 0, st>>>(rb, x.xb_bad, u8_nm, n, T, dirs, S, d_pad, cur,
                                                                         node_pos, keys);
             else if (((x.d + 15) & ~15) <= 128)
@@ -997,7 +1139,7 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
             }
             big_count_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, SB, NC, chunks, keys, cur, sel, cnt);
             note_launches(1);
-            big_base_kernel<<<(SB * T + 127) / 128, 128, 0, st>>>(SB, T, NC, chunks, cnt);
+            big_base_kernel<256><<<dim3(SB, T), 256, 0, st>>>(SB, NC, chunks, cnt);
             note_launches(1);
             big_scatter_kernel<NT><<<dim3(NC, T), NT, 0, st>>>(n, SB, NC, chunks, nodes, keys, cur, sel, cnt, nxt,
                                                                node_pos, pos_of, node_of, id_mode, x.xb_bad);
