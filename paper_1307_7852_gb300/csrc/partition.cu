@@ -589,11 +589,18 @@ __global__ void __launch_bounds__(256, 4) project_bytes_tma_kernel(const __grid_
         }
         phase ^= 1u;
         if (sn >= 0) {
+            // the rows of two groups share their banks (groups are 128-byte
+            // aligned): lanes of odd groups read their 16-byte words in the
+            // order c ^ 4, so the eight lanes of a phase hit 32 distinct banks
             uint32_t w[32];
             const uint4* rowp = reinterpret_cast<const uint4*>(buf + (lane >> 2) * kTmaGroup + (lane & 3) * kTmaRow);
+            const bool odd = (lane & 4) != 0;
+            uint4 v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] = rowp[odd ? (c ^ 4) : c];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const uint4 u = rowp[c];
+                const uint4 u = odd ? v[c ^ 4] : v[c];
                 w[4 * c + 0] = u.x;
                 w[4 * c + 1] = u.y;
                 w[4 * c + 2] = u.z;
