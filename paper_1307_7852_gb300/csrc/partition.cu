@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(NT) big_scatter_kernel(int64_t n, int S, int n
 // Host driver
 // ---------------------------------------------------------------------------
 // Tensor map of byte rows for the gather4 projection: n rows of ld bytes,
-// boxes of 144 bytes x one row.  False when the driver entry point or the
+// boxes of 144 bytes x one row.  False when the CUDA driver's encoder or the
 // encoding is unavailable (the projection then loads the rows itself).
 static bool rows_tensor_map(CUtensorMap* map, const void* base, int64_t ld, int64_t n)
 {
