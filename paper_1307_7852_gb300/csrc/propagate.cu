@@ -63,7 +63,9 @@ static PropLayout prop_layout(int k)
     return L;
 }
 
-template <int E, int kDT>
+// kMasks: the first round after the merge, with the merge's tree masks
+// (a separate instantiation, so the later rounds carry none of its code).
+template <int E, int kDT, bool kMasks>
 __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
                                  const int* __restrict__ xb_bad, const uint8_t* __restrict__ lane_X,
                                  int64_t lane_ld, PairOffers po, int64_t n, int k,
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                 own_fl[e] = q >= 0 ? flags_in[q] : 0ull;
             }
         // trees whose (exact) leaf lists held p's entries
-        if (tm_in)
+        if (kMasks)
             for (int e = lane; e < k; e += 32) own_tm[e] = tm_in[(int64_t)p * k + e];
         __syncwarp();
         // the neighbours' lists, lanes over (neighbour e, slot f) with
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                             // exact leaf: c then is in p's merged list or
                             // k listed points beat it
                             int32_t c = ids_in[(int64_t)q * k + f];
-                            if (tm_in && (own_tm[e] & (int)tm_in[(int64_t)q * k + f])) c = -1;
+                            if (kMasks && (own_tm[e] & (int)tm_in[(int64_t)q * k + f])) c = -1;
                             o[gi] = c;
                         }
                     }
@@ -345,7 +347,7 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     if (warps > 8) warps = 8;
     if (warps < 1) return cudaErrorInvalidConfiguration;
     const size_t smem = PL.per_warp * warps;
-    auto kern = propagate_kernel<E, kDT>;
+    auto kern = tm ? propagate_kernel<E, kDT, true> : propagate_kernel<E, kDT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
