@@ -63,9 +63,11 @@ static PropLayout prop_layout(int k)
     return L;
 }
 
-// kMasks: the first round after the merge, with the merge's tree masks
-// (a separate instantiation, so the later rounds carry none of its code).
-template <int E, int kDT, bool kMasks>
+// kMode: 1 = the first round after the merge, with the merge's tree masks
+// and no flags; 2 = a later first-order round, with flags; 0 = any other
+// (flags optional, pairwise offers possible).  Separate instantiations, so
+// no round carries the code of the others.
+template <int E, int kDT, int kMode>
 __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(RowLoader<kDT> L, RowLoader<kDtU8> Lb,
                                  const int* __restrict__ xb_bad, const uint8_t* __restrict__ lane_X,
                                  int64_t lane_ld, PairOffers po, int64_t n, int k,
@@ -101,7 +103,8 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         for (int s = lane * 4; s < H; s += 128) *reinterpret_cast<int4*>(tab + s) = make_int4(-1, -1, -1, -1);
         __syncwarp();
         if (lane == 0) hash_insert(tab, (uint32_t)hshift, hmask, p);
-        const unsigned long long pf = flags_in ? flags_in[p] : ~0ull;
+        const bool use_flags = kMode == 2 || (kMode == 0 && flags_in != nullptr);
+        const unsigned long long pf = use_flags ? flags_in[p] : ~0ull;
         __syncwarp();
         // p's own list: ids keep their distances
         int cnt = 0;
@@ -126,13 +129,13 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         }
         const int nknown = cnt;
         // flags of the neighbours' lists (entries of a list that are new)
-        if (flags_in)
+        if (use_flags)
             for (int e = lane; e < k; e += 32) {
                 const int32_t q = own[e];
                 own_fl[e] = q >= 0 ? flags_in[q] : 0ull;
             }
         // trees whose (exact) leaf lists held p's entries
-        if (kMasks)
+        if (kMode == 1)
             for (int e = lane; e < k; e += 32) own_tm[e] = tm_in[(int64_t)p * k + e];
         __syncwarp();
         // the neighbours' lists, lanes over (neighbour e, slot f) with
@@ -149,13 +152,13 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                     const int32_t q = own[e];
                     if (q >= 0 && q != p) {
                         const bool qnew = (pf >> e) & 1ull;
-                        const bool cnew = flags_in ? ((own_fl[e] >> f) & 1ull) : true;
+                        const bool cnew = use_flags ? ((own_fl[e] >> f) & 1ull) : true;
                         if (qnew || cnew) {
                             // c of q is useless when p, q and c shared an
                             // exact leaf: c then is in p's merged list or
                             // k listed points beat it
                             int32_t c = ids_in[(int64_t)q * k + f];
-                            if (kMasks && (own_tm[e] & (int)tm_in[(int64_t)q * k + f])) c = -1;
+                            if (kMode == 1 && (own_tm[e] & (int)tm_in[(int64_t)q * k + f])) c = -1;
                             o[gi] = c;
                         }
                     }
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
             }
         }
         __syncwarp();
-        if (po.tgt) {
+        if (kMode == 0 && po.tgt) {
             // pairwise updating: offer p to every candidate c whose input
             // list it would enter, i.e. (D, p) below c's k-th (dist, id)
             for (int i0 = 0; i0 < cnt; i0 += 32) {
@@ -347,7 +350,13 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     if (warps > 8) warps = 8;
     if (warps < 1) return cudaErrorInvalidConfiguration;
     const size_t smem = PL.per_warp * warps;
-    auto kern = tm ? propagate_kernel<E, kDT, true> : propagate_kernel<E, kDT, false>;
+    // the build's first round (masks, no flags) / a later first-order round
+    // (flags) / anything else
+    // (flags) / anything else; lists of more than 32 take the general one
+    auto kern = E > 1                       ? propagate_kernel<E, kDT, 0>
+                : (tm && !fin && !po.tgt)  ? propagate_kernel<E, kDT, (E > 1 ? 0 : 1)>
+                : (fin && !tm && !po.tgt)  ? propagate_kernel<E, kDT, (E > 1 ? 0 : 2)>
+                                           : propagate_kernel<E, kDT, 0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
