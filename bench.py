@@ -48,7 +48,7 @@ PROPAGATION = {"first_order": 0, "best_first": 1, "pairwise": 2}
 # current kernels on the 400k-point case of the sift1m configuration (leaf:
 # per point and tree; propagation: per point and round).
 TRAFFIC = {("sift1m", "bf16"): {"leaf_knn": (948.755968e6 + 560.620288e6) / (400_000 * 8),
-                                "propagate": (267.727872e6 + 69.586176e6) / 400_000}}
+                                "propagate": (269.010944e6 + 69.613056e6 + 221.221632e6 + 61.197824e6) / 2 / 400_000}}
 METRIC = "points/sec to build the k-NN graph (recall@k reported on a 10k-point sample)"
 
 
