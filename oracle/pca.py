@@ -13,11 +13,13 @@ the readings used here (the kernel takes the same ones):
   word r mod 4 of Philox4x32-10 with counter (t, level | 2^30, v, r // 4) and
   key = seed (with replacement).  s_cap = clamp(floor(40960 / d), 8, 128).
 * covariance of the sample, C = A^T A / s with A the centred rows.
-* Lanczos with full reorthogonalisation (each C v_j is orthogonalised
-  against every earlier basis vector by one classical Gram-Schmidt pass; its
-  coefficient on v_j is alpha_j) from the node's random direction (the one
-  the random partitioner would use, normalised), at most q = min(8, d)
-  steps, stopping once beta_j <= 1e-4 * max_i alpha_i.
+* the textbook Lanczos recurrence, alpha_j = v_j . C v_j and
+  w = C v_j - alpha_j v_j - beta_{j-1} v_{j-1}, with full reorthogonalisation
+  (w is orthogonalised against every earlier basis vector by classical
+  Gram-Schmidt, applied twice: a second pass restores orthogonality to
+  working precision), from the node's random direction (the one the random
+  partitioner would use, normalised), at most q = min(8, d) steps, stopping
+  once beta_j <= 1e-4 * max_i alpha_i.
 * the Ritz vector of the largest eigenvalue of the tridiagonal matrix,
   normalised, with its largest-magnitude entry made positive (ties: the
   lowest index).
@@ -62,13 +64,16 @@ def lanczos_top(C_mul, v0: np.ndarray, steps: int):
     amax = 0.0
     for j in range(steps):
         w = C_mul(V[j])
-        # one classical Gram-Schmidt pass against v_0 .. v_j: the coefficient
-        # on v_j is alpha_j; the pass also removes the three-term part
-        coef = V[:j + 1] @ w
-        a = float(coef[j])
+        a = float(V[j] @ w)
         alpha.append(a)
         amax = max(amax, a)
-        w = w - V[:j + 1].T @ coef
+        # three-term recurrence
+        w = w - a * V[j]
+        if j > 0:
+            w = w - beta[j - 1] * V[j - 1]
+        # full reorthogonalisation: classical Gram-Schmidt, twice
+        for _ in range(2):
+            w = w - V[:j + 1].T @ (V[:j + 1] @ w)
         b = float(np.linalg.norm(w))
         if j == steps - 1 or b <= 1e-4 * amax:
             break
