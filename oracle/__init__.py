@@ -10,6 +10,8 @@ with ``-ffp-contract=off``); this module compiles it with gcc, loads it with
 ctypes and composes the stages in the order of the paper:
 
 * ``partition``   -- one random partition tree (Sec. 3.1; App. after Lemma 1)
+* ``partition_features`` -- one tree of the learned partitioner's per-level
+  feature splits (not in the paper)
 * ``leaf_knn``    -- brute force inside every leaf (Sec. 3.1)
 * ``merge``       -- union of the T base graphs, k nearest kept (Sec. 3.1)
 * ``propagate``   -- one first-order propagation round (Sec. 3.2, Theorem 1)
@@ -69,6 +71,8 @@ def _load():
             lib.orc_leaf_count.restype = i64
             lib.orc_partition.argtypes = [P, i64, i32, i64, u64, u32, i32, P, P]
             lib.orc_partition_dirs.argtypes = [P, i64, i32, i64, P, i32, P, P]
+            lib.orc_feature_order.argtypes = [u64, u32, i32, P]
+            lib.orc_partition_features.argtypes = [P, i64, i32, i64, P, i32, u64, u32, i32, ctypes.c_float, P, P]
             lib.orc_leaf_knn.argtypes = [P, i64, i32, i64, P, P, i64, i32, P, P]
             lib.orc_leaf_knn_quant.argtypes = [P, i64, i32, i64, P, P, P, i64, i32, i32, P, P]
             lib.orc_merge.argtypes = [P, i64, i32, i64, i32, i32, P, P, P]
@@ -161,6 +165,33 @@ def partition_with_dirs(X, dirs, g: int):
     perm = np.zeros(n, dtype=np.int32)
     off = np.zeros(leaf_count(n, g) + 1, dtype=np.int64)
     lib.orc_partition_dirs(_ptr(X), n, d, d, _ptr(dirs), g, _ptr(perm), _ptr(off))
+    return perm, off
+
+
+LEARNED_TAU = 0.02
+
+
+def feature_order(seed: int, t: int, C: int) -> np.ndarray:
+    """Tree t's order of the C learned features (Philox Fisher-Yates)."""
+    out = np.zeros(C, dtype=np.int32)
+    _load().orc_feature_order(seed, t, C, _ptr(out))
+    return out
+
+
+def partition_features(X, Z, seed: int, t: int, g: int, tau: float = LEARNED_TAU):
+    """Canonical leaf set of tree t under the learned partitioner's
+    per-level feature splits (Z: float32 [n, C] network outputs); random
+    directions where a feature is flat in a node and past level C."""
+    lib = _load()
+    X = _as_f32(X)
+    n, d = X.shape
+    Z = np.ascontiguousarray(Z, dtype=np.float32)
+    assert Z.shape[0] == n
+    C = Z.shape[1]
+    perm = np.zeros(n, dtype=np.int32)
+    off = np.zeros(leaf_count(n, g) + 1, dtype=np.int64)
+    rc = lib.orc_partition_features(_ptr(X), n, d, d, _ptr(Z), C, seed, t, g, float(tau), _ptr(perm), _ptr(off))
+    assert rc == 0
     return perm, off
 
 

@@ -311,6 +311,135 @@ int orc_partition_dirs(const float* X, int64_t n, int d, int64_t ld, const float
 }
 
 /* ------------------------------------------------------------------------ */
+/* Learned-feature splits (not in the paper; the learned partitioner's       */
+/* per-level feature mode).  Z holds C network outputs per point (FP32, row  */
+/* i at Z + i*C).  Tree t uses the feature order pi_t, a Fisher-Yates         */
+/* shuffle of 0..C-1 driven by Philox4x32-10: for i = C-1 down to 1, word 0  */
+/* of Philox(counter (t, 0x4C524E44, i, 0), key seed) modulo i+1 is the      */
+/* index j swapped with i.  A node at level l < C splits at the median of    */
+/* feature f = pi_t(l) (key ord(z_f) << 32 | id) when its range inside the   */
+/* node exceeds tau times its range over all points -- both ranges are       */
+/* max - min in FP32 and the product is rounded to FP32 -- and otherwise,    */
+/* like every node at level >= C, at the median of its random direction.    */
+/* ------------------------------------------------------------------------ */
+void orc_feature_order(uint64_t seed, uint32_t t, int C, int32_t* order)
+{
+    const uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    for (int c = 0; c < C; ++c) order[c] = c;
+    for (int i = C - 1; i > 0; --i) {
+        const uint32_t ctr[4] = {t, 0x4C524E44u, (uint32_t)i, 0u};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        const int j = (int)(w[0] % (uint32_t)(i + 1));
+        const int32_t tmp = order[i];
+        order[i] = order[j];
+        order[j] = tmp;
+    }
+}
+
+typedef struct {
+    part_ctx base;
+    const float* Z;
+    int C;
+    const int32_t* order;
+    const float* zrange; /* range of every feature over all points */
+    float tau;
+} feat_ctx;
+
+static void split_node_feat(feat_ctx* f, int32_t* ids, int64_t m, uint32_t level, uint32_t v)
+{
+    part_ctx* c = &f->base;
+    if (m <= c->g) {
+        qsort(ids, (size_t)m, sizeof(int32_t), cmp_i32);
+        memcpy(c->perm + c->pos, ids, (size_t)m * sizeof(int32_t));
+        c->leaf_off[c->nleaves++] = c->pos;
+        c->pos += m;
+        return;
+    }
+    uint64_t* keys = (uint64_t*)malloc((size_t)m * sizeof(uint64_t));
+    int learned = 0;
+    int feat = 0;
+    if ((int)level < f->C) {
+        feat = f->order[level];
+        float lo = f->Z[(int64_t)ids[0] * f->C + feat], hi = lo;
+        for (int64_t i = 1; i < m; ++i) {
+            const float z = f->Z[(int64_t)ids[i] * f->C + feat];
+            if (z < lo) lo = z;
+            if (z > hi) hi = z;
+        }
+        const float span = hi - lo;
+        const float bar = f->tau * f->zrange[feat];
+        learned = span > bar;
+    }
+    if (learned) {
+        for (int64_t i = 0; i < m; ++i)
+            keys[i] = ((uint64_t)orc_ord(f->Z[(int64_t)ids[i] * f->C + feat]) << 32) | (uint32_t)ids[i];
+    } else {
+        float* a = (float*)malloc((size_t)c->d * sizeof(float));
+        orc_direction(c->seed, c->t, level, v, c->d, a);
+        for (int64_t i = 0; i < m; ++i) {
+            const float s = orc_project(c->X + (int64_t)ids[i] * c->ld, a, c->d);
+            keys[i] = ((uint64_t)orc_ord(s) << 32) | (uint32_t)ids[i];
+        }
+        free(a);
+    }
+    qsort(keys, (size_t)m, sizeof(uint64_t), cmp_u64);
+    const int64_t ml = m / 2;
+    int32_t* left = (int32_t*)malloc((size_t)ml * sizeof(int32_t));
+    int32_t* right = (int32_t*)malloc((size_t)(m - ml) * sizeof(int32_t));
+    for (int64_t i = 0; i < ml; ++i) left[i] = (int32_t)(keys[i] & 0xFFFFFFFFu);
+    for (int64_t i = ml; i < m; ++i) right[i - ml] = (int32_t)(keys[i] & 0xFFFFFFFFu);
+    free(keys);
+    split_node_feat(f, left, ml, level + 1, 2 * v);
+    split_node_feat(f, right, m - ml, level + 1, 2 * v + 1);
+    free(left);
+    free(right);
+}
+
+/* Canonical leaf set of tree t under learned-feature splits (perm: n
+ * entries; leaf_off: orc_leaf_count(n, g) + 1 entries). */
+int orc_partition_features(const float* X, int64_t n, int d, int64_t ld, const float* Z, int C, uint64_t seed,
+                           uint32_t t, int g, float tau, int32_t* perm, int64_t* leaf_off)
+{
+    if (C < 1 || C > 64) return -1;
+    int32_t order[64];
+    orc_feature_order(seed, t, C, order);
+    float zrange[64];
+    for (int c = 0; c < C; ++c) {
+        float lo = Z[c], hi = Z[c];
+        for (int64_t i = 1; i < n; ++i) {
+            const float z = Z[i * C + c];
+            if (z < lo) lo = z;
+            if (z > hi) hi = z;
+        }
+        zrange[c] = hi - lo;
+    }
+    feat_ctx f;
+    f.base.X = X;
+    f.base.d = d;
+    f.base.ld = ld;
+    f.base.seed = seed;
+    f.base.t = t;
+    f.base.g = g;
+    f.base.perm = perm;
+    f.base.leaf_off = leaf_off;
+    f.base.nleaves = 0;
+    f.base.pos = 0;
+    f.base.dirs = NULL;
+    f.Z = Z;
+    f.C = C;
+    f.order = order;
+    f.zrange = zrange;
+    f.tau = tau;
+    int32_t* ids = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    for (int64_t i = 0; i < n; ++i) ids[i] = (int32_t)i;
+    split_node_feat(&f, ids, n, 0, 0);
+    free(ids);
+    leaf_off[f.base.nleaves] = n;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Leaf graph (Sec. 3.1): brute force inside each subset.  For every point i */
 /* of a leaf, the k nearest other members by (D, id).  ids/dists: [n, k],    */
 /* row i belongs to point i.                                                 */

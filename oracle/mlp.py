@@ -36,6 +36,8 @@ import math
 
 import numpy as np
 
+from . import philox4x32_10
+
 SQRT2 = math.sqrt(2.0)
 INV_SQRT_2PI = 1.0 / math.sqrt(2.0 * math.pi)
 
@@ -107,3 +109,49 @@ def loss_and_grads(X, W1, b1, W2, b2, lam=0.05, eps=1e-4, mu_s=1.0):
     dW1 = dA.T @ X
     db1 = dA.sum(axis=0)
     return L, (dW1, db1, dW2, db2)
+
+
+# --------------------------------------------------------------- training --
+# The training loop draws each batch from the graph with Philox4x32-10 and
+# takes one Adam step (Kingma and Ba, "Adam: a method for stochastic
+# optimization", ICLR 2015, Algorithm 1) per batch.
+
+BATCH_TAG = 0x4C4E4E42
+
+
+def sample_batch(X, ids, B: int, seed: int, step: int) -> np.ndarray:
+    """The FP32 pair rows [2B, d] of training step `step`: edge b takes point
+    i = (w0 * 2^32 + w1) mod n and the first valid entry of i's list at slots
+    ((w2 + t) mod 2^32) mod k, t = 0, 1, ... (i itself if the list is empty),
+    where
+    (w0..w3) = Philox4x32-10(counter (b, step, BATCH_TAG, 0), key seed).
+    Row b is x_i, row B + b is x_j."""
+    X = np.asarray(X)
+    X = X.astype(np.float32) if X.dtype != np.float32 else X
+    ids = np.asarray(ids)
+    n, k = ids.shape
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    out = np.empty((2 * B, X.shape[1]), dtype=np.float32)
+    for b in range(B):
+        w = [int(x) for x in philox4x32_10((b, step, BATCH_TAG, 0), key)]
+        i = ((w[0] << 32) | w[1]) % n
+        j = -1
+        for t in range(k):
+            j = int(ids[i, ((w[2] + t) & 0xFFFFFFFF) % k])
+            if j >= 0:
+                break
+        if j < 0 or j >= n:
+            j = i
+        out[b] = X[i]
+        out[B + b] = X[j]
+    return out
+
+
+def adam_step(w, g, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """Step t (1-based) of Adam, FP64: returns the new (w, m, v)."""
+    w, g, m, v = (np.asarray(a, dtype=np.float64) for a in (w, g, m, v))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return w - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -54,9 +54,10 @@ def sample_rows(members, seed: int, t: int, level: int, v: int, d: int) -> np.nd
     return members[idx]
 
 
-def lanczos_top(C_mul, v0: np.ndarray, steps: int):
+def lanczos_top(C_mul, v0: np.ndarray, steps: int, with_value: bool = False):
     """Top Ritz vector of the symmetric operator C_mul after at most
-    `steps` Lanczos steps with full reorthogonalisation, from v0."""
+    `steps` Lanczos steps with full reorthogonalisation, from v0 (and its
+    Ritz value when with_value)."""
     d = v0.shape[0]
     V = np.zeros((steps + 1, d))
     V[0] = v0 / np.linalg.norm(v0)
@@ -90,12 +91,22 @@ def lanczos_top(C_mul, v0: np.ndarray, steps: int):
     i = int(np.argmax(np.abs(a)))
     if a[i] < 0:
         a = -a
-    return a
+    return (a, float(evals[-1])) if with_value else a
 
 
-def principal_direction(X, members, seed: int, t: int, level: int, v: int) -> np.ndarray:
+def sample_covariance(X, members, seed: int, t: int, level: int, v: int) -> np.ndarray:
+    """C = A^T A / s of the node's sampled rows A, centred (FP64)."""
+    X = np.asarray(X)
+    rows = sample_rows(members, seed, t, level, v, X.shape[1])
+    A = X[rows].astype(np.float64)
+    A = A - A.mean(axis=0)
+    return A.T @ A / A.shape[0]
+
+
+def principal_direction(X, members, seed: int, t: int, level: int, v: int, with_value: bool = False):
     """Split direction of node (t, level, v) whose members (ascending ids)
-    are given: the principal direction of the sampled, centred rows."""
+    are given: the principal direction of the sampled, centred rows (and its
+    Ritz value, the variance along it, when with_value)."""
     X = np.asarray(X)
     d = X.shape[1]
     rows = sample_rows(members, seed, t, level, v, d)
@@ -103,4 +114,4 @@ def principal_direction(X, members, seed: int, t: int, level: int, v: int) -> np
     A = A - A.mean(axis=0)
     s = A.shape[0]
     v0 = direction(seed, t, level, v, d).astype(np.float64)
-    return lanczos_top(lambda x: A.T @ (A @ x) / s, v0, min(STEPS, d))
+    return lanczos_top(lambda x: A.T @ (A @ x) / s, v0, min(STEPS, d), with_value)

@@ -68,3 +68,47 @@ def test_loss_terms_special_cases():
     # collapse to a constant costs the spread term: C * mu_s
     L, _ = mlp.loss_from_z(np.full((8, 3), 0.3), 0.0, 1e-4, 2.0)
     assert abs(L - 6.0) < 1e-12
+
+
+# ------------------------------------------------------------ training --
+def test_adam_first_step_is_a_sign_step():
+    # from zero moments the bias corrections make the first step
+    # lr * g / (|g| + eps): a step of lr against the sign of the gradient
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=50)
+    g = rng.normal(size=50)
+    g[3] = 0.0
+    w1, m1, v1 = mlp.adam_step(w, g, np.zeros(50), np.zeros(50), 1, 0.01)
+    np.testing.assert_allclose(w1, w - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(m1, 0.1 * g)
+    np.testing.assert_allclose(v1, 0.001 * g * g)
+
+
+def test_adam_constant_gradient_moves_at_the_learning_rate():
+    # a constant gradient g: the bias-corrected moments equal g and g^2 at
+    # every step, so each step moves every weight by lr * g / (|g| + eps)
+    rng = np.random.default_rng(1)
+    w0 = rng.normal(size=20)
+    g = rng.normal(size=20)
+    w, m, v = w0, np.zeros(20), np.zeros(20)
+    for t in range(1, 8):
+        w, m, v = mlp.adam_step(w, g, m, v, t, 3e-3)
+    np.testing.assert_allclose(w, w0 - 7 * 3e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-12)
+
+
+def test_batch_sampler_draws_graph_edges():
+    rng = np.random.default_rng(2)
+    n, k, d = 300, 5, 7
+    X = rng.normal(size=(n, d)).astype(np.float32)
+    ids = rng.integers(0, n, size=(n, k)).astype(np.int32)
+    ids[7] = -1                       # an empty list: the edge is (i, i)
+    P = mlp.sample_batch(X, ids, 400, 9, 3)
+    rowid = {X[i].tobytes(): i for i in range(n)}
+    hits = np.zeros(n)
+    for b in range(400):
+        i, j = rowid[P[b].tobytes()], rowid[P[400 + b].tobytes()]
+        hits[i] += 1
+        assert (j in ids[i]) or (i == 7 and j == 7)
+    assert (hits > 0).sum() > 200     # points drawn across the whole set
+    np.testing.assert_array_equal(P, mlp.sample_batch(X, ids, 400, 9, 3))
+    assert not np.array_equal(P, mlp.sample_batch(X, ids, 400, 9, 4))
