@@ -310,6 +310,13 @@ int knng_mlp_train(knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t
 /* Binary file with a header and the packed FP32 parameters. */
 int knng_mlp_save(const knng_mlp* m, const char* path);
 int knng_mlp_load(knng_mlp* m, const char* path);
+/* Adam state of the training loop (to resume training where it stopped):
+ * the first and second moment estimates (HOST, param_count floats each) and
+ * the number of steps taken, which sets the bias corrections 1 - 0.9^t and
+ * 1 - 0.999^t of the next step.  A new network starts at zero moments and
+ * t = 0.  set_adam_state rejects t < 0 with KNNG_ERR_INVALID_ARG. */
+int knng_mlp_get_adam_state(const knng_mlp* m, float* m1_host, float* m2_host, int64_t* t);
+int knng_mlp_set_adam_state(knng_mlp* m, const float* m1_host, const float* m2_host, int64_t t);
 /* Features of every point: Z (device, FP32 [n][d_out]), BF16 inference. */
 int knng_mlp_forward(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                      float* Z, void* stream);
@@ -326,6 +333,20 @@ int knng_mlp_forward(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, 
  * of the random ones.  Leaf graphs, merge and propagation use X. */
 int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                        const knng_params* p, int32_t* ids, float* dists, void* stream);
+/* The partition stage of knng_build_learned with KNNG_PART_FEATURES: the T
+ * canonical leaf sets (perm, device [T][n], as knng_partition writes them)
+ * of the per-level learned-feature splits.  Level l < d_out of tree t splits
+ * every node at the median of output f = pi_t(l) (key ord(z_f) << 32 | id)
+ * when the node's range of z_f, max - min in FP32, exceeds 0.02 x (the
+ * range of z_f over all points), FP32 product; otherwise, and on levels
+ * l >= d_out, at the median of the node's random direction (as
+ * knng_partition).  pi_t: Fisher-Yates over 0..d_out-1, i = d_out-1 down to
+ * 1, j = w.x mod (i + 1) with w = Philox4x32-10(counter (t, 0x4C524E44, i,
+ * 0), key seed).  Z (device, may be NULL) receives the network outputs used,
+ * FP32 [n][d_out].  T <= 32, d <= 128. */
+int knng_partition_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d,
+                           int64_t ld, int32_t T, int32_t g, uint64_t seed, int32_t* perm, float* Z,
+                           void* stream);
 
 /* ---- propagation without device allocation ---------------------------- */
 /* The paper has no counterpart: this entry point exists for callers that

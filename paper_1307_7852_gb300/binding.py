@@ -83,6 +83,8 @@ SIGNATURES = {
     "knng_mlp_param_count": [_P, ctypes.POINTER(ctypes.c_int64)],
     "knng_mlp_get_params": [_P, _P],
     "knng_mlp_set_params": [_P, _P],
+    "knng_mlp_get_adam_state": [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)],
+    "knng_mlp_set_adam_state": [_P, _P, _P, _I64],
     "knng_mlp_loss_grad": [_P, _P, _I32, ctypes.POINTER(ctypes.c_float), _P, _P],
     "knng_mlp_train": [_P, _P, _I32, _I64, _I32, _I64, _P, _I32, _I32, _I32, ctypes.c_float, _U64,
                        ctypes.POINTER(ctypes.c_float), _P],
@@ -90,6 +92,7 @@ SIGNATURES = {
     "knng_mlp_load": [_P, ctypes.c_char_p],
     "knng_mlp_forward": [_P, _P, _P, _I32, _I64, _I32, _I64, _P, _P],
     "knng_build_learned": [_P, _P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P],
+    "knng_partition_learned": [_P, _P, _P, _I32, _I64, _I32, _I64, _I32, _I32, _U64, _P, _P, _P],
     "knng_build_batched": [_P, _I32, _P, ctypes.POINTER(knng_params), _P],
     "knng_propagate_noalloc": [_P, _I32, _I64, _I32, _I64, _I32, _I32, _P, _P, _P, _P, _P],
 }
@@ -543,6 +546,24 @@ class Mlp:
         assert buf.size == self.param_count()
         self._chk(lib().knng_mlp_set_params(self._p, ctypes.c_void_p(buf.ctypes.data)), "knng_mlp_set_params")
 
+    def get_adam_state(self):
+        """(m1, m2, t): Adam moment estimates (float32 numpy) and steps taken."""
+        m1 = np.empty(self.param_count(), dtype=np.float32)
+        m2 = np.empty_like(m1)
+        t = ctypes.c_int64()
+        self._chk(lib().knng_mlp_get_adam_state(self._p, ctypes.c_void_p(m1.ctypes.data),
+                                                ctypes.c_void_p(m2.ctypes.data), ctypes.byref(t)),
+                  "knng_mlp_get_adam_state")
+        return m1, m2, int(t.value)
+
+    def set_adam_state(self, m1, m2, t):
+        m1 = np.ascontiguousarray(m1, dtype=np.float32)
+        m2 = np.ascontiguousarray(m2, dtype=np.float32)
+        assert m1.size == m2.size == self.param_count()
+        self._chk(lib().knng_mlp_set_adam_state(self._p, ctypes.c_void_p(m1.ctypes.data),
+                                                ctypes.c_void_p(m2.ctypes.data), int(t)),
+                  "knng_mlp_set_adam_state")
+
     def loss_grad(self, Xpairs, stream=None):
         """Loss and packed gradient of a batch (CUDA float32 [2B, d_in])."""
         torch = _torch()
@@ -603,3 +624,19 @@ def knng_build_learned(mlp: Mlp, X, k, T, leaf_size, prop_rounds, seed, precisio
     h.check(lib().knng_build_learned(h.ptr, mlp.ptr, xp, dt, n, d, ld, ctypes.byref(p), _ptr(ids), _ptr(dists),
                                      _stream(X.device, stream)), "knng_build_learned")
     return ids, dists
+
+
+def knng_partition_learned(mlp: Mlp, X, T, leaf_size, seed, perm=None, with_z=False, stream=None,
+                           h: Handle = None):
+    """Canonical leaf sets of the per-level learned-feature splits
+    (knng_build_learned's KNNG_PART_FEATURES partition): perm [T, n], and the
+    network outputs Z [n, d_out] used when with_z."""
+    torch = _torch()
+    xp, dt, n, d, ld = _xdesc(X)
+    h = h or handle(X.device.index or 0)
+    perm = _out((T, n), torch.int32, X.device, perm)
+    Z = torch.empty((n, mlp.d_out), dtype=torch.float32, device=X.device) if with_z else None
+    h.check(lib().knng_partition_learned(h.ptr, mlp.ptr, xp, dt, n, d, ld, int(T), int(leaf_size),
+                                         int(seed) & (2**64 - 1), _ptr(perm), _ptr(Z) if Z is not None else None,
+                                         _stream(X.device, stream)), "knng_partition_learned")
+    return (perm, Z) if with_z else perm

@@ -1210,6 +1210,46 @@ int knng_build_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype
                           feat ? nullptr : &xz);
 }
 
+int knng_partition_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t dtype, int64_t n, int32_t d,
+                           int64_t ld, int32_t T, int32_t g, uint64_t seed, int32_t* perm, float* Zout, void* stream)
+{
+    XDesc x;
+    int r = check_x(h, X, dtype, n, d, ld, x);
+    if (r) return r;
+    if ((r = check_tree(h, T, g))) return r;
+    if (!perm) return fail(h, KNNG_ERR_INVALID_ARG, "perm is NULL");
+    if (T > 32) return fail(h, KNNG_ERR_INVALID_ARG, "T");
+    MlpModel* M = mlp_model(m);
+    if (!M) return fail(h, KNNG_ERR_INVALID_ARG, "NULL network");
+    if (M->d != d) return fail(h, KNNG_ERR_INVALID_ARG, "network input %d != d %d", M->d, d);
+    if (d > 128) return fail(h, KNNG_ERR_UNSUPPORTED, "tensor-core inference supports d <= 128");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((r = ensure_plan(h, n, g, st))) return r;
+    LearnedFeat lf;
+    lf.C = M->C;
+    learned_feature_order(seed, T, M->C, lf);
+    Arena m0;
+    if (!Zout) m0.take<float>((size_t)n * M->C);
+    m0.take<uint32_t>(2 * (size_t)M->C);
+    m0.take<float>((size_t)M->C);
+    run_partition(x, h->plan, h->dplan, T, seed, nullptr, m0, st, &lf);
+    if ((r = ensure_ws(h, m0.off, st))) return r;
+    Arena a;
+    a.base = h->ws;
+    float* Z = Zout ? Zout : a.take<float>((size_t)n * M->C);
+    uint32_t* mm = a.take<uint32_t>(2 * (size_t)M->C);
+    float* frange = a.take<float>((size_t)M->C);
+    lf.Z = Z;
+    lf.frange = frange;
+    cudaError_t e = run_mlp_forward(*M, x, Z, h->dev_err, st);
+    if (e == cudaSuccess) e = run_feature_range(Z, n, M->C, mm, frange, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "network inference");
+    e = run_partition(x, h->plan, h->dplan, T, seed, perm, a, st, &lf, 0, nullptr, h->dev_err);
+    if (e != cudaSuccess) return cuda_fail(h, e, "partition");
+    return KNNG_OK;
+}
+
 int knng_build_host(knng_handle* h, const void* X, int32_t dtype, int64_t n, int32_t d, int64_t ld,
                     const knng_params* p, int32_t* ids, float* dists, void* stream)
 {

@@ -458,6 +458,32 @@ int knng_mlp_set_params(knng_mlp* o, const float* host)
     return e == cudaSuccess ? KNNG_OK : KNNG_ERR_CUDA;
 }
 
+int knng_mlp_get_adam_state(const knng_mlp* o, float* m1_host, float* m2_host, int64_t* t)
+{
+    if (!o || !m1_host || !m2_host || !t) return KNNG_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(o->m.device);
+    cudaError_t e = cudaMemcpy(m1_host, o->m.am, sizeof(float) * o->m.count, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(m2_host, o->m.av, sizeof(float) * o->m.count, cudaMemcpyDeviceToHost);
+    *t = o->m.adam_t;
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? KNNG_OK : KNNG_ERR_CUDA;
+}
+
+int knng_mlp_set_adam_state(knng_mlp* o, const float* m1_host, const float* m2_host, int64_t t)
+{
+    if (!o || !m1_host || !m2_host || t < 0) return KNNG_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(o->m.device);
+    cudaError_t e = cudaMemcpy(o->m.am, m1_host, sizeof(float) * o->m.count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(o->m.av, m2_host, sizeof(float) * o->m.count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) o->m.adam_t = t;
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? KNNG_OK : KNNG_ERR_CUDA;
+}
+
 int knng_mlp_loss_grad(knng_mlp* o, const float* Xpairs, int32_t B, float* loss, float* grad, void* stream)
 {
     if (!o || !Xpairs || B < 2 || !loss || !grad) return KNNG_ERR_INVALID_ARG;

@@ -10,7 +10,8 @@ import pytest
 
 import oracle
 from paper_1307_7852_gb300 import synthetic
-from test_gpu_parity import assert_lists_close, assert_valid_rows
+from test_gpu_parity import assert_valid_rows
+from validity import check_build_stagewise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,11 +63,11 @@ def test_cosine_build_matches_oracle(n, d, k, T, g, R):
     oi, od = oracle.build_graph(X, k, T, g, R, 11, metric=oracle.METRIC_COSINE)
     gi, gd = host(gi), host(gd)
     assert_valid_rows(gi, gd, n)
-    # whole-build lists may differ after a near-tie flip upstream; the stages
-    # are bit-exact or tolerance-checked, so compare rows and distances
+    # the build through its stages on the unit rows, every row checked
+    check_build_stagewise(knng(), torch, X, k, T, g, R, 11, gi, gd, cosine=True)
+    # and against the oracle's whole build where the two agree row for row
     same = np.all(gi == oi, axis=1)
-    assert same.mean() > 0.99
-    assert_lists_close(gi[same], gd[same], oi[same], od[same])
+    np.testing.assert_allclose(gd[same], od[same], rtol=1e-5)
 
 
 def test_cosine_is_scale_invariant_on_gpu():
@@ -90,7 +91,9 @@ def test_cosine_on_unit_rows_is_half_the_l2_graph():
         np.testing.assert_array_equal(host(a[0]), host(b[0]))
         np.testing.assert_array_equal(host(a[1]), host(b[1]) * np.float32(0.5))
     else:
-        assert np.mean(host(a[0]) == host(b[0])) > 0.99
+        # scaling moved some rows by an FP32 step: the cosine build is still
+        # checked in full through its stages
+        check_build_stagewise(knng(), torch, X, 10, 3, 64, 1, 3, host(a[0]), host(a[1]), cosine=True)
 
 
 def test_cosine_batched_and_bf16():
@@ -102,7 +105,7 @@ def test_cosine_batched_and_bf16():
         np.testing.assert_array_equal(host(bi), host(si))
         np.testing.assert_array_equal(host(bd), host(sd))
     X = Xs[1]
-    fi, fd = k.knng_build(dev(X), 10, 3, 64, 1, 4, metric=k.METRIC_COSINE)
     qi, qd = k.knng_build(dev(X), 10, 3, 64, 1, 4, precision=k.PREC_BF16, metric=k.METRIC_COSINE)
-    assert np.mean(host(fi) == host(qi)) > 0.97
     assert np.all(host(qd) >= 0) and np.all(host(qd) <= 2.0)
+    # the BF16 candidate stage on the unit rows, every row checked
+    check_build_stagewise(k, torch, X, 10, 3, 64, 1, 4, host(qi), host(qd), precision=k.PREC_BF16, cosine=True)

@@ -8,6 +8,7 @@ import pytest
 import oracle
 from oracle import mlp as omlp
 from paper_1307_7852_gb300 import synthetic
+from validity import check_build_stagewise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -117,24 +118,83 @@ def test_learned_splits_gain_over_random_at_equal_trees(trained, mode):
     assert r_lrn > r_rand, (r_lrn, r_rand)
 
 
-def test_learned_embedding_build_matches_oracle_stagewise(trained):
-    # the embedding trees are the random partition of the points z = f(x)
-    # (the GPU's BF16 inference), the lists those of the rows x
+@pytest.mark.parametrize("mode", ["embedding", "features"])
+def test_learned_build_matches_oracle_stagewise(trained, mode):
+    # the learned build through its stages: the partition of the GPU's network
+    # outputs z (random trees on z, or per-level feature splits) bit-exact,
+    # then the lists of the rows x, every row checked in full
     k = knng()
     X, net = trained
     X = np.ascontiguousarray(X[:8000])
     Xd = torch.from_numpy(X).cuda()
-    Z = k.knng_mlp_forward(net, Xd).cpu().numpy()
     T, g, kk, seed = 3, 64, 10, 4
-    gi, gd = k.knng_build_learned(net, Xd, kk, T, g, 1, seed)
-    Xf = X.astype(np.float32)
-    lists = np.empty((T, 8000, kk), dtype=np.int32)
+    part = k.PART_RANDOM if mode == "embedding" else k.PART_FEATURES
+    gi, gd = k.knng_build_learned(net, Xd, kk, T, g, 1, seed, partitioner=part)
+    check_build_stagewise(k, torch, X, kk, T, g, 1, seed, gi.cpu().numpy(), gd.cpu().numpy(), net=net,
+                          learned=mode)
+
+
+def test_feature_partition_bit_exact(trained):
+    # the per-level learned-feature partition replayed by the oracle on the
+    # GPU's own network outputs (BF16 inference) is bit-exact
+    k = knng()
+    X, net = trained
+    T, g, seed = 3, 48, 17
+    perm, Z = k.knng_partition_learned(net, torch.from_numpy(X).cuda(), T, g, seed, with_z=True)
+    perm, Z = perm.cpu().numpy(), Z.cpu().numpy()
     for t in range(T):
-        perm, off = oracle.partition(Z, seed, t, g)
-        np.testing.assert_array_equal(k.knng_partition(torch.from_numpy(Z).cuda(), T, g, seed)[t].cpu().numpy(),
-                                      perm)
-        lists[t], _ = oracle.leaf_knn(Xf, perm, off, kk)
-    oi, od = oracle.merge(Xf, lists, kk)
-    oi, od = oracle.propagate(Xf, oi, kk)
-    gi = gi.cpu().numpy()
-    assert np.mean(gi == oi) > 0.99
+        np.testing.assert_array_equal(perm[t], oracle.partition_features(X, Z, seed, t, g)[0])
+
+
+def test_feature_partition_flat_outputs_and_deep_trees():
+    # outputs 0..7 constant (zero output weights): those levels fall back to
+    # random directions of x; 140,000 points at leaf size 2 need 17 levels,
+    # one more than the 16 outputs
+    k = knng()
+    net = k.Mlp(96, 64, 16, seed=8)
+    W1, b1, W2, b2 = net.get_params()
+    W2 = W2.copy()
+    W2[:8] = 0.0
+    b2 = b2.copy()
+    b2[:8] = np.linspace(-0.5, 0.5, 8, dtype=np.float32)
+    net.set_params(W1, b1, W2, b2)
+    X = synthetic.sphere_f16(140000, 96, centers=64, seed=12)
+    T, g, seed = 2, 2, 23
+    perm, Z = k.knng_partition_learned(net, torch.from_numpy(X).cuda(), T, g, seed, with_z=True)
+    perm, Z = perm.cpu().numpy(), Z.cpu().numpy()
+    assert np.all(Z[:, :8] == Z[0, :8])
+    for t in range(T):
+        np.testing.assert_array_equal(perm[t], oracle.partition_features(X, Z, seed, t, g)[0])
+
+
+def test_adam_step_matches_fp64_oracle():
+    # one training step from a given Adam state: the batch the GPU draws is
+    # the oracle's sampler's (Philox), its gradient the GPU's own (checked
+    # against FP64 above), and the update must be the FP64 Adam step of it
+    k = knng()
+    rng = np.random.default_rng(4)
+    net = k.Mlp(32, 64, 16, seed=6)
+    n, kk, B, lr, seed = 3000, 8, 256, 3e-3, 41
+    X = rng.normal(size=(n, 32)).astype(np.float32)
+    ids = rng.integers(0, n, size=(n, kk)).astype(np.int32)
+    ids[5, :] = -1
+    P = net.param_count()
+    w0 = np.concatenate([a.ravel() for a in net.get_params()]).astype(np.float32)
+    m0 = (rng.normal(size=P) * 1e-2).astype(np.float32)
+    v0 = (rng.uniform(0, 1e-4, size=P)).astype(np.float32)
+    net.set_adam_state(m0, v0, 5)
+    Xp = omlp.sample_batch(X, ids, B, seed, 0)
+    _, g = net.loss_grad(torch.from_numpy(Xp).cuda())
+    g = g.cpu().numpy()
+    Xd, idd = torch.from_numpy(X).cuda(), torch.from_numpy(ids).cuda()
+    net.train(Xd, idd, 1, batch_edges=B, lr=lr, seed=seed)
+    w1 = np.concatenate([a.ravel() for a in net.get_params()])
+    m1, v1, t1 = net.get_adam_state()
+    assert t1 == 6
+    ow, om, ov = omlp.adam_step(w0, g, m0, v0, 6, lr)
+    np.testing.assert_allclose(m1, om, rtol=2e-6, atol=1e-12)
+    np.testing.assert_allclose(v1, ov, rtol=2e-6, atol=1e-15)
+    step = np.abs(ow - w0)
+    tol = 2 * np.spacing(np.abs(w0).astype(np.float32)).astype(np.float64) + 1e-5 * step
+    assert np.all(np.abs(w1 - ow) <= tol), np.max(np.abs(w1 - ow) / np.maximum(tol, 1e-30))
+    assert np.median(step) > 1e-4      # the step is not vacuous

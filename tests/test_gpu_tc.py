@@ -6,9 +6,10 @@ takes the k' best by the FP64 distance between the quantised rows, then the k
 best of those by the exact distance.  On integer-valued data every bfloat16 is
 exact, so the BF16 path must match the exact leaf graph bit for bit.  On
 real-valued data the GPU's FP32-accumulated candidate distances can order two
-near-equal candidates at the k'-th place differently from FP64; such rows are
-counted, not failed, while every row whose ids agree must carry distances
-within 1e-5 relative.
+near-equal candidates at the k'-th place differently from FP64; every row is
+checked (tests/validity.py): a row may differ from the oracle's only through
+candidates whose quantised distance lies within the accumulation error bound
+of the k'-th, and its distances must be the pairs' own within 1e-5.
 """
 import numpy as np
 import pytest
@@ -16,7 +17,8 @@ import pytest
 import oracle
 from paper_1307_7852_gb300 import synthetic
 
-from test_gpu_parity import assert_lists_close, assert_lists_exact, assert_valid_rows, dev, host, knng
+from test_gpu_parity import assert_lists_exact, assert_valid_rows, dev, host, knng
+from validity import check_quant_leaf
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -43,7 +45,7 @@ def test_bf16_integer_data_is_exact(n, d, k, g):
         assert_lists_exact(ids[t], dd[t], oi, od)
 
 
-def _compare_quant(X, T, g, k, mult, prec, min_rows=0.99):
+def _compare_quant(X, T, g, k, mult, prec):
     n = X.shape[0]
     Xd, perm = _perm(X, T, g, 5)
     ids, dd = knng().knng_leaf_knn(Xd, T, g, perm, k, prec, mult)
@@ -52,11 +54,10 @@ def _compare_quant(X, T, g, k, mult, prec, min_rows=0.99):
     assert_valid_rows(ids, dd, n)
     same_rows = 0
     for t in range(T):
+        check_quant_leaf(X, perm[t], off, ids[t], dd[t], k, mult * k, prec)
         oi, od = oracle.leaf_knn_quant(X, perm[t], off, k, mult * k, prec)
-        eq = np.all(ids[t] == oi, axis=1)
-        same_rows += eq.sum()
-        assert_lists_close(ids[t][eq], dd[t][eq], oi[eq], od[eq])
-    assert same_rows / (T * n) >= min_rows, same_rows / (T * n)
+        same_rows += np.all(ids[t] == oi, axis=1).sum()
+    print(f"rows identical to the FP64 quantised oracle: {same_rows / (T * n):.4f}")
 
 
 @pytest.mark.parametrize("n,d,k,g", [(6000, 96, 10, 128), (3000, 960, 10, 512), (4000, 200, 20, 256)])
