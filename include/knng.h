@@ -131,6 +131,16 @@ const char* knng_last_error(const knng_handle* h);
  * of those calls are then invalid); the flag is cleared. */
 int knng_sync(knng_handle* h, void* stream);
 
+/* Limit, in SM clock cycles, of the tensor-core leaf kernel's waits for its
+ * TMA copies and for the MMAs to release a pipeline stage, for later calls
+ * on h (0, the default: 2e9 cycles, about one second).  A CTA whose wait
+ * runs out records KNNG_ERR_TIMEOUT for knng_sync, waits (under the one-second
+ * limit) for the copies and MMAs it started, frees its tensor memory and
+ * returns; the context stays usable.  A small limit makes waits on copies
+ * that do complete give up -- a way to exercise that path.  cycles < 0:
+ * KNNG_ERR_INVALID_ARG.  No counterpart in the paper. */
+int knng_set_wait_limit(knng_handle* h, int64_t cycles);
+
 /* ---- tree shape (host only) ------------------------------------------ */
 /* Every split halves a node of m points into floor(m/2) (left) and
  * ceil(m/2) (right) points, so the leaf layout of a tree depends on (n, g)
@@ -364,7 +374,11 @@ int knng_partition_learned(knng_handle* h, knng_mlp* m, const void* X, int32_t d
  *    KNNG_ERR_LIMIT without doing any work.  Other bad arguments return
  *    KNNG_ERR_INVALID_ARG; a failed launch returns KNNG_ERR_CUDA.
  *  - The first call on a device looks up the array's device address (once
- *    per device); make that first call before any stream capture.
+ *    per device) and keeps it for the life of the process; make that first
+ *    call before any stream capture.  A device reset (cudaDeviceReset, or a
+ *    primary-context reset by another library) may move the array: after
+ *    one, restart the process before calling again.
+ *  - dtype F32, F16 or U8, with the alignment rule of knng_propagate.
  *  - Every call shares the one array, which keeps the previous call's
  *    contents (nothing in it needs to start at zero): calls whose work
  *    overlaps on the GPU -- on different streams, or from different host

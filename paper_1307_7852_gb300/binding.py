@@ -75,6 +75,7 @@ SIGNATURES = {
     "knng_set_stage_events": [_P, _P, _I32],
     "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
     "knng_sync": [_P, _P],
+    "knng_set_wait_limit": [_P, _I64],
     "knng_autotune": [_P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P, _P],
     "knng_tune_save": [_P, ctypes.c_char_p],
     "knng_tune_load": [_P, ctypes.c_char_p],
@@ -423,6 +424,12 @@ def knng_set_stage_events(events, h: Handle):
         return
     arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
     h.check(lib().knng_set_stage_events(h.ptr, arr, len(events)), "knng_set_stage_events")
+
+
+def knng_set_wait_limit(cycles: int, h: Handle):
+    """Limit (SM cycles, 0 = about one second) of the tensor-core leaf
+    kernel's pipeline waits for later calls on h."""
+    h.check(lib().knng_set_wait_limit(h.ptr, int(cycles)), "knng_set_wait_limit")
 
 
 def knng_launch_counter() -> int:

@@ -70,6 +70,7 @@ struct knng_handle {
     std::vector<float> div_rates;  // their effective rates r_m (adaptive builds)
     char* staging = nullptr;     // device copies of knng_build_host's buffers (grow-only)
     size_t staging_size = 0;
+    long long wait_cycles = 0;   // limit of the leaf kernel's pipeline waits (0: about 1 s)
 };
 
 namespace {
@@ -232,7 +233,8 @@ int leaf_stage(knng_handle* h, const TreePlan& P, const DevPlan& dp, const XDesc
         const TcTile* tile = it == h->tune.end() ? nullptr : &it->second;
         e = (all_exact && ar.base) ? cudaMemsetAsync(all_exact, 0x01, sizeof(int), st) : cudaSuccess;
         if (e == cudaSuccess)
-            e = run_leaf_knn_tc(x, P, dp, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st, tile, all_exact);
+            e = run_leaf_knn_tc(x, P, dp, T, perm, k, kp, prec, ids, dists, h->dev_err, ar, st, tile, all_exact,
+                                h->wait_cycles);
     } else {
         return fail(h, KNNG_ERR_INVALID_ARG, "precision %d", prec);
     }
@@ -830,6 +832,14 @@ int knng_sync(knng_handle* h, void* stream)
                                            "the lists are valid but some offers were dropped");
         return fail(h, KNNG_ERR_TIMEOUT, "a bounded device wait gave up; results of the affected calls are invalid");
     }
+    return KNNG_OK;
+}
+
+int knng_set_wait_limit(knng_handle* h, int64_t cycles)
+{
+    if (!h) return KNNG_ERR_INVALID_ARG;
+    if (cycles < 0) return fail(h, KNNG_ERR_INVALID_ARG, "wait limit %lld", (long long)cycles);
+    h->wait_cycles = cycles;
     return KNNG_OK;
 }
 

@@ -179,9 +179,13 @@ std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec);
 
 // all_exact (nullable): cleared by every leaf whose distances are not all
 // exact (its list is then not the exact k best of the leaf).
+// wait_cycles: limit of the waits on the TMA copies and on the MMAs' release
+// of a pipeline stage (0: about one second); a CTA that gives up sets *err,
+// then waits for its own copies and MMAs under the long limit and returns.
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
                             int k, int kp, int prec, int32_t* ids, float* dists, int* err, Arena& ar,
-                            cudaStream_t st, const TcTile* tile = nullptr, int* all_exact = nullptr);
+                            cudaStream_t st, const TcTile* tile = nullptr, int* all_exact = nullptr,
+                            long long wait_cycles = 0);
 
 // tmask (nullable, T <= 8): per output entry, the trees whose lists held
 // it, when *all_exact != 0 (every leaf list exact); zeros otherwise.

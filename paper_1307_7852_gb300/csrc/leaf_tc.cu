@@ -97,7 +97,7 @@ std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec)
 
 cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T, const int32_t* perm,
                             int k, int kp, int prec, int32_t* ids, float* dists, int* err, Arena& ar,
-                            cudaStream_t st, const TcTile* tile, int* all_exact)
+                            cudaStream_t st, const TcTile* tile, int* all_exact, long long wait_cycles)
 {
     const int elem = prec == 1 ? 2 : 1;
     const int slice = 128 / elem;
@@ -109,7 +109,8 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     uint8_t* qx = ar.take<uint8_t>((size_t)rows);
     if (!ar.base) return cudaSuccess;
     if (kp > kTcCand) kp = kTcCand;
-    const TcGeom G = tc_geometry(P, x.d, prec, tile);
+    TcGeom G = tc_geometry(P, x.d, prec, tile);
+    G.wait = wait_cycles > 0 ? wait_cycles : kWaitCycles;
     if (G.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
 
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();

@@ -229,6 +229,7 @@ struct TcGeom {
     int pipe_bytes;
     int wsc_off;     // offset of the warps' selection scratch in the pipeline region
     int smem;
+    long long wait;  // limit of the producer's waits (copies landed, stage released)
 };
 
 // Bitonic sorting network on a thread's own registers (N a power of two;
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
         for (int kc = 0; kc < G.nK; ++kc) {
             const int s = kc % G.S;
             const uint32_t ph = (uint32_t)(kc / G.S) & 1u;
-            if (!tc::mbar_wait(&full[s], ph, kWaitCycles)) { ok = false; break; }
+            if (!tc::mbar_wait(&full[s], ph, G.wait)) { ok = false; break; }
             consumed = kc + 1;
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_u32(pipe + (size_t)s * G.stage_bytes);
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
             }
             tc::mma_commit(&empty[s]);
             if (kc + G.S < G.nK) {
-                if (!tc::mbar_wait(&empty[s], ph, kWaitCycles)) { ok = false; break; }
+                if (!tc::mbar_wait(&empty[s], ph, G.wait)) { ok = false; break; }
                 load(kc + G.S);
                 ++loaded;
             }
@@ -378,7 +379,8 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
         if (!ok) {
             abort_flag = 1;
             atomicExch(err, 1);
-            // wait (bounded) for the copies this CTA still has in flight
+            // wait (bounded, under the long limit whatever G.wait is) for the
+            // copies this CTA still has in flight
             for (int kc = consumed; kc < loaded; ++kc)
                 tc::mbar_wait(&full[kc % G.S], (uint32_t)(kc / G.S) & 1u, kWaitCycles);
         }

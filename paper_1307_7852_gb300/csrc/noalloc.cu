@@ -33,7 +33,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Device address of the scratch array on the current device.  The name of a
 // __device__ array in host code is only a host-side stand-in, so the address
-// is looked up once per device with that device current.
+// is looked up once per device with that device current and kept for the
+// life of the process (a device reset would invalidate it; the header asks
+// for a process restart after one).
 static int scratch_address(int dev, char** out)
 {
     if (dev < 0 || dev >= kMaxDevices) return KNNG_ERR_UNSUPPORTED;
@@ -60,7 +62,7 @@ extern "C" int knng_propagate_noalloc(const void* X, int32_t dtype, int64_t n, i
                                       float* dists, void* stream)
 {
     if (!X || !ids_in || !dists_in || !ids || !dists) return KNNG_ERR_INVALID_ARG;
-    if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16) return KNNG_ERR_INVALID_ARG;
+    if (dtype != KNNG_DTYPE_F32 && dtype != KNNG_DTYPE_F16 && dtype != KNNG_DTYPE_U8) return KNNG_ERR_INVALID_ARG;
     if (n < 2 || d < 1 || d > 4096 || ld < d || ld >= (int64_t)1 << 31 || k < 1 || k > kMaxK) return KNNG_ERR_INVALID_ARG;
     if (rounds < 1 || rounds > 16) return KNNG_ERR_INVALID_ARG;
     if (n > kNoAllocMaxPoints || n * (int64_t)k > kNoAllocMaxEntries) return KNNG_ERR_LIMIT;
@@ -74,8 +76,8 @@ extern "C" int knng_propagate_noalloc(const void* X, int32_t dtype, int64_t n, i
     if (r != KNNG_OK) return r;
 
     XDesc x;
-    const size_t es = dtype == KNNG_DTYPE_F16 ? 2 : 4;
-    const size_t align = dtype == KNNG_DTYPE_F16 ? 8 : 16;
+    const size_t es = dtype == KNNG_DTYPE_F16 ? 2 : dtype == KNNG_DTYPE_U8 ? 1 : 4;
+    const size_t align = dtype == KNNG_DTYPE_F16 ? 8 : dtype == KNNG_DTYPE_U8 ? 4 : 16;
     x.X = X;
     x.dtype = dtype;
     x.n = n;

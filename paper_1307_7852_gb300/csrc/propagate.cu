@@ -350,13 +350,12 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
     if (warps > 8) warps = 8;
     if (warps < 1) return cudaErrorInvalidConfiguration;
     const size_t smem = PL.per_warp * warps;
-    // the build's first round (masks, no flags) / a later first-order round
-    // (flags) / anything else
-    // (flags) / anything else; lists of more than 32 take the general one
-    auto kern = E > 1                       ? propagate_kernel<E, kDT, 0>
-                : (tm && !fin && !po.tgt)  ? propagate_kernel<E, kDT, (E > 1 ? 0 : 1)>
-                : (fin && !tm && !po.tgt)  ? propagate_kernel<E, kDT, (E > 1 ? 0 : 2)>
-                                           : propagate_kernel<E, kDT, 0>;
+    // the build's first round (tree masks, no flags), a later first-order
+    // round (flags), or the general form (pairwise offers, optional flags)
+    const int mode = (tm && !fin && !po.tgt) ? 1 : (fin && !tm && !po.tgt) ? 2 : 0;
+    auto kern = mode == 1 ? propagate_kernel<E, kDT, 1>
+              : mode == 2 ? propagate_kernel<E, kDT, 2>
+                          : propagate_kernel<E, kDT, 0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -42,11 +42,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait for the phase with the given parity to complete.  Gives up
-// after `limit_cycles` SM clock cycles and returns false.
+// after `limit_cycles` SM clock cycles and returns false.  try_wait may
+// suspend the thread until the phase completes, so limits below
+// kPollBelow cycles poll with the non-blocking test instead: a phase still
+// open after such a limit is then always reported as a give-up.
+constexpr long long kPollBelow = 1000000;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit_cycles)
 {
     const long long t0 = clock64();
+    if (limit_cycles < kPollBelow) {
+        while (!mbar_test_wait(bar, parity)) {
+            if (clock64() - t0 > limit_cycles) return false;
+        }
+        return true;
+    }
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > limit_cycles) return false;
     }

@@ -27,14 +27,21 @@ def _graph(X, k, T, g, seed):
     return Xd, mi, md
 
 
-@pytest.mark.parametrize("maker,k,rounds", [
-    (lambda: synthetic.sift_like(20000, 64, centers=32, seed=41), 10, 3),
-    (lambda: synthetic.gist_like(12000, 100, centers=16, seed=42), 16, 2),
+@pytest.mark.parametrize("maker,k,rounds,g", [
+    (lambda: synthetic.sift_like(20000, 64, centers=32, seed=41), 10, 3, 64),
+    (lambda: synthetic.gist_like(12000, 100, centers=16, seed=42), 16, 2, 64),
+    # lists of more than 32 (the two-keys-per-lane kernel; flags of entries
+    # 32..63 kept in the array between rounds), n * k near the capacity
+    (lambda: synthetic.sift_like(12000, 48, centers=24, seed=43), 40, 3, 128),
+    # one round: the input goes straight to the output, no scratch used
+    (lambda: synthetic.gist_like(8000, 64, centers=16, seed=44), 12, 1, 64),
+    # byte rows
+    (lambda: synthetic.sift_like(15000, 32, centers=16, seed=45).astype(np.uint8), 12, 2, 64),
 ])
-def test_noalloc_matches_allocating_entry_point(maker, k, rounds):
+def test_noalloc_matches_allocating_entry_point(maker, k, rounds, g):
     import paper_1307_7852_gb300 as knng
     X = maker()
-    Xd, mi, md = _graph(X, k, 3, 64, 5)
+    Xd, mi, md = _graph(X, k, 3, g, 5)
     ri, rd = knng.knng_propagate(Xd, mi, md, rounds)
     torch.cuda.synchronize()
     ref_i, ref_d = ri.cpu().numpy(), rd.cpu().numpy()
