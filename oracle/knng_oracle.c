@@ -596,31 +596,40 @@ int orc_propagate_rows(const float* X, int64_t n, int d, int64_t ld, int k, cons
 }
 
 /* ------------------------------------------------------------------------ */
-/* Canonical FP32 squared distance: the 32-lane order of orc_project with    */
-/* t_j = x_j - y_j in place of the product, s_l = fmaf(t_j, t_j, s_l), then  */
-/* the five pairwise rounds.  Used where an FP32 distance decides an order   */
-/* (the best-first queue below), so that the decision is the kernel's.       */
+/* Canonical FP32 squared distance (a reading: the paper fixes no FP32      */
+/* arithmetic).  The entries are cut into blocks of 32, b = 0, 1, ...; in   */
+/* block b, partial q (0..7) sums s_q = fmaf(t_j, t_j, s_q) over            */
+/* j = 32b + 4q + e, e = 0..3 (entries past d contribute nothing), with     */
+/* t_j = x_j - y_j; the block's value is                                    */
+/*     B_b = ((s_0 + s_4) + (s_2 + s_6)) + ((s_1 + s_5) + (s_3 + s_7)),     */
+/* and the distance is B_0 + B_1 + B_2 + ... added in block order.  Every   */
+/* term is non-negative, so the relative error is at most                   */
+/* (4 + 3 + ceil(d/32) + 1) units of 2^-24 (the last for the difference):   */
+/* 2.3e-6 at d = 960, 8.1e-6 at d = 4096.  It is symmetric in x and y and   */
+/* exact on integer rows whose squared distances stay below 2^24.  Used     */
+/* where an FP32 distance decides an order (the best-first queue below),    */
+/* so that the decision is the kernel's.                                    */
 /* ------------------------------------------------------------------------ */
 float orc_canon_dist32(const float* x, const float* y, int d)
 {
-    float s[32];
-    for (int l = 0; l < 32; ++l) s[l] = 0.0f;
-    int nchunks = (d + 127) / 128;
-    for (int l = 0; l < 32; ++l)
-        for (int c = 0; c < nchunks; ++c)
+    const int nblocks = (d + 31) / 32;
+    float total = 0.0f;
+    for (int b = 0; b < nblocks; ++b) {
+        float s[8];
+        for (int q = 0; q < 8; ++q) {
+            s[q] = 0.0f;
             for (int e = 0; e < 4; ++e) {
-                int j = 128 * c + 4 * l + e;
+                const int j = 32 * b + 4 * q + e;
                 if (j < d) {
-                    float t = x[j] - y[j];
-                    s[l] = fmaf(t, t, s[l]);
+                    const float t = x[j] - y[j];
+                    s[q] = fmaf(t, t, s[q]);
                 }
             }
-    for (int o = 16; o >= 1; o >>= 1) {
-        float nxt[32];
-        for (int l = 0; l < 32; ++l) nxt[l] = s[l] + s[l ^ o];
-        for (int l = 0; l < 32; ++l) s[l] = nxt[l];
+        }
+        const float blk = ((s[0] + s[4]) + (s[2] + s[6])) + ((s[1] + s[5]) + (s[3] + s[7]));
+        total = b == 0 ? blk : total + blk;
     }
-    return s[0];
+    return total;
 }
 
 /* ------------------------------------------------------------------------ */

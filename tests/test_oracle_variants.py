@@ -9,6 +9,7 @@ gets worse, every pairwise offer is honoured, and r_m is 1 for the first
 division and 0 once a division adds nothing.
 """
 import numpy as np
+import pytest
 
 import oracle
 from paper_1307_7852_gb300 import synthetic
@@ -25,6 +26,53 @@ def test_canon_dist32_is_the_fp32_distance_of_integers():
     for a, b in [(0, 1), (5, 9), (7, 7)]:
         want = float(np.sum((X[a].astype(np.float64) - X[b]) ** 2))
         assert float(oracle.canon_dist32(X[a], X[b])) == want  # integers < 2^24: exact
+
+
+@pytest.mark.parametrize("d", [1, 3, 31, 32, 33, 100, 128, 960, 4096])
+def test_canon_dist32_error_bound_and_symmetry(d):
+    # relative error at most (4 fmaf + 3 butterfly + ceil(d/32) block
+    # additions + 1 difference) units of 2^-24 against the FP64 distance of
+    # the same FP32 rows
+    rng = np.random.default_rng(d)
+    bound = (8 + -(-d // 32)) * 2.0 ** -24
+    for _ in range(20):
+        x = rng.normal(size=d).astype(np.float32)
+        y = (x + rng.normal(size=d) * rng.choice([1e-3, 0.1, 3.0])).astype(np.float32)
+        want = float(np.sum((x.astype(np.float64) - y) ** 2))
+        got = float(oracle.canon_dist32(x, y))
+        assert abs(got - want) <= bound * want
+        assert oracle.canon_dist32(y, x) == oracle.canon_dist32(x, y)
+
+
+def test_canon_dist32_reads_every_entry():
+    # a single differing entry t = 2^-3 at any position of a ragged row gives
+    # exactly t^2 (an index that skips or repeats an entry fails)
+    d = 100
+    x = np.zeros(d, dtype=np.float32)
+    for j in range(d):
+        y = x.copy()
+        y[j] = 0.125
+        assert float(oracle.canon_dist32(x, y)) == 0.015625
+
+
+def test_canon_dist32_block_order():
+    # values that round differently under different summation orders:
+    # t^2 = 1 and two terms of 2^-24 (half a unit of 1.0, ties to even)
+    e = 2.0 ** -12
+    # within a block the partials pair as (s_q, s_q+4) first: 2^-24 in s_0 and
+    # 1 in s_4 give 1 + 2^-24 = 1 (tie), then + (s_1 + s_5) = 2^-24 -> 1;
+    # a plain left-to-right sum would give 1 + 2^-23
+    x = np.zeros(32, dtype=np.float32)
+    y = x.copy()
+    y[0], y[4], y[16] = e, e, 1.0
+    assert float(oracle.canon_dist32(x, y)) == 1.0
+    # across blocks the values are added in block order: 2^-24 (block 0),
+    # 2^-24 (block 1), then 1 (block 2) gives 2^-23 + 1 exactly; a butterfly
+    # over all 32-entry slices (the 1 meets the first 2^-24) would give 1
+    x = np.zeros(96, dtype=np.float32)
+    y = x.copy()
+    y[0], y[32], y[64] = e, e, 1.0
+    assert float(oracle.canon_dist32(x, y)) == 1.0 + 2.0 ** -23
 
 
 def test_best_first_budget_k_keeps_the_own_list():
