@@ -44,11 +44,15 @@ WORKLOADS = {
 }
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
 PROPAGATION = {"first_order": 0, "best_first": 1, "pairwise": 2}
-# DRAM bytes (read + write) per point of one launch, from ncu captures of the
-# current kernels on the 400k-point case of the sift1m configuration (leaf:
-# per point and tree; propagation: per point and round).
-TRAFFIC = {("sift1m", "bf16"): {"leaf_knn": (948.755968e6 + 560.620288e6) / (400_000 * 8),
-                                "propagate": (269.010944e6 + 69.613056e6 + 221.221632e6 + 61.197824e6) / 2 / 400_000}}
+# Small cases of the workloads for DRAM-traffic captures (ncu): the same
+# method parameters and data law, fewer points (inputs still larger than L2).
+PROFILE_CASE = {"sift1m": dict(n=400_000, centers=410), "gist1m": dict(n=60_000, centers=256),
+                "sift400k": dict(n=400_000, centers=410)}
+# kernels whose DRAM bytes are recorded, and the unit each is scaled by
+TRAFFIC_KERNELS = {"propagate_kernel": "point-round", "leaf_tc_kernel": "point-tree",
+                   "leaf_rescore_staged_kernel": "point-tree", "gather_quant_kernel": "point-tree",
+                   "merge_kernel": "point", "project_bytes_tma_kernel": "point-tree-level",
+                   "project_kernel": "point-level"}
 METRIC = "points/sec to build the k-NN graph (recall@k reported on a 10k-point sample)"
 
 
@@ -72,6 +76,84 @@ def aggregate(elapsed_s: float, points_per_rank: int, world: int, dist=None, dev
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         el = float(t.item())
     return el, points_per_rank * world / el
+
+
+# ------------------------------------------------------------ DRAM traffic
+def source_hash() -> str:
+    """Hash of the CUDA sources: a recorded traffic figure holds only for the
+    kernels it was measured on."""
+    import glob
+    import hashlib
+    hh = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1307_7852_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                    glob.glob(os.path.join(csrc, "*.h"))):
+        with open(f, "rb") as fh:
+            hh.update(os.path.basename(f).encode())
+            hh.update(fh.read())
+    return hh.hexdigest()[:16]
+
+
+def traffic_path(workload, precision):
+    return os.path.join(ROOT, "profiles", f"dram_traffic_{workload}_{precision}.json")
+
+
+def load_traffic(workload, precision):
+    """Per-unit DRAM bytes of the kernels, from a capture of the current
+    sources (None when the sources changed since or nothing was captured)."""
+    try:
+        with open(traffic_path(workload, precision)) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    return rec if rec.get("source_hash") == source_hash() else None
+
+
+def traffic_from_csv(args, w):
+    """Writes the per-unit DRAM bytes of an ncu launch list (--metrics
+    dram__bytes_read.sum,dram__bytes_write.sum, --csv) of `bench.py
+    --profile-case` to profiles/dram_traffic_<workload>_<precision>.json."""
+    import csv
+    case = PROFILE_CASE[args.workload]
+    n, T, R = case["n"], w["T"], w["R"]
+    launches = {}
+    order = []
+    with open(args.traffic_from) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        name = row.get("Kernel Name", "")
+        base = name.split("(")[0].split("<")[0].split("::")[-1].strip()
+        if base not in TRAFFIC_KERNELS:
+            continue
+        key = row["ID"]
+        if key not in launches:
+            launches[key] = {"kernel": base, "bytes": 0.0}
+            order.append(key)
+        unit = row.get("Metric Unit", "byte").lower()
+        scale = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}.get(unit, 1)
+        if row["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            launches[key]["bytes"] += float(row["Metric Value"].replace(",", "")) * scale
+    per = {}
+    for key in order:
+        per.setdefault(launches[key]["kernel"], []).append(launches[key]["bytes"])
+    out = {}
+    for kname, vals in per.items():
+        unit = TRAFFIC_KERNELS[kname]
+        if unit == "point-round":
+            out[kname] = {"unit": unit, "bytes_per_unit": [v / n for v in vals[-R:]]}
+        elif unit == "point-tree":
+            out[kname] = {"unit": unit, "bytes_per_unit": sum(vals) / (n * T)}
+        elif unit == "point":
+            out[kname] = {"unit": unit, "bytes_per_unit": sum(vals) / n}
+        else:
+            out[kname] = {"unit": "point-build", "bytes_per_unit": sum(vals) / n}
+    rec = {"workload": args.workload, "precision": args.precision, "source_hash": source_hash(),
+           "case": {"n": n, **{k_: w[k_] for k_ in ("d", "k", "T", "g", "R")}, "centers": case["centers"]},
+           "command": args.traffic_command or "", "per_unit": out}
+    with open(traffic_path(args.workload, args.precision), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+    return 0
 
 
 # ------------------------------------------------------------------ clocks
@@ -382,6 +464,12 @@ def main():
     ap.add_argument("--r-stop", type=float, default=0.0, help="> 0: divisions until r_m < r_stop (at most T)")
     ap.add_argument("--metric-kind", choices=["l2", "cosine"], default="l2")
     ap.add_argument("--partitioner", choices=["random", "pca"], default="random")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one build of the workload's small profiling case (for an ncu launch list), then exit")
+    ap.add_argument("--traffic-from", default=None,
+                    help="ncu --csv launch list of --profile-case with dram__bytes_{read,write}.sum: record the "
+                         "kernels' DRAM bytes per unit under profiles/ and exit")
+    ap.add_argument("--traffic-command", default=None, help="the ncu command line, recorded with the traffic")
     args = ap.parse_args()
     if args.workload in ("batched256", "learned10m"):
         if args.impl == "reference":
@@ -405,6 +493,17 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, w, rank)
+    if args.traffic_from:
+        return traffic_from_csv(args, w)
+    if args.profile_case:
+        import torch
+        import paper_1307_7852_gb300 as knng
+        case = PROFILE_CASE[args.workload]
+        wc = dict(w, n=case["n"], centers=case["centers"])
+        Xc = torch.from_numpy(make_data(wc, seed=args.data_seed)).cuda()
+        knng.knng_build(Xc, w["k"], w["T"], w["g"], w["R"], args.seed, PRECISIONS[args.precision], 2)
+        torch.cuda.synchronize()
+        return 0
 
     import torch
     import paper_1307_7852_gb300 as knng
@@ -483,67 +582,109 @@ def main():
 
     if not args.no_extras and rank == 0:
         hbm, bf16, sm_mhz, src = peaks()
-        # ---- per-stage roofline figures (algorithmic work / measured time)
         off = knng.knng_leaf_offsets(n, g)
         m = np.diff(off).astype(np.float64)
-        perm = knng.knng_partition(Xd, T, g, args.seed, h=h)
-        li, ld_ = knng.knng_leaf_knn(Xd, T, g, perm, k, prec, 2, h=h)
-        mi, md = knng.knng_merge(li, ld_, h=h)
-        graphs = [mi]
-        cur_i, cur_d = mi, md
-        for _ in range(R):
-            cur_i, cur_d = knng.knng_propagate(Xd, cur_i, cur_d, 1, h=h)
-            graphs.append(cur_i)
-        torch.cuda.synchronize()
-        rng = np.random.default_rng(7)
-        samp = rng.choice(n, size=min(n, 20000), replace=False)
-        u = [unique_candidates(gph.cpu().numpy(), samp) for gph in graphs[:R]]
-        del perm, li, ld_, graphs
-        # bytes per row entry the propagation reads: float rows holding only
-        # bytes (d <= 256) are read from their exact byte copy
+        depth = knng.knng_split_levels(n, g)
+        # bytes per row entry the gathers read: float rows holding only bytes
+        # (d <= 256) are read from their exact byte copy
         byte_rows = X.dtype == np.float32 and d <= 256 and args.metric_kind == "l2" and bool(
             np.all((X >= 0) & (X <= 255) & (X == np.rint(X))))
         s_el = 1 if byte_rows else X.itemsize
+        traffic = load_traffic(args.workload if args.workload != "sift400k" else "sift1m", args.precision)
+        tr = (traffic or {}).get("per_unit", {})
+        plain = args.propagation == "first_order" and args.partitioner == "random" and args.metric_kind == "l2"
         roof = {}
-        if R > 0:
-            if args.propagation == "best_first":
-                # every visit reads one row and one list slot
-                per_launch = [n * (args.budget * (d * s_el + 4) + 2 * k * 8 + d * s_el) for _ in u]
-            else:
-                per_launch = [n * (k * k * 4 + u_r * d * s_el + 2 * k * 8 + d * s_el) for u_r in u]
+        # ---- propagation: what the build's rounds read, counted on the device
+        # (one more, untimed build with the read counters on), next to the
+        # survey's count k^2*4 + u*d*s + k*8 per point (u measured on a
+        # sample of the graphs the rounds start from)
+        if R > 0 and args.propagation == "first_order":
+            cnt = torch.zeros(2 * R, dtype=torch.int64, device=dev)
+            knng.knng_set_propagation_counters(cnt, h)
+            step()
+            torch.cuda.synchronize()
+            knng.knng_set_propagation_counters(None, h)
+            counts = cnt.cpu().numpy().reshape(R, 2)
+            perm = knng.knng_partition(Xd, T, g, args.seed, h=h)
+            li, ld_ = knng.knng_leaf_knn(Xd, T, g, perm, k, prec, 2, h=h)
+            cur_i, cur_d = knng.knng_merge(li, ld_, h=h)
+            del perm, li, ld_
+            rng = np.random.default_rng(7)
+            samp = rng.choice(n, size=min(n, 20000), replace=False)
+            u = []
+            for r in range(R):
+                u.append(unique_candidates(cur_i.cpu().numpy(), samp))
+                if r + 1 < R:
+                    cur_i, cur_d = knng.knng_propagate(Xd, cur_i, cur_d, 1, h=h)
+            del cur_i, cur_d
             t_prop = [stage_ms[f"propagate_r{r}"] / 1e3 for r in range(R)]
-            ach = sum(per_launch) / sum(t_prop) / 1e9
-            roof["propagate"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                                 "frac": ach / hbm, "traffic": None,
-                                 "algorithmic_bytes_per_launch": statistics.mean(per_launch),
-                                 "unique_candidates_per_point": u, "ms": sum(t_prop) * 1e3 / R}
+            survey = [n * (k * k * 4 + u[r] * d * s_el + k * 8) for r in range(R)]
+            # rows scored and list slots loaded, plus every point's own list,
+            # row and output
+            scored = [int(counts[r, 0]) * d * s_el + int(counts[r, 1]) * 4 + n * (2 * k * 8 + d * s_el)
+                      for r in range(R)]
+            dram = None
+            if traffic and plain and "propagate_kernel" in tr:
+                per = tr["propagate_kernel"]["bytes_per_unit"]
+                if len(per) == R:
+                    dram = [b * n for b in per]
+            ach = sum(scored) / sum(t_prop) / 1e9
+            roof["propagate"] = {
+                "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": statistics.mean(dram) if dram else None,
+                "scored_bytes": statistics.mean(scored), "survey_bytes": statistics.mean(survey),
+                "dram_bytes": statistics.mean(dram) if dram else None,
+                "survey_achieved": sum(survey) / sum(t_prop) / 1e9,
+                "rows_scored_per_point": [float(counts[r, 0]) / n for r in range(R)],
+                "list_slots_per_point": [float(counts[r, 1]) / n for r in range(R)],
+                "unique_candidates_per_point": u, "ms": sum(t_prop) * 1e3 / R,
+                "basis": "achieved = scored_bytes (rows scored and list slots loaded, counted on the device, "
+                         "+ each point's list, row and output) per launch / launch time"}
+        # ---- leaf graphs: Gram flops of the distinct pairs (tensor pipe or
+        # FP32 ALU), and the bytes the stage reads and writes
         gram_flops = T * float(np.sum(2.0 * d * m * (m - 1) / 2.0))
         t_leaf = stage_ms["leaf_knn"] / 1e3
+        leaf_dram = None
+        if traffic and plain:
+            leaf_dram = sum(tr[kn]["bytes_per_unit"] * n * T for kn in
+                            ("leaf_tc_kernel", "leaf_rescore_staged_kernel", "gather_quant_kernel") if kn in tr)
+        ach = gram_flops / t_leaf / 1e12
         if prec == 0:
             alu = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-            ach = gram_flops / t_leaf / 1e12
-            roof["leaf_knn"] = {"bound": "alu", "achieved": ach, "peak": alu, "unit": "TFLOP/s",
-                                "frac": ach / alu, "traffic": None, "algorithmic_flops_per_launch": gram_flops}
+            roof["leaf_knn"] = {"bound": "alu", "achieved": ach, "peak": alu, "unit": "TFLOP/s", "frac": ach / alu,
+                                "traffic": leaf_dram, "algorithmic_flops_per_launch": gram_flops}
         else:
-            ach = gram_flops / t_leaf / 1e12
             roof["leaf_knn"] = {"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                                "frac": ach / bf16, "traffic": None, "algorithmic_flops_per_launch": gram_flops}
+                                "frac": ach / bf16, "traffic": leaf_dram, "algorithmic_flops_per_launch": gram_flops}
+        if leaf_dram:
+            roof["leaf_knn"]["dram_gbs"] = leaf_dram / t_leaf / 1e9
+            roof["leaf_knn"]["dram_frac"] = leaf_dram / t_leaf / 1e9 / hbm
+        # ---- merge: (T + 1) k 8 bytes per point (survey), DRAM measured
         merge_bytes = n * (T + 1) * k * 8
         ach = merge_bytes / (stage_ms["merge"] / 1e3) / 1e9
+        mdram = tr["merge_kernel"]["bytes_per_unit"] * n if (traffic and plain and "merge_kernel" in tr) else None
         roof["merge"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "traffic": None, "algorithmic_bytes_per_launch": merge_bytes}
-        # DRAM traffic per launch from the ncu captures of the current kernels
-        # (profiles/leaf_tc_propagate_sift400k.md: 400k points, scaled by the
-        # points a launch processes); other configurations have no capture
-        cap = TRAFFIC.get((args.workload if args.workload != "sift400k" else "sift1m", args.precision))
-        if cap and args.propagation == "first_order" and args.partitioner == "random" and args.metric_kind == "l2":
-            roof["leaf_knn"]["traffic"] = cap["leaf_knn"] * n * T
-            if "propagate" in roof:
-                roof["propagate"]["traffic"] = cap["propagate"] * n
+                         "traffic": mdram, "algorithmic_bytes_per_launch": merge_bytes}
+        # ---- partition: the survey's depth * n * d * s per tree plus 16 bytes
+        # of keys and permutation per point and level; the rows the kernels
+        # read: byte rows once per tree and level (node-major), float rows
+        # once per level for all trees (point-major)
+        part_survey = T * depth * (n * d * s_el + 16 * n)
+        rows_read = depth * n * d * s_el * (T if byte_rows else 1)
+        part_read = rows_read + T * depth * 16 * n
+        t_part = stage_ms["partition"] / 1e3
+        roof["partition"] = {"bound": "hbm", "achieved": part_read / t_part / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": part_read / t_part / 1e9 / hbm, "traffic": None,
+                             "read_bytes": part_read, "survey_bytes": part_survey,
+                             "survey_achieved": part_survey / t_part / 1e9, "levels": depth}
+        if traffic:
+            roof["dram_capture"] = {"source_hash": traffic["source_hash"], "case": traffic["case"],
+                                    "command": traffic.get("command", "")}
         # the kernel that takes the most time in a step carries the headline
         # roofline object (its figures are per launch)
-        stage_of = {"leaf_knn": stage_ms["leaf_knn"], "merge": stage_ms["merge"]}
-        if R > 0:
+        stage_of = {"leaf_knn": stage_ms["leaf_knn"], "merge": stage_ms["merge"],
+                    "partition": stage_ms["partition"]}
+        if "propagate" in roof:
             stage_of["propagate"] = sum(stage_ms[f"propagate_r{r}"] for r in range(R))
         dom = max(stage_of, key=stage_of.get)
         line["roofline"] = dict(roof[dom], kernel=dom, peak_source=src)
@@ -551,7 +692,6 @@ def main():
 
         # ---- recall on a sample against exact brute force (GPU, same FP32 distance)
         if not args.no_recall:
-            import oracle  # noqa: F401  (recall helpers only; exact lists from the GPU kernel)
             from paper_1307_7852_gb300 import synthetic
             q = synthetic.sample_ids(n, args.recall_sample, args.seed + 1)
             qd = torch.from_numpy(q).to(dev)

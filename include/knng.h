@@ -141,6 +141,17 @@ int knng_sync(knng_handle* h, void* stream);
  * KNNG_ERR_INVALID_ARG.  No counterpart in the paper. */
 int knng_set_wait_limit(knng_handle* h, int64_t cycles);
 
+/* Counters of what the first-order propagation rounds read (Sec. 3.2;
+ * measurement of the rounds' real traffic, with the exact skips of pairs
+ * that cannot enter a list).  counters: device array of 2 * rounds uint64,
+ * zeroed by the caller; while set, round r < rounds of every later
+ * knng_build / knng_propagate call on h adds to counters[2r] the candidate
+ * rows it scored and to counters[2r + 1] the slots of neighbours' lists it
+ * loaded.  rounds = 0 (or counters NULL with rounds 0) turns counting off,
+ * the default; counting adds one atomic per warp.  The array must outlive
+ * the calls that use it.  No counterpart in the paper. */
+int knng_set_propagation_counters(knng_handle* h, uint64_t* counters, int32_t rounds);
+
 /* ---- tree shape (host only) ------------------------------------------ */
 /* Every split halves a node of m points into floor(m/2) (left) and
  * ceil(m/2) (right) points, so the leaf layout of a tree depends on (n, g)

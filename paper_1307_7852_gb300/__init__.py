@@ -12,4 +12,4 @@ from .binding import (  # noqa: F401
     knng_exact_knn, knng_launch_counter, knng_leaf_count, knng_leaf_knn, knng_leaf_offsets, knng_merge,
     knng_mlp_forward, knng_normalize_rows, knng_partition, knng_partition_learned, knng_partition_pca, knng_split_levels, knng_propagate, knng_propagate_best_first, knng_propagate_noalloc,
     knng_propagate_pairwise,
-    knng_set_stage_events, knng_set_wait_limit, knng_sync, knng_tune_load, knng_tune_save, lib)
+    knng_set_propagation_counters, knng_set_stage_events, knng_set_wait_limit, knng_sync, knng_tune_load, knng_tune_save, lib)

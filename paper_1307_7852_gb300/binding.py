@@ -76,6 +76,7 @@ SIGNATURES = {
     "knng_launch_counter": [ctypes.POINTER(ctypes.c_uint64)],
     "knng_sync": [_P, _P],
     "knng_set_wait_limit": [_P, _I64],
+    "knng_set_propagation_counters": [_P, _P, _I32],
     "knng_autotune": [_P, _P, _I32, _I64, _I32, _I64, ctypes.POINTER(knng_params), _P, _P, _P, _P],
     "knng_tune_save": [_P, ctypes.c_char_p],
     "knng_tune_load": [_P, ctypes.c_char_p],
@@ -430,6 +431,17 @@ def knng_set_wait_limit(cycles: int, h: Handle):
     """Limit (SM cycles, 0 = about one second) of the tensor-core leaf
     kernel's pipeline waits for later calls on h."""
     h.check(lib().knng_set_wait_limit(h.ptr, int(cycles)), "knng_set_wait_limit")
+
+
+def knng_set_propagation_counters(counters, h: Handle):
+    """counters: CUDA int64 tensor of 2 * rounds zeros (rows scored, list
+    slots loaded per first-order round of later calls on h), or None."""
+    if counters is None:
+        h.check(lib().knng_set_propagation_counters(h.ptr, None, 0), "knng_set_propagation_counters")
+        return
+    assert counters.numel() % 2 == 0
+    h.check(lib().knng_set_propagation_counters(h.ptr, _ptr(counters), int(counters.numel() // 2)),
+            "knng_set_propagation_counters")
 
 
 def knng_launch_counter() -> int:

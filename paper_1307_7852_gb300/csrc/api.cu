@@ -71,6 +71,8 @@ struct knng_handle {
     char* staging = nullptr;     // device copies of knng_build_host's buffers (grow-only)
     size_t staging_size = 0;
     long long wait_cycles = 0;   // limit of the leaf kernel's pipeline waits (0: about 1 s)
+    unsigned long long* prop_stats = nullptr;  // caller's read counters, 2 per round
+    int prop_stats_rounds = 0;
 };
 
 namespace {
@@ -430,7 +432,8 @@ int build_pipeline(knng_handle* h, const TreePlan& P, const DevPlan& dp, const X
         else if (p.propagation == KNNG_PROP_PAIRWISE)
             e = run_propagate_pairwise(x, k, perm, si, sd, sf, oi, od, of, pw, h->dev_err, st);
         else
-            e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st, nullptr, rd == 0 ? tmask : nullptr);
+            e = run_propagate(x, k, perm, si, sd, sf, oi, od, of, st, nullptr, rd == 0 ? tmask : nullptr,
+                              rd < h->prop_stats_rounds ? h->prop_stats + 2 * rd : nullptr);
         if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
         cur ^= 1;
         mark(4 + rd);
@@ -664,7 +667,8 @@ int knng_propagate(knng_handle* h, const void* X, int32_t dtype, int64_t n, int3
         int32_t* oi = last ? ids : bi[rd & 1];
         float* od = last ? dists : bd[rd & 1];
         unsigned long long* of = last ? nullptr : fl[rd & 1];
-        cudaError_t e = run_propagate(x, k, nullptr, si, sd, sf, oi, od, of, st);
+        cudaError_t e = run_propagate(x, k, nullptr, si, sd, sf, oi, od, of, st, nullptr, nullptr,
+                                      rd < h->prop_stats_rounds ? h->prop_stats + 2 * rd : nullptr);
         if (e != cudaSuccess) return cuda_fail(h, e, "propagate");
         si = oi;
         sd = od;
@@ -832,6 +836,15 @@ int knng_sync(knng_handle* h, void* stream)
                                            "the lists are valid but some offers were dropped");
         return fail(h, KNNG_ERR_TIMEOUT, "a bounded device wait gave up; results of the affected calls are invalid");
     }
+    return KNNG_OK;
+}
+
+int knng_set_propagation_counters(knng_handle* h, uint64_t* counters, int32_t rounds)
+{
+    if (!h) return KNNG_ERR_INVALID_ARG;
+    if (rounds < 0 || (rounds > 0 && !counters)) return fail(h, KNNG_ERR_INVALID_ARG, "bad counters");
+    h->prop_stats = rounds > 0 ? reinterpret_cast<unsigned long long*>(counters) : nullptr;
+    h->prop_stats_rounds = rounds;
     return KNNG_OK;
 }
 

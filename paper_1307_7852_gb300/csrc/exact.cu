@@ -61,19 +61,26 @@ __global__ void __launch_bounds__(kQB * 32) exact_knn_kernel(RowLoader<kDT> L, i
         unsigned long long mine = kKeyMax;
         const int rows = (n - j0) < 32 ? (int)(n - j0) : 32;
         for (int r = 0; r < rows; ++r) {
-            float s = 0.f;
-            for (int j = 4 * lane; j < L.d; j += 128) {
-                const float4 a = *reinterpret_cast<const float4*>(qrow + w * dp + j);
-                const float4 b = *reinterpret_cast<const float4*>(tile + r * dp + j);
-                float t;
-                t = a.x - b.x; s = fmaf(t, t, s);
-                t = a.y - b.y; s = fmaf(t, t, s);
-                t = a.z - b.z; s = fmaf(t, t, s);
-                t = a.w - b.w; s = fmaf(t, t, s);
+            // the canonical distance (blocks of 32 entries added in order)
+            float tot = 0.f;
+            for (int c0 = 0; c0 < L.d; c0 += 128) {
+                const int j = c0 + 4 * lane;
+                float s = 0.f;
+                if (j < dp) {
+                    const float4 a = *reinterpret_cast<const float4*>(qrow + w * dp + j);
+                    const float4 b = *reinterpret_cast<const float4*>(tile + r * dp + j);
+                    float t;
+                    t = a.x - b.x; s = fmaf(t, t, s);
+                    t = a.y - b.y; s = fmaf(t, t, s);
+                    t = a.z - b.z; s = fmaf(t, t, s);
+                    t = a.w - b.w; s = fmaf(t, t, s);
+                }
+                s += __shfl_xor_sync(KNNG_FULL_MASK, s, 4);
+                s += __shfl_xor_sync(KNNG_FULL_MASK, s, 2);
+                s += __shfl_xor_sync(KNNG_FULL_MASK, s, 1);
+                tot = chunk_blocks_add(tot, s);
             }
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
-            if (lane == r && j0 + r != q) mine = pack_key(s, (uint32_t)(j0 + r));
+            if (lane == r && j0 + r != q) mine = pack_key(tot, (uint32_t)(j0 + r));
         }
         const bool take = mine < thr;
         const uint32_t b = __ballot_sync(KNNG_FULL_MASK, take);

@@ -161,31 +161,56 @@ struct RowLoader {
 };
 
 // ---------------------------------------------------------------------------
-// Canonical FP32 squared distance between points a and b, computed by a full
-// warp: lane l accumulates s = fmaf(t, t, s), t = x_a[j] - x_b[j], over
-// j = 128c + 4l + e (chunk c ascending, e = 0..3), then pairwise rounds at
-// offsets 16, 8, 4, 2, 1.  Every lane returns the same value, and the value
-// depends only on the two rows (so D(a, b) == D(b, a) bit for bit).
+// Canonical FP32 squared distance.  The entries are cut into blocks of 32:
+// in block b, partial q = 0..7 sums s_q = fmaf(t, t, s_q), t = x_a[j] - x_b[j],
+// over j = 32b + 4q + e (e = 0..3); the block's value is the xor butterfly of
+// its eight partials, B_b = ((s0 + s4) + (s2 + s6)) + ((s1 + s5) + (s3 + s7)),
+// and the distance adds B_0, B_1, ... in block order.  Every term is
+// non-negative, so the relative error stays below (8 + ceil(d/32)) * 2^-24
+// (8.1e-6 at d = 4096), and the value depends only on the two rows, so
+// D(a, b) == D(b, a) bit for bit.  Because each block is closed before the
+// next, a kernel can stream the rows in 32-entry slices and keep one running
+// sum per pair.
+//
+// The warp form: lane l holds entries 128c + 4l .. +3 of 128-entry chunk c,
+// which are partial l & 7 of block 4c + (l >> 3); a butterfly over the eight
+// lanes of each group closes the four blocks, and their values are added in
+// order.  Entries past d load as 0 and add nothing (fmaf(0, 0, s) = s, and a
+// block of zeros adds +0).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float chunk_blocks_add(float tot, float blk)
+{
+    // blk: lane group g holds block 4c + g; add the four in block order
+    const float b0 = __shfl_sync(KNNG_FULL_MASK, blk, 0);
+    const float b1 = __shfl_sync(KNNG_FULL_MASK, blk, 8);
+    const float b2 = __shfl_sync(KNNG_FULL_MASK, blk, 16);
+    const float b3 = __shfl_sync(KNNG_FULL_MASK, blk, 24);
+    return (((tot + b0) + b1) + b2) + b3;
+}
+
 template <int kDT>
 __device__ __forceinline__ float warp_canon_dist(const RowLoader<kDT>& L, int64_t a, int64_t b)
 {
     const int lane = threadIdx.x & 31;
-    float s = 0.0f;
-    for (int j = 4 * lane; j < L.d; j += 128) {
-        const float4 xa = L.load4(a, j), xb = L.load4(b, j);
-        float t;
-        t = xa.x - xb.x; s = fmaf(t, t, s);
-        t = xa.y - xb.y; s = fmaf(t, t, s);
-        t = xa.z - xb.z; s = fmaf(t, t, s);
-        t = xa.w - xb.w; s = fmaf(t, t, s);
+    float tot = 0.0f;
+    for (int j0 = 0; j0 < L.d; j0 += 128) {
+        const int j = j0 + 4 * lane;
+        float s = 0.0f;
+        if (j < L.d) {
+            const float4 xa = L.load4(a, j), xb = L.load4(b, j);
+            float t;
+            t = xa.x - xb.x; s = fmaf(t, t, s);
+            t = xa.y - xb.y; s = fmaf(t, t, s);
+            t = xa.z - xb.z; s = fmaf(t, t, s);
+            t = xa.w - xb.w; s = fmaf(t, t, s);
+        }
+        s += __shfl_xor_sync(KNNG_FULL_MASK, s, 4);
+        s += __shfl_xor_sync(KNNG_FULL_MASK, s, 2);
+        s += __shfl_xor_sync(KNNG_FULL_MASK, s, 1);
+        tot = chunk_blocks_add(tot, s);
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(KNNG_FULL_MASK, s, o);
-    return s;
+    return tot;
 }
-// Note: for entries past d both loads return 0, so t = 0 and fmaf(0,0,s) = s
-// (s >= +0 never becomes -0), leaving the partial sums unchanged.
 
 // ---------------------------------------------------------------------------
 // Warp bitonic sort of 32*E 64-bit keys, E per lane; element index
@@ -502,56 +527,84 @@ __device__ int warp_topk_sorted(const KeyFn& key, int cnt, int want, uint64_t* o
 // Canonical distances from point a to W points b[0..W) (W = 8, 16 or 32;
 // b in shared memory, entries c >= nb unused); lane l returns the distance to
 // b[l % W] (for l % W < nb).  Rows must be vector-aligned with d % 4 == 0.
-// Each lane first forms its partial sums (entries j = 128c' + 4l + e, fmaf)
-// for the W points; then, for offsets o = 16, 8, 4, 2, 1, the partials of
-// lanes l and l^o are added -- for o >= W as a plain butterfly on all W
-// values, for o < W by recursive halving (each lane keeps half of its values
-// and receives its partner's copy of them).  These are the pairwise additions
-// of the xor butterfly in warp_canon_dist, so the result is bit-identical to
-// it, with far fewer shuffles and W row loads in flight.
+// Per 128-entry chunk each lane forms its partials (entries 128c + 4l + e,
+// fmaf) for the W points; recursive halving over the eight lanes of each
+// group (offsets 4, 2, 1: each lane keeps half of its values and receives
+// its partner's copy of them) performs the additions of the block butterfly
+// and leaves lane l with the block values of points (W/8)(l & 7) + i,
+// i < W/8, for block 4c + (l >> 3); the four blocks are then added in order
+// to running sums.  Bit-identical to warp_canon_dist, with far fewer
+// shuffles and W row loads in flight.
 template <int W, int kDT>
 __device__ __forceinline__ float warp_canon_dist_batch(const RowLoader<kDT>& L, int64_t a, const int* b, int nb)
 {
+    static_assert(W == 8 || W == 16 || W == 32, "batch of 8, 16 or 32 points");
+    constexpr int V = W / 8;  // values a lane keeps after the halving
     const int lane = threadIdx.x & 31;
+    const int g8 = lane & 7;
     int bid[W];
 #pragma unroll
     for (int c = 0; c < W; ++c) bid[c] = c < nb ? b[c] : (int)a;
-    float p[W];
+    float tot[V];
 #pragma unroll
-    for (int c = 0; c < W; ++c) p[c] = 0.f;
-    for (int j = 4 * lane; j < L.d; j += 128) {
-        const float4 xa = L.load4v(a, j);
+    for (int i = 0; i < V; ++i) tot[i] = 0.f;
+    for (int j0 = 0; j0 < L.d; j0 += 128) {
+        const int j = j0 + 4 * lane;
+        float p[W];
 #pragma unroll
-        for (int c0 = 0; c0 < W; c0 += 8) {
-            float4 xb[8];
+        for (int c = 0; c < W; ++c) p[c] = 0.f;
+        if (j < L.d) {
+            const float4 xa = L.load4v(a, j);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) xb[c] = L.load4v(bid[c0 + c], j);
+            for (int c0 = 0; c0 < W; c0 += 8) {
+                float4 xb[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float t;
-                t = xa.x - xb[c].x; p[c0 + c] = fmaf(t, t, p[c0 + c]);
-                t = xa.y - xb[c].y; p[c0 + c] = fmaf(t, t, p[c0 + c]);
-                t = xa.z - xb[c].z; p[c0 + c] = fmaf(t, t, p[c0 + c]);
-                t = xa.w - xb[c].w; p[c0 + c] = fmaf(t, t, p[c0 + c]);
+                for (int c = 0; c < 8; ++c) xb[c] = L.load4v(bid[c0 + c], j);
+                // points c and c + 1 side by side in packed FP32 pairs (each
+                // half rounds exactly like the scalar operation)
+#pragma unroll
+                for (int c = 0; c < 8; c += 2) {
+                    const float4 u = xb[c], v = xb[c + 1];
+                    float2 acc = make_float2(0.f, 0.f), t;
+                    t = __fadd2_rn(make_float2(xa.x, xa.x), make_float2(-u.x, -v.x)); acc = __ffma2_rn(t, t, acc);
+                    t = __fadd2_rn(make_float2(xa.y, xa.y), make_float2(-u.y, -v.y)); acc = __ffma2_rn(t, t, acc);
+                    t = __fadd2_rn(make_float2(xa.z, xa.z), make_float2(-u.z, -v.z)); acc = __ffma2_rn(t, t, acc);
+                    t = __fadd2_rn(make_float2(xa.w, xa.w), make_float2(-u.w, -v.w)); acc = __ffma2_rn(t, t, acc);
+                    p[c0 + c] = acc.x;
+                    p[c0 + c + 1] = acc.y;
+                }
             }
         }
-    }
+        // recursive halving inside each group of eight lanes
 #pragma unroll
-    for (int o = 16; o >= W; o >>= 1) {
+        for (int o = 4, h = W / 2; o >= 1; o >>= 1, h >>= 1) {
+            const bool hi = (lane & o) != 0;
 #pragma unroll
-        for (int c = 0; c < W; ++c) p[c] += __shfl_xor_sync(KNNG_FULL_MASK, p[c], o);
-    }
+            for (int i = 0; i < h; ++i) {
+                const float send = hi ? p[i] : p[i + h];
+                const float keep = hi ? p[i + h] : p[i];
+                p[i] = keep + __shfl_xor_sync(KNNG_FULL_MASK, send, o);
+            }
+        }
+        // lane (group g, g8) holds block 4c + g of points V * g8 + i
 #pragma unroll
-    for (int o = W / 2; o >= 1; o >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = hi ? p[i] : p[i + o];
-            const float keep = hi ? p[i + o] : p[i];
-            p[i] = keep + __shfl_xor_sync(KNNG_FULL_MASK, send, o);
+        for (int i = 0; i < V; ++i) {
+            const float b0 = __shfl_sync(KNNG_FULL_MASK, p[i], g8);
+            const float b1 = __shfl_sync(KNNG_FULL_MASK, p[i], 8 + g8);
+            const float b2 = __shfl_sync(KNNG_FULL_MASK, p[i], 16 + g8);
+            const float b3 = __shfl_sync(KNNG_FULL_MASK, p[i], 24 + g8);
+            tot[i] = (((tot[i] + b0) + b1) + b2) + b3;
         }
     }
-    return p[0];
+    // point c = lane % W is held as value c % V by the lanes with g8 = c / V
+    const int c = lane % W;
+    float out = 0.f;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const float v = __shfl_sync(KNNG_FULL_MASK, tot[i], c / V);
+        if (c % V == i) out = v;
+    }
+    return out;
 }
 
 // Byte rows with exact integer distances (RowLoader::int_exact): the same
@@ -722,6 +775,22 @@ __device__ void leaf_rescore_list(const RowLoader<kDT>& L, const int32_t* lid, i
 //
 // ws: per-warp shared scratch of kLeafWarpScratch bytes.  m <= 32 * PER.
 constexpr int kLeafWarpScratch = 256 * 4 + 192 * 8;
+
+// The kp (<= 64) best candidates of one row by (D~, local index), as local
+// indices to out[0..min(kp, m - 1)) (collective over one warp; ws as
+// above): the input of the staged FP32 rescoring.
+template <int PER, class DFn>
+__device__ void leaf_row_cands(const DFn& Drow, int m, int self, int kp, unsigned char* ws, uint16_t* out)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(ws + 1024);
+    auto key = [&](int j) -> uint64_t { return j == self ? kKeyMax : pack_key(Drow(j), (uint32_t)j); };
+    const int want = min(kp, m - 1);
+    const int nsel = warp_topk_sorted<PER>(key, m, want, keys, keys + 64, hist);
+    for (int c = lane; c < nsel; c += 32) out[c] = (uint16_t)(uint32_t)keys[c];
+    __syncwarp();
+}
 
 template <int PER, int kDT, class DFn>
 __device__ void leaf_row_finish(const RowLoader<kDT>& L, const DFn& Drow, int m, int self, const int32_t* lid,

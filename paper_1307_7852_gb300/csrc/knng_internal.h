@@ -177,6 +177,14 @@ TcKey tc_key(const TreePlan& P, int d, int prec);
 // Candidate tiles for a shape (valid for its shared-memory budget).
 std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec);
 
+// Staged FP32 rescoring of reduced-precision leaf candidates (one CTA per
+// tree and leaf; the leaf's rows stream through shared memory in 32-entry
+// slices): FP32 rows, 16-byte aligned, k' <= 32, leaves of at most 512.
+bool leaf_rescore_staged_ok(const XDesc& x, int kp, int max_leaf);
+cudaError_t run_leaf_rescore_staged(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                                    const int32_t* perm, const uint8_t* leaf_exact, const uint16_t* cand, int kp,
+                                    int k, int32_t* ids, float* dists, cudaStream_t st);
+
 // all_exact (nullable): cleared by every leaf whose distances are not all
 // exact (its list is then not the exact k best of the leaf).
 // wait_cycles: limit of the waits on the TMA copies and on the MMAs' release
@@ -227,10 +235,13 @@ struct PairOffers {
 // tmask_in (nullable): the merge's tree masks of the input lists (exact
 // leaves only); a neighbour's entry that shares a tree with p's entry for
 // that neighbour is skipped.
+// stats (nullable): stats[0] += candidate rows scored, stats[1] += slots of
+// the neighbours' lists loaded (what the round actually reads).
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
                           unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers = nullptr,
-                          const uint8_t* tmask_in = nullptr);
+                          const uint8_t* tmask_in = nullptr,
+                          unsigned long long* stats = nullptr);
 
 // Scratch of a pairwise round: offers (cap entries), per-target counts and
 // offsets, forward lists.  pairwise_bytes() sizes it.

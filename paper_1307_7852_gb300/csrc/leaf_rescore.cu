@@ -1,0 +1,183 @@
+// FP32 rescoring of the reduced-precision leaf candidates (the leaf graphs of
+// Sec. 3.1 of arXiv:1307.7852 with a BF16 / FP8 candidate stage), one CTA per
+// (tree, leaf).
+//
+// The tensor-core leaf kernel leaves, for every row of a leaf that is not
+// exact in reduced precision, its k' candidates (local indices in the leaf).
+// Rescoring them with the canonical FP32 distance reads k' rows of d floats
+// per point; fetched one pair at a time from L2 that is k' * d * 4 bytes per
+// point (0.6 TB over the eight trees of a 1M x 960 build).  Here the leaf's
+// rows stream through shared memory instead, in 32-entry slices (one block
+// of the canonical distance), double-buffered with cp.async, so each row of
+// the leaf crosses L2 once per tree:
+//   * one thread per row holds its own slice in registers and one running
+//     sum per candidate; per slice it forms the eight 4-entry partials of
+//     every candidate pair, closes the block by the butterfly and adds it to
+//     the pair's sum -- exactly the canonical distance, block by block;
+//   * thread r reads the slice's eight 16-byte columns in the order
+//     u ^ (r mod 8), so the eight threads of a quarter warp touch eight
+//     different bank groups whatever rows they read;
+//   * at the end every row keeps its k best by (distance, id).
+// Leaves that are exact in reduced precision (their lists are final) are
+// skipped by a flag the leaf kernel writes.
+#include "knng_common.cuh"
+#include "knng_internal.h"
+
+namespace knng {
+
+namespace {
+constexpr int kSlice = 32;       // floats per row and slice (one block of the distance)
+constexpr int kMaxCand = 32;     // candidates per row handled here
+}  // namespace
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Canonical block value of a pair: own slice a (columns in the order
+// u ^ x, u = 0..7, already in registers), candidate slice b in shared
+// memory.  s[u] is the partial of column u ^ x; since the block's butterfly
+// pairs columns by xor (q with q ^ 4, then q ^ 2, then q ^ 1), relabelling
+// them by xor with x only swaps the operands of some additions, so the tree
+// below over s[] gives the block value bit for bit.
+__device__ __forceinline__ float slice_block(const float4 (&a)[8], const float4* __restrict__ b, int x)
+{
+    // columns u and u + 4 side by side in packed FP32 pairs (each lane of
+    // the pair rounds exactly like the scalar operation)
+    float2 s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float4 v0 = b[u ^ x], v1 = b[(u + 4) ^ x];
+        const float4 a0 = a[u], a1 = a[u + 4];
+        float2 acc = make_float2(0.f, 0.f), t;
+        t = __fadd2_rn(make_float2(a0.x, a1.x), make_float2(-v0.x, -v1.x)); acc = __ffma2_rn(t, t, acc);
+        t = __fadd2_rn(make_float2(a0.y, a1.y), make_float2(-v0.y, -v1.y)); acc = __ffma2_rn(t, t, acc);
+        t = __fadd2_rn(make_float2(a0.z, a1.z), make_float2(-v0.z, -v1.z)); acc = __ffma2_rn(t, t, acc);
+        t = __fadd2_rn(make_float2(a0.w, a1.w), make_float2(-v0.w, -v1.w)); acc = __ffma2_rn(t, t, acc);
+        s[u] = acc;  // (partial u, partial u + 4)
+    }
+    return ((s[0].x + s[0].y) + (s[2].x + s[2].y)) + ((s[1].x + s[1].y) + (s[3].x + s[3].y));
+}
+
+// grid (nleaves, T); blockDim >= the largest leaf (multiple of 32, <= 512).
+// cand: [T * n][kp] local indices (u16) of every row's candidates, the first
+// want = min(kp, m - 1) valid.  X rows: FP32, 16-byte aligned, ld % 4 == 0.
+__global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
+    const float* __restrict__ X, int64_t ld, int d, int64_t n, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ leaf_off, int nleaves, const uint8_t* __restrict__ leaf_exact,
+    const uint16_t* __restrict__ cand, int kp, int k, int32_t* __restrict__ out_ids, float* __restrict__ out_d)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = blockIdx.y, leaf = blockIdx.x;
+    if (leaf_exact[(int64_t)t * nleaves + leaf]) return;
+    const int off = leaf_off[leaf];
+    const int m = leaf_off[leaf + 1] - off;
+    const int mp = (m + 7) & ~7;
+    float4* buf = reinterpret_cast<float4*>(smem_raw);             // [2][mp][8] float4
+    int32_t* lid = reinterpret_cast<int32_t*>(buf + 2 * (size_t)mp * 8);  // [m]
+    const int tid = threadIdx.x;
+    const int64_t rowbase = (int64_t)t * n + off;
+    for (int j = tid; j < m; j += blockDim.x) lid[j] = perm[rowbase + j];
+    __syncthreads();
+
+    const int nslices = (d + kSlice - 1) / kSlice;
+    auto stage = [&](int sl, int b) {
+        float4* dst = buf + (size_t)b * mp * 8;
+        for (int u = tid; u < m * 8; u += blockDim.x) {
+            const int r = u >> 3, col = u & 7;
+            const int j = sl * kSlice + 4 * col;
+            const int avail = d - j;
+            const float* src = X + (uint64_t)(uint32_t)lid[r] * (uint64_t)ld;
+            const int bytes = avail >= 4 ? 16 : (avail > 0 ? 4 * avail : 0);
+            cp_async16(dst + (size_t)r * 8 + col, bytes > 0 ? src + j : src, bytes);
+        }
+        cp_async_commit();
+    };
+
+    const bool active = tid < m;
+    const int want = min(kp, m - 1);
+    uint16_t c[kMaxCand];
+    float tot[kMaxCand];
+#pragma unroll
+    for (int i = 0; i < kMaxCand; ++i) {
+        c[i] = 0;
+        tot[i] = 0.f;
+    }
+    if (active) {
+        const uint16_t* cr = cand + (rowbase + tid) * kp;
+#pragma unroll
+        for (int i = 0; i < kMaxCand; ++i)
+            if (i < want) c[i] = cr[i];
+    }
+    const int x8 = tid & 7;  // columns read in the order u ^ x8: a quarter warp hits eight bank groups
+
+    stage(0, 0);
+    for (int sl = 0; sl < nslices; ++sl) {
+        if (sl + 1 < nslices) {
+            stage(sl + 1, (sl + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (active) {
+            const float4* B = buf + (size_t)(sl & 1) * mp * 8;
+            float4 a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = B[(size_t)tid * 8 + (u ^ x8)];
+#pragma unroll
+            for (int i = 0; i < kMaxCand; ++i)
+                if (i < want) tot[i] = tot[i] + slice_block(a, B + (size_t)c[i] * 8, x8);
+        }
+        __syncthreads();  // the buffer of this slice is staged again two slices on
+    }
+    if (!active) return;
+    // the k best of the row's candidates by (distance, point id)
+    uint64_t key[kMaxCand];
+#pragma unroll
+    for (int i = 0; i < kMaxCand; ++i) key[i] = i < want ? pack_key(tot[i], (uint32_t)lid[c[i]]) : kKeyMax;
+    const int gi = lid[tid];
+    int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
+    float* od = out_d + ((int64_t)t * n + gi) * k;
+    uint64_t prev = 0;
+    for (int s = 0; s < k; ++s) {
+        uint64_t best = kKeyMax;
+#pragma unroll
+        for (int i = 0; i < kMaxCand; ++i)
+            if (key[i] < best && (s == 0 || key[i] > prev)) best = key[i];
+        const bool ok = s < want && best != kKeyMax;
+        oi[s] = ok ? (int32_t)(uint32_t)best : -1;
+        od[s] = ok ? unord_key((uint32_t)(best >> 32)) : __int_as_float(0x7f800000);
+        prev = best;
+    }
+}
+
+bool leaf_rescore_staged_ok(const XDesc& x, int kp, int max_leaf)
+{
+    return x.dtype == kDtF32 && x.vec && (x.ld % 4) == 0 && kp <= kMaxCand && max_leaf <= 512;
+}
+
+cudaError_t run_leaf_rescore_staged(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
+                                    const int32_t* perm, const uint8_t* leaf_exact, const uint16_t* cand, int kp,
+                                    int k, int32_t* ids, float* dists, cudaStream_t st)
+{
+    const int nleaves = (int)P.leaf_off.size() - 1;
+    const int threads = std::max(32, (P.max_leaf + 31) & ~31);
+    const int mp = (P.max_leaf + 7) & ~7;
+    const size_t smem = 2 * (size_t)mp * 8 * sizeof(float4) + (size_t)P.max_leaf * sizeof(int32_t);
+    cudaError_t e = cudaFuncSetAttribute(leaf_rescore_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    leaf_rescore_staged_kernel<<<dim3(nleaves, T), threads, smem, st>>>(
+        static_cast<const float*>(x.X), x.ld, x.d, x.n, perm, dp.leaf_off, nleaves, leaf_exact, cand, kp, k, ids,
+        dists);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace knng

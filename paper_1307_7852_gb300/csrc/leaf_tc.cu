@@ -16,13 +16,16 @@ namespace knng {
 
 extern template cudaError_t leaf_tc_run<kDtF32>(int, const CUtensorMap&, const XDesc&, const TreePlan&, const DevPlan&,
                                                 int, const int32_t*, int, void*, float*, float*, uint8_t*, int, int,
-                                                const TcGeom&, int32_t*, float*, int*, int*, cudaStream_t);
+                                                const TcGeom&, int32_t*, float*, int*, int*, uint16_t*, uint8_t*,
+                                                cudaStream_t);
 extern template cudaError_t leaf_tc_run<kDtF16>(int, const CUtensorMap&, const XDesc&, const TreePlan&, const DevPlan&,
                                                 int, const int32_t*, int, void*, float*, float*, uint8_t*, int, int,
-                                                const TcGeom&, int32_t*, float*, int*, int*, cudaStream_t);
+                                                const TcGeom&, int32_t*, float*, int*, int*, uint16_t*, uint8_t*,
+                                                cudaStream_t);
 extern template cudaError_t leaf_tc_run<kDtU8>(int, const CUtensorMap&, const XDesc&, const TreePlan&, const DevPlan&,
                                                int, const int32_t*, int, void*, float*, float*, uint8_t*, int, int,
-                                               const TcGeom&, int32_t*, float*, int*, int*, cudaStream_t);
+                                               const TcGeom&, int32_t*, float*, int*, int*, uint16_t*, uint8_t*,
+                                                cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -107,8 +110,14 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     float* qn = ar.take<float>((size_t)rows);
     float* qs = ar.take<float>((size_t)rows);
     uint8_t* qx = ar.take<uint8_t>((size_t)rows);
-    if (!ar.base) return cudaSuccess;
     if (kp > kTcCand) kp = kTcCand;
+    // rows of leaves that are not exact are rescored by the staged kernel
+    // (their candidates in [rows][kp] local indices, a flag per leaf)
+    const bool staged = leaf_rescore_staged_ok(x, kp, P.max_leaf);
+    const int nleaves = (int)P.leaf_off.size() - 1;
+    uint16_t* cand = staged ? ar.take<uint16_t>((size_t)rows * kp) : nullptr;
+    uint8_t* leaf_flag = staged ? ar.take<uint8_t>((size_t)T * nleaves) : nullptr;
+    if (!ar.base) return cudaSuccess;
     TcGeom G = tc_geometry(P, x.d, prec, tile);
     G.wait = wait_cycles > 0 ? wait_cycles : kWaitCycles;
     if (G.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -125,11 +134,19 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
+    cudaError_t e;
     if (x.dtype == kDtF16)
-        return leaf_tc_run<kDtF16>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
-    if (x.dtype == kDtU8)
-        return leaf_tc_run<kDtU8>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
-    return leaf_tc_run<kDtF32>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
+        e = leaf_tc_run<kDtF16>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact,
+                                cand, leaf_flag, st);
+    else if (x.dtype == kDtU8)
+        e = leaf_tc_run<kDtU8>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact,
+                               cand, leaf_flag, st);
+    else
+        e = leaf_tc_run<kDtF32>(prec, map, x, P, dp, T, perm, dq, Xq, qn, qs, qx, k, kp, G, ids, dists, err, all_exact,
+                                cand, leaf_flag, st);
+    if (e == cudaSuccess && staged)
+        e = run_leaf_rescore_staged(x, P, dp, T, perm, leaf_flag, cand, kp, k, ids, dists, st);
+    return e;
 }
 
 }  // namespace knng

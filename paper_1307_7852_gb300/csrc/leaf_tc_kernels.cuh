@@ -271,7 +271,9 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                                                                 const float* __restrict__ qscl,
                                                                 const uint8_t* __restrict__ qexact, int k, int kp,
                                                                 TcGeom G, int32_t* __restrict__ out_ids,
-                                                                float* __restrict__ out_d, int* err, int* all_exact)
+                                                                float* __restrict__ out_d, int* err, int* all_exact,
+                                                                uint16_t* __restrict__ cand_out,
+                                                                uint8_t* __restrict__ leaf_flag)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -328,6 +330,10 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
     // the whole leaf is exact: candidate distances are final, no rescoring
     const bool exact_leaf = __syncthreads_and(ex) != 0;
     if (tid == 0 && all_exact && !exact_leaf) atomicAnd(all_exact, 0);
+    // with cand_out, rows of a leaf that is not exact leave their candidates
+    // (local indices) for the staged FP32 rescoring kernel instead
+    const bool to_cands = cand_out != nullptr && !exact_leaf;
+    if (leaf_flag && tid == 0 && r0 == 0) leaf_flag[(int64_t)t * nleaves + leaf] = exact_leaf ? 1 : 0;
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
@@ -592,6 +598,11 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                             oi[s2] = -1;
                             od[s2] = __int_as_float(0x7f800000);
                         }
+                } else if (to_cands) {
+                    uint16_t* oc = cand_out + (rowbase + iloc) * kp;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (r0s + e < want) oc[r0s + e] = (uint16_t)(uint32_t)v[e];
                 } else {
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
@@ -599,7 +610,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 }
             }
             __syncthreads();
-            if (!exact_leaf) {
+            if (!exact_leaf && !to_cands) {
                 // rescore the listed candidates of each row, one warp per row
                 for (int rr = w; rr < 128; rr += kTcWarps) {
                     const int il2 = r0 + rr;
@@ -640,9 +651,14 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                     if (!rowflag[g0 + rr]) continue;
                     const float* drow = Dblk + (size_t)rr * ldD;
                     const int gi = lid[il2];
-                    leaf_row_finish<PER, kDT>(L, [&](int j) { return drow[j]; }, m, il2, lid, k, kw,
-                                              wsc + (size_t)kLeafWarpScratch * w, out_ids + ((int64_t)t * n + gi) * k,
-                                              out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
+                    if (to_cands)
+                        leaf_row_cands<PER>([&](int j) { return drow[j]; }, m, il2, kw,
+                                            wsc + (size_t)kLeafWarpScratch * w, cand_out + (rowbase + il2) * kp);
+                    else
+                        leaf_row_finish<PER, kDT>(L, [&](int j) { return drow[j]; }, m, il2, lid, k, kw,
+                                                  wsc + (size_t)kLeafWarpScratch * w,
+                                                  out_ids + ((int64_t)t * n + gi) * k,
+                                                  out_d + ((int64_t)t * n + gi) * k, !exact_leaf);
                 }
                 __syncthreads();
             }
@@ -656,7 +672,8 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
 template <int PREC, int PER, int kDT>
 static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                              const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
-                             const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, cudaStream_t st)
+                             const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact,
+                             uint16_t* cand, uint8_t* leaf_flag, cudaStream_t st)
 {
     auto kern = leaf_tc_kernel<PREC, PER, kDT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G.smem);
@@ -665,7 +682,7 @@ static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreeP
     const int nleaves = (int)P.leaf_off.size() - 1;
     const int RB = (P.max_leaf + 127) / 128;
     kern<<<dim3(nleaves * RB, T), kTcThreads, G.smem, st>>>(map, rl, x.n, perm, dp.leaf_off, nleaves, qn, qs, qx, k, kp,
-                                                            G, ids, dists, err, all_exact);
+                                                            G, ids, dists, err, all_exact, cand, leaf_flag);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -673,20 +690,29 @@ static cudaError_t launch_tc(const CUtensorMap& map, const XDesc& x, const TreeP
 template <int PREC, int kDT>
 static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                                const int32_t* perm, const float* qn, const float* qs, const uint8_t* qx, int k, int kp,
-                               const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, cudaStream_t st)
+                               const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, uint16_t* cand,
+                               uint8_t* leaf_flag, cudaStream_t st)
 {
     // keys per lane in the row selection: leaves of up to 32 * PER points
-    if (P.max_leaf <= 128) return launch_tc<PREC, 4, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
-    if (P.max_leaf <= 256) return launch_tc<PREC, 8, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
-    return launch_tc<PREC, 16, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
+    if (P.max_leaf <= 128)
+        return launch_tc<PREC, 4, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, cand,
+                                       leaf_flag, st);
+    if (P.max_leaf <= 256)
+        return launch_tc<PREC, 8, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, cand,
+                                       leaf_flag, st);
+    return launch_tc<PREC, 16, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, cand,
+                                    leaf_flag, st);
 }
 
 // Gather + quantise the leaf-ordered copy, then the leaf kernel, for one
 // element type of X (explicitly instantiated per type).
+// cand, leaf_flag (both or neither): candidates of the rows of leaves that
+// are not exact, for run_leaf_rescore_staged, and each leaf's exactness.
 template <int kDT>
 cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
                         const int32_t* perm, int dq, void* Xq, float* qn, float* qs, uint8_t* qx, int k, int kp,
-                        const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, cudaStream_t st)
+                        const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, uint16_t* cand,
+                        uint8_t* leaf_flag, cudaStream_t st)
 {
     const int64_t rows = (int64_t)T * x.n;
     const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);
@@ -704,8 +730,11 @@ cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const 
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (prec == 1) return dispatch_tc<1, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
-    return dispatch_tc<2, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, st);
+    if (prec == 1)
+        return dispatch_tc<1, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, cand,
+                                   leaf_flag, st);
+    return dispatch_tc<2, kDT>(map, x, P, dp, T, perm, qn, qs, qx, k, kp, G, ids, dists, err, all_exact, cand,
+                               leaf_flag, st);
 }
 
 }  // namespace knng

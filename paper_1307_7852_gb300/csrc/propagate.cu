@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                                  const unsigned long long* __restrict__ flags_in,
                                  const uint8_t* __restrict__ tm_in, int32_t* __restrict__ ids_out,
                                  float* __restrict__ d_out, unsigned long long* __restrict__ flags_out, int H,
-                                 int hshift, int cap, int per_warp_bytes)
+                                 int hshift, int cap, int per_warp_bytes, unsigned long long* __restrict__ stats)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
 
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long n_rows = 0, n_slots = 0;  // what this lane read (stats)
     for (int64_t wi = gw; wi < n; wi += nw) {
         const int32_t p = order ? order[wi] : (int32_t)wi;
         for (int s = lane * 4; s < H; s += 128) *reinterpret_cast<int4*>(tab + s) = make_int4(-1, -1, -1, -1);
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                             // exact leaf: c then is in p's merged list or
                             // k listed points beat it
                             int32_t c = ids_in[(int64_t)q * k + f];
+                            if (stats) ++n_slots;
                             if (kMode == 1 && (own_tm[e] & (int)tm_in[(int64_t)q * k + f])) c = -1;
                             o[gi] = c;
                         }
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
             }
         }
         __syncwarp();
+        if (stats && lane == 0) n_rows += (unsigned long long)(cnt - nknown);
         // score the new candidates, 32 at a time
         if (lane_X && (kDT == kDtU8 || bytes)) {
             // byte rows, d <= 128: eight lanes per candidate
@@ -338,12 +341,21 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         }
         __syncwarp();
     }
+    if (stats) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) n_slots += __shfl_xor_sync(KNNG_FULL_MASK, n_slots, o);
+        if (lane == 0) {
+            atomicAdd(&stats[0], n_rows);
+            atomicAdd(&stats[1], n_slots);
+        }
+    }
 }
 
 template <int E, int kDT>
 static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                                const unsigned long long* fin, int32_t* ids, float* dists, unsigned long long* fout,
-                               const PairOffers& po, const uint8_t* tm, cudaStream_t st)
+                               const PairOffers& po, const uint8_t* tm, cudaStream_t st,
+                               unsigned long long* stats)
 {
     const PropLayout PL = prop_layout(k);
     int warps = (int)((200 * 1024) / PL.per_warp);
@@ -380,7 +392,8 @@ static cudaError_t launch_prop(const XDesc& x, int k, const int32_t* order, cons
         }
     }
     kern<<<(int)blocks, warps * 32, smem, st>>>(rl, rb, x.xb_bad, lane_X, lane_ld, po, x.n, k, order, ids_in, d_in, fin,
-                                                tm, ids, dists, fout, PL.H, PL.hshift, PL.cap, (int)PL.per_warp);
+                                                tm, ids, dists, fout, PL.H, PL.hshift, PL.cap, (int)PL.per_warp,
+                                                stats);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -389,23 +402,25 @@ template <int kDT>
 static cudaError_t prop_dispatch(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in,
                                  const float* d_in, const unsigned long long* fin, int32_t* ids, float* dists,
                                  unsigned long long* fout, const PairOffers& po, const uint8_t* tm,
-                                 cudaStream_t st)
+                                 cudaStream_t st, unsigned long long* stats)
 {
-    if (k <= 32) return launch_prop<1, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, tm, st);
-    return launch_prop<2, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, tm, st);
+    if (k <= 32) return launch_prop<1, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, tm, st, stats);
+    return launch_prop<2, kDT>(x, k, order, ids_in, d_in, fin, ids, dists, fout, po, tm, st, stats);
 }
 
 cudaError_t run_propagate(const XDesc& x, int k, const int32_t* order, const int32_t* ids_in, const float* d_in,
                           const unsigned long long* flags_in, int32_t* ids, float* dists,
                           unsigned long long* flags_out, cudaStream_t st, const PairOffers* offers,
-                          const uint8_t* tmask_in)
+                          const uint8_t* tmask_in, unsigned long long* stats)
 {
     const PairOffers po = offers ? *offers : PairOffers{};
     if (x.dtype == kDtF16)
-        return prop_dispatch<kDtF16>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st);
+        return prop_dispatch<kDtF16>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st,
+                                     stats);
     if (x.dtype == kDtU8)
-        return prop_dispatch<kDtU8>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st);
-    return prop_dispatch<kDtF32>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st);
+        return prop_dispatch<kDtU8>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st,
+                                    stats);
+    return prop_dispatch<kDtF32>(x, k, order, ids_in, d_in, flags_in, ids, dists, flags_out, po, tmask_in, st, stats);
 }
 
 }  // namespace knng
