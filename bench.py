@@ -239,6 +239,55 @@ def unique_candidates(ids: np.ndarray, sample: np.ndarray) -> float:
     return tot / max(1, len(sample))
 
 
+def distance_errors(X, q, gi, gd, precision, cosine):
+    """Relative errors of the graph's FP32 distances on a sample of rows
+    against FP64 distances of the same pairs (plain NumPy), and, for the
+    reduced-precision paths, of the candidate distance between the quantised
+    rows (BF16 round to nearest even; E4M3 with a per-row scale max|x|/448)
+    -- the error the FP32 rescoring removes."""
+    Xf = np.asarray(X, dtype=np.float64)
+    if cosine:
+        nrm = np.linalg.norm(Xf, axis=1, keepdims=True)
+        Xf = Xf / np.where(nrm > 0, nrm, 1.0)
+    a = np.repeat(q, gi.shape[1])
+    b = gi.ravel()
+    ok = b >= 0
+    a, b, g = a[ok], b[ok], gd.ravel()[ok].astype(np.float64)
+    exact = np.empty(len(a))
+    for s0 in range(0, len(a), 65536):
+        dd = Xf[a[s0:s0 + 65536]] - Xf[b[s0:s0 + 65536]]
+        exact[s0:s0 + 65536] = np.einsum("ij,ij->i", dd, dd)
+    if cosine:
+        exact *= 0.5
+    pos = exact > 0
+    rel = np.abs(g[pos] - exact[pos]) / exact[pos]
+
+    def summary(r):
+        return {"max": float(r.max()) if len(r) else 0.0, "p50": float(np.percentile(r, 50)) if len(r) else 0.0,
+                "p99": float(np.percentile(r, 99)) if len(r) else 0.0,
+                "p99.9": float(np.percentile(r, 99.9)) if len(r) else 0.0,
+                "hist_log10": {str(e): int(np.sum((r >= 10.0 ** e) & (r < 10.0 ** (e + 1)))) for e in range(-9, 0)},
+                "zero": int(np.sum(r == 0))}
+    out = {"pairs": int(len(a)), "graph_fp32": summary(rel), "reference": "FP64 squared distance of the same pairs"}
+    if precision != "fp32" and not cosine:
+        import torch
+        sel = np.nonzero(pos)[0][:200000]
+        rows = np.unique(np.concatenate([a[sel], b[sel]]))
+        Xt = torch.from_numpy(np.asarray(X, dtype=np.float32)[rows])
+        if precision == "bf16":
+            Q = Xt.to(torch.bfloat16).to(torch.float64).numpy()
+        else:
+            sc = Xt.abs().amax(dim=1, keepdim=True) / 448.0
+            sc = torch.where(sc > 0, sc, torch.ones_like(sc))
+            Q = ((Xt / sc).to(torch.float8_e4m3fn).to(torch.float64) * sc.to(torch.float64)).numpy()
+        pos_of = {int(r): i for i, r in enumerate(rows)}
+        ia = np.array([pos_of[int(v)] for v in a[sel]])
+        ib = np.array([pos_of[int(v)] for v in b[sel]])
+        dq = np.einsum("ij,ij->i", Q[ia] - Q[ib], Q[ia] - Q[ib])
+        out[f"candidate_{precision}"] = summary(np.abs(dq - exact[sel]) / exact[sel])
+    return out
+
+
 # ---------------------------------------------------------- batched sets
 def run_batched(args):
     """256 independent Gaussian-mixture sets (n log-uniform in [2k, 200k], d in
@@ -705,6 +754,8 @@ def main():
             idset = float(np.mean([len(set(gi[r]) & set(eii[r])) / k for r in range(len(q))]))
             line["recall"] = {"tie_tolerant": tie, "id_set": idset, "sample": int(len(q)),
                               "reference": "exact brute force over all n (GPU, FP32 distances)"}
+            line["distance_error"] = distance_errors(X, q, gi, got_d.cpu().numpy(), args.precision,
+                                                     args.metric_kind == "cosine")
 
         # ---- end to end through the host-buffer C ABI call
         if not args.no_e2e:
