@@ -322,7 +322,8 @@ def run_batched(args):
             knng.knng_build(X, k, T, g, R, args.seed, prec, 2, ids=oi, dists=od, h=h)
 
     res = {}
-    for name, fn in (("separate", separate), ("batched", batched)):
+    legs = (("batched", batched),) if args.no_separate else (("separate", separate), ("batched", batched))
+    for name, fn in legs:
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
@@ -348,10 +349,11 @@ def run_batched(args):
                    "dims": sorted(set(int(X.shape[1]) for X in sets)), "k": k, "T": T, "leaf_size": g,
                    "rounds": R, "precision": args.precision},
         "gpu_launches": int(res["batched"]["launches_per_step"] * args.steps),
-        "separate": {"value": ntot / (res["separate"]["ms_per_step"] / 1e3),
-                     "ms_per_step": res["separate"]["ms_per_step"],
-                     "launches_per_step": res["separate"]["launches_per_step"]},
-        "speedup_vs_separate": res["separate"]["ms_per_step"] / res["batched"]["ms_per_step"],
+        "separate": None if args.no_separate else {
+            "value": ntot / (res["separate"]["ms_per_step"] / 1e3), "ms_per_step": res["separate"]["ms_per_step"],
+            "launches_per_step": res["separate"]["launches_per_step"]},
+        "speedup_vs_separate": None if args.no_separate else
+        res["separate"]["ms_per_step"] / res["batched"]["ms_per_step"],
         "autotuned_tiles": {str(dd): {"stages": t[0], "rows_per_group": t[1], "leaf_ms": t[2]}
                             for dd, t in tiles.items()},
         "clocks": res["batched"]["clocks"],
@@ -427,7 +429,7 @@ def run_learned(args):
         ms_l, _ = timed(lambda: knng.knng_build_learned(net, Xd, k, 4, g, R, args.seed, prec, 2, ids=ids,
                                                         dists=dists, h=h, partitioner=part))
         res[name] = {"ms_per_step": ms_l, "recall": recall()}
-    for T in (8, 6, 4):
+    for T in (8, 6, 5, 4):
         ms_r, _ = timed(lambda: knng.knng_build(Xd, k, T, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h))
         res[f"random_T{T}"] = {"ms_per_step": ms_r, "recall": recall()}
     ms_p, _ = timed(lambda: knng.knng_build(Xd, k, 4, g, R, args.seed, prec, 2, ids=ids, dists=dists, h=h,
@@ -495,6 +497,7 @@ def main():
     ap.add_argument("--learned-n", type=int, default=10_000_000)
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--batch-sets", type=int, default=256)
+    ap.add_argument("--no-separate", action="store_true", help="batched256: time the batched launch only")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16")
     ap.add_argument("--seed", type=int, default=12345)
     ap.add_argument("--data-seed", type=int, default=2013)

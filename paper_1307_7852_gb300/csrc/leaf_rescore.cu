@@ -44,29 +44,37 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // memory.  s[u] is the partial of column u ^ x; since the block's butterfly
 // pairs columns by xor (q with q ^ 4, then q ^ 2, then q ^ 1), relabelling
 // them by xor with x only swaps the operands of some additions, so the tree
-// below over s[] gives the block value bit for bit.
+// below over s[] gives the block value bit for bit -- and, t = a - b and
+// b - a squaring alike, the same value whichever row is the own one.
+// (Scalar FP32: packed pairs need their operands in adjacent registers,
+// which these columns are not, and measured slower.)
 __device__ __forceinline__ float slice_block(const float4 (&a)[8], const float4* __restrict__ b, int x)
 {
-    // columns u and u + 4 side by side in packed FP32 pairs (each lane of
-    // the pair rounds exactly like the scalar operation)
-    float2 s[4];
+    float s[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const float4 v0 = b[u ^ x], v1 = b[(u + 4) ^ x];
-        const float4 a0 = a[u], a1 = a[u + 4];
-        float2 acc = make_float2(0.f, 0.f), t;
-        t = __fadd2_rn(make_float2(a0.x, a1.x), make_float2(-v0.x, -v1.x)); acc = __ffma2_rn(t, t, acc);
-        t = __fadd2_rn(make_float2(a0.y, a1.y), make_float2(-v0.y, -v1.y)); acc = __ffma2_rn(t, t, acc);
-        t = __fadd2_rn(make_float2(a0.z, a1.z), make_float2(-v0.z, -v1.z)); acc = __ffma2_rn(t, t, acc);
-        t = __fadd2_rn(make_float2(a0.w, a1.w), make_float2(-v0.w, -v1.w)); acc = __ffma2_rn(t, t, acc);
-        s[u] = acc;  // (partial u, partial u + 4)
+    for (int u = 0; u < 8; ++u) {
+        const float4 v = b[u ^ x];
+        float acc = 0.f, t;
+        t = a[u].x - v.x; acc = fmaf(t, t, acc);
+        t = a[u].y - v.y; acc = fmaf(t, t, acc);
+        t = a[u].z - v.z; acc = fmaf(t, t, acc);
+        t = a[u].w - v.w; acc = fmaf(t, t, acc);
+        s[u] = acc;
     }
-    return ((s[0].x + s[0].y) + (s[2].x + s[2].y)) + ((s[1].x + s[1].y) + (s[3].x + s[3].y));
+    return ((s[0] + s[4]) + (s[2] + s[6])) + ((s[1] + s[5]) + (s[3] + s[7]));
 }
 
 // grid (nleaves, T); blockDim >= the largest leaf (multiple of 32, <= 512).
 // cand: [T * n][kp] local indices (u16) of every row's candidates, the first
 // want = min(kp, m - 1) valid.  X rows: FP32, 16-byte aligned, ld % 4 == 0.
+//
+// A pair listed by both of its rows (r in c's list and c in r's) is scored
+// once, by the smaller row: the canonical distance is symmetric bit for bit,
+// so the other row takes the value from a table in shared memory.
+// Membership is a 512-bit bitmap per row.  (Dealing the pairs out evenly,
+// both rows then read from shared memory, measured slower: the row-per-
+// thread form keeps the own slice in registers.)
+template <int KC>
 __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
     const float* __restrict__ X, int64_t ld, int d, int64_t n, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ leaf_off, int nleaves, const uint8_t* __restrict__ leaf_exact,
@@ -78,12 +86,50 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
     const int off = leaf_off[leaf];
     const int m = leaf_off[leaf + 1] - off;
     const int mp = (m + 7) & ~7;
-    float4* buf = reinterpret_cast<float4*>(smem_raw);             // [2][mp][8] float4
-    int32_t* lid = reinterpret_cast<int32_t*>(buf + 2 * (size_t)mp * 8);  // [m]
+    // [2][mp][8] float4 slices | lid[mp] | bits[mp][16] u32 | cand_s[mp][kp] u16
+    float4* buf = reinterpret_cast<float4*>(smem_raw);
+    int32_t* lid = reinterpret_cast<int32_t*>(buf + 2 * (size_t)mp * 8);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(lid + mp);
+    uint16_t* cand_s = reinterpret_cast<uint16_t*>(bits + (size_t)mp * 16);
+    float* res = reinterpret_cast<float*>(buf);  // [mp][kp], after the slices
     const int tid = threadIdx.x;
     const int64_t rowbase = (int64_t)t * n + off;
     for (int j = tid; j < m; j += blockDim.x) lid[j] = perm[rowbase + j];
+
+    const bool active = tid < m;
+    const int want = min(kp, m - 1);
+    uint16_t c[KC];
+    float tot[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+        c[i] = 0;
+        tot[i] = 0.f;
+    }
+    if (active) {
+        const uint16_t* cr = cand + (rowbase + tid) * kp;
+        uint32_t* mybits = bits + (size_t)tid * 16;  // this row's bitmap: only this thread writes it
+#pragma unroll
+        for (int z = 0; z < 16; ++z) mybits[z] = 0u;
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < want) {
+                c[i] = cr[i];
+                cand_s[(size_t)tid * kp + i] = c[i];
+                mybits[c[i] >> 5] |= 1u << (c[i] & 31);
+            }
+    }
     __syncthreads();
+    // the pairs this row scores: its candidate is larger, or does not list it
+    uint32_t mine = 0u;
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < want) {
+                const int cc = c[i];
+                const bool listed = (bits[(size_t)cc * 16 + (tid >> 5)] >> (tid & 31)) & 1u;
+                if (cc > tid || !listed) mine |= 1u << i;
+            }
+    }
 
     const int nslices = (d + kSlice - 1) / kSlice;
     auto stage = [&](int sl, int b) {
@@ -98,22 +144,6 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
         }
         cp_async_commit();
     };
-
-    const bool active = tid < m;
-    const int want = min(kp, m - 1);
-    uint16_t c[kMaxCand];
-    float tot[kMaxCand];
-#pragma unroll
-    for (int i = 0; i < kMaxCand; ++i) {
-        c[i] = 0;
-        tot[i] = 0.f;
-    }
-    if (active) {
-        const uint16_t* cr = cand + (rowbase + tid) * kp;
-#pragma unroll
-        for (int i = 0; i < kMaxCand; ++i)
-            if (i < want) c[i] = cr[i];
-    }
     const int x8 = tid & 7;  // columns read in the order u ^ x8: a quarter warp hits eight bank groups
 
     stage(0, 0);
@@ -131,16 +161,33 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
 #pragma unroll
             for (int u = 0; u < 8; ++u) a[u] = B[(size_t)tid * 8 + (u ^ x8)];
 #pragma unroll
-            for (int i = 0; i < kMaxCand; ++i)
-                if (i < want) tot[i] = tot[i] + slice_block(a, B + (size_t)c[i] * 8, x8);
+            for (int i = 0; i < KC; ++i)
+                if ((mine >> i) & 1u) tot[i] = tot[i] + slice_block(a, B + (size_t)c[i] * 8, x8);
         }
         __syncthreads();  // the buffer of this slice is staged again two slices on
     }
-    if (!active) return;
-    // the k best of the row's candidates by (distance, point id)
-    uint64_t key[kMaxCand];
+    // exchange: every row publishes what it scored, then takes the pairs its
+    // candidate scored from the candidate's row of the table
+    if (active) {
 #pragma unroll
-    for (int i = 0; i < kMaxCand; ++i) key[i] = i < want ? pack_key(tot[i], (uint32_t)lid[c[i]]) : kKeyMax;
+        for (int i = 0; i < KC; ++i)
+            if ((mine >> i) & 1u) res[(size_t)tid * kp + i] = tot[i];
+    }
+    __syncthreads();
+    if (!active) return;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+        if (i < want && !((mine >> i) & 1u)) {
+            const int cc = c[i];
+            const uint16_t* lc = cand_s + (size_t)cc * kp;
+            int j = 0;
+            while (j < kp - 1 && lc[j] != (uint16_t)tid) ++j;
+            tot[i] = res[(size_t)cc * kp + j];
+        }
+    // the k best of the row's candidates by (distance, point id)
+    uint64_t key[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) key[i] = i < want ? pack_key(tot[i], (uint32_t)lid[c[i]]) : kKeyMax;
     const int gi = lid[tid];
     int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
     float* od = out_d + ((int64_t)t * n + gi) * k;
@@ -148,7 +195,7 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
     for (int s = 0; s < k; ++s) {
         uint64_t best = kKeyMax;
 #pragma unroll
-        for (int i = 0; i < kMaxCand; ++i)
+        for (int i = 0; i < KC; ++i)
             if (key[i] < best && (s == 0 || key[i] > prev)) best = key[i];
         const bool ok = s < want && best != kKeyMax;
         oi[s] = ok ? (int32_t)(uint32_t)best : -1;
@@ -157,9 +204,17 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
     }
 }
 
+static size_t staged_smem(int max_leaf, int kp)
+{
+    const size_t mp = (size_t)((max_leaf + 7) & ~7);
+    return 2 * mp * 8 * sizeof(float4) + mp * sizeof(int32_t) + mp * 16 * sizeof(uint32_t) +
+           mp * kp * sizeof(uint16_t);
+}
+
 bool leaf_rescore_staged_ok(const XDesc& x, int kp, int max_leaf)
 {
-    return x.dtype == kDtF32 && x.vec && (x.ld % 4) == 0 && kp <= kMaxCand && max_leaf <= 512;
+    return x.dtype == kDtF32 && x.vec && (x.ld % 4) == 0 && kp <= kMaxCand && max_leaf <= 512 &&
+           staged_smem(max_leaf, kp) <= 220 * 1024;
 }
 
 cudaError_t run_leaf_rescore_staged(const XDesc& x, const TreePlan& P, const DevPlan& dp, int T,
@@ -168,14 +223,15 @@ cudaError_t run_leaf_rescore_staged(const XDesc& x, const TreePlan& P, const Dev
 {
     const int nleaves = (int)P.leaf_off.size() - 1;
     const int threads = std::max(32, (P.max_leaf + 31) & ~31);
-    const int mp = (P.max_leaf + 7) & ~7;
-    const size_t smem = 2 * (size_t)mp * 8 * sizeof(float4) + (size_t)P.max_leaf * sizeof(int32_t);
-    cudaError_t e = cudaFuncSetAttribute(leaf_rescore_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = staged_smem(P.max_leaf, kp);
+    // candidate capacity per row: the smallest of 16, 24, 32 holding k'
+    auto kern = kp <= 16 ? leaf_rescore_staged_kernel<16>
+              : kp <= 24 ? leaf_rescore_staged_kernel<24>
+                         : leaf_rescore_staged_kernel<32>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    leaf_rescore_staged_kernel<<<dim3(nleaves, T), threads, smem, st>>>(
-        static_cast<const float*>(x.X), x.ld, x.d, x.n, perm, dp.leaf_off, nleaves, leaf_exact, cand, kp, k, ids,
-        dists);
+    kern<<<dim3(nleaves, T), threads, smem, st>>>(static_cast<const float*>(x.X), x.ld, x.d, x.n, perm, dp.leaf_off,
+                                                  nleaves, leaf_exact, cand, kp, k, ids, dists);
     note_launches(1);
     return cudaGetLastError();
 }

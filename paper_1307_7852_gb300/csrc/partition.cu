@@ -192,36 +192,71 @@ __global__ void gen_dirs_kernel(float* dirs, int T, int S, int d, int d_pad,
 }
 
 // Learned splits, step 1: range (as order keys) of every tree's feature of
-// this level inside every node.
+// this level inside every node.  Positions are visited in node order, so the
+// lanes of a warp nearly always share one node: the warp then reduces its
+// keys and one lane updates the node's range (on the top levels every point
+// of a tree would otherwise hit the same two words).
 struct FeatOfTree {
     int f[32];
 };
 __global__ void node_feature_range_kernel(int64_t n, int T, const float* __restrict__ Z, int C, FeatOfTree ft,
-                                          const int32_t* __restrict__ node_of, int S, uint32_t* __restrict__ rmin,
-                                          uint32_t* __restrict__ rmax)
+                                          const int32_t* __restrict__ node_pos, const int32_t* __restrict__ perm,
+                                          int S, uint32_t* __restrict__ rmin, uint32_t* __restrict__ rmax)
 {
     const int64_t total = (int64_t)T * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = node_of[e];
-        if (s < 0) continue;
-        const int t = (int)(e / n);
-        const int64_t i = e - (int64_t)t * n;
-        const uint32_t o = ord_key(Z[i * C + ft.f[t]]);
-        atomicMin(&rmin[(int64_t)t * S + s], o);
-        atomicMax(&rmax[(int64_t)t * S + s], o);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < total; e0 += stride) {
+        const int64_t e = e0 + threadIdx.x;
+        int64_t key = -1;  // (tree, node), -1: nothing to add
+        uint32_t o = 0;
+        if (e < total) {
+            const int sn = node_pos[e];
+            if (sn >= 0) {
+                const int t = (int)(e / n);
+                key = (int64_t)t * S + sn;
+                o = ord_key(Z[(int64_t)perm[e] * C + ft.f[t]]);
+            }
+        }
+        const int64_t key0 = __shfl_sync(KNNG_FULL_MASK, key, 0);
+        if (__all_sync(KNNG_FULL_MASK, key == key0)) {
+            if (key0 < 0) continue;
+            const uint32_t mn = __reduce_min_sync(KNNG_FULL_MASK, o);
+            const uint32_t mx = __reduce_max_sync(KNNG_FULL_MASK, o);
+            if (lane == 0) {
+                atomicMin(&rmin[key0], mn);
+                atomicMax(&rmax[key0], mx);
+            }
+        } else if (key >= 0) {
+            atomicMin(&rmin[key], o);
+            atomicMax(&rmax[key], o);
+        }
     }
 }
 
 // Range of every feature over all points (order keys in scratch, then
-// max - min in frange).
+// max - min in frange).  C divides 32 and every thread's stride, so a thread
+// only ever sees feature gtid mod C: it keeps its own minimum and maximum,
+// the lanes of a warp holding the same feature combine theirs, and one
+// atomic per warp and feature remains (not one per element).
 __global__ void feature_range_kernel(const float* __restrict__ Z, int64_t n, int C, uint32_t* __restrict__ mm)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * C; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
+    const int lane = threadIdx.x & 31;
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+    for (int64_t e = gtid; e < n * C; e += stride) {
         const uint32_t o = ord_key(Z[e]);
-        atomicMin(&mm[c], o);
-        atomicMax(&mm[C + c], o);
+        mn = min(mn, o);
+        mx = max(mx, o);
+    }
+    for (int o = 16; o >= C; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(KNNG_FULL_MASK, mn, o));
+        mx = max(mx, __shfl_xor_sync(KNNG_FULL_MASK, mx, o));
+    }
+    if (lane < C) {
+        atomicMin(&mm[lane], mn);
+        atomicMax(&mm[C + lane], mx);
     }
 }
 __global__ void feature_range_finish_kernel(int C, const uint32_t* __restrict__ mm, float* __restrict__ frange)
@@ -232,9 +267,10 @@ __global__ void feature_range_finish_kernel(int C, const uint32_t* __restrict__ 
 
 cudaError_t run_feature_range(const float* Z, int64_t n, int C, uint32_t* mm, float* frange, cudaStream_t st)
 {
+    if (C < 1 || C > 32 || (32 % C) != 0) return cudaErrorInvalidValue;
     cudaMemsetAsync(mm, 0xFF, sizeof(uint32_t) * C, st);
     cudaMemsetAsync(mm + C, 0, sizeof(uint32_t) * C, st);
-    const int blocks = (int)std::min<int64_t>((n * C + 255) / 256, (int64_t)num_sms() * 8);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n * C + 255) / 256, (int64_t)num_sms() * 8));
     feature_range_kernel<<<blocks, 256, 0, st>>>(Z, n, C, mm);
     feature_range_finish_kernel<<<1, 32, 0, st>>>(C, mm, frange);
     note_launches(2);
@@ -284,9 +320,26 @@ __device__ __forceinline__ void project_body(const Loader& L, int64_t n, int T, 
             const int tl = t0 + lane;
             const int my_s = (lane < 8 && tl < T) ? node_of[(int64_t)tl * n + i] : -1;
             if (__ballot_sync(KNNG_FULL_MASK, my_s >= 0) == 0) continue;
+            // learned levels: a node splits on its learned feature while the
+            // feature still varies there, and then needs no projection
+            bool my_feat = false;
+            if (kLearned && my_s >= 0) {
+                const int f = lv.ft.f[tl];
+                const int64_t ns = (int64_t)tl * S + my_s;
+                const float span = unord_key(lv.rmax[ns]) - unord_key(lv.rmin[ns]);
+                my_feat = span > lv.tau * lv.frange[f];
+            }
+            const int proj_s = my_feat ? -1 : my_s;
             int sv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) sv[u] = __shfl_sync(KNNG_FULL_MASK, my_s, u);
+            for (int u = 0; u < 8; ++u) sv[u] = __shfl_sync(KNNG_FULL_MASK, proj_s, u);
+            if (kLearned && __ballot_sync(KNNG_FULL_MASK, proj_s >= 0) == 0) {
+                if (my_s >= 0) {
+                    const int64_t row = (int64_t)tl * n;
+                    keys[row + pos_of[row + i]] = ord_key(lv.Z[i * lv.C + lv.ft.f[tl]]);
+                }
+                continue;
+            }
             float acc[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) acc[u] = 0.0f;
@@ -319,14 +372,7 @@ __device__ __forceinline__ void project_body(const Loader& L, int64_t n, int T, 
             }
             if (my_s >= 0) {
                 const int64_t row = (int64_t)tl * n;
-                uint32_t key = ord_key(mine);
-                if (kLearned) {
-                    // the node's learned feature, while it still varies there
-                    const int f = lv.ft.f[tl];
-                    const int64_t ns = (int64_t)tl * S + my_s;
-                    const float span = unord_key(lv.rmax[ns]) - unord_key(lv.rmin[ns]);
-                    if (span > lv.tau * lv.frange[f]) key = ord_key(lv.Z[i * lv.C + f]);
-                }
+                const uint32_t key = my_feat ? ord_key(lv.Z[i * lv.C + lv.ft.f[tl]]) : ord_key(mine);
                 keys[row + pos_of[row + i]] = key;
             }
         }
@@ -1047,7 +1093,8 @@ cudaError_t run_partition(const XDesc& x, const TreePlan& P, const DevPlan& dp, 
             cudaMemsetAsync(rmin, 0xFF, sizeof(uint32_t) * (size_t)T * S, st);
             cudaMemsetAsync(rmax, 0, sizeof(uint32_t) * (size_t)T * S, st);
             node_feature_range_kernel<<<grid_for((int64_t)T * n, 256, gcap), 256, 0, st>>>(n, T, lf->Z, lf->C, lv.ft,
-                                                                                         node_of, S, rmin, rmax);
+                                                                                         node_pos, cur, S, rmin,
+                                                                                         rmax);
             note_launches(1);
         }
         gen_dirs_kernel<<<grid_for((int64_t)T * S * (d_pad / 4), 256, gcap), 256, 0, st>>>(

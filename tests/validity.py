@@ -13,7 +13,7 @@ FP32 stages (a top-k of a known candidate set by exact distance):
     pair (the entry is real);
   * the sorted distance profile within 1e-5 relative of the oracle's, position
     by position, and ids equal wherever the oracle's neighbouring distances
-    differ by more than 1e-5 relative (the benchmark spec tie rule).
+    differ by more than 1e-5 relative (the tie rule of the FP32 parity bar).
 
 Reduced-precision leaf stage (top-k' by the quantised distance D~, then the
 exact top-k of those): with e_pj a bound on the GPU's error in D~(p, j),
