@@ -57,7 +57,7 @@ static TcGeom tc_geometry(const TreePlan& P, int d, int prec, const TcTile* tile
     G.nbox = G.R_load / G.box_rows;
     G.stage_bytes = G.R_load * 128;
     G.ldD = ((G.N_load + 31) & ~31) + 1;
-    const int s_max = std::max(1, std::min(std::min(G.nK, 4), (160 * 1024) / G.stage_bytes));
+    const int s_max = std::max(1, std::min(std::min(G.nK, 4), (200 * 1024) / G.stage_bytes));
     if (tile && tile->S >= 1 && tile->RG >= 32) {
         G.S = std::min(tile->S, s_max);
         G.RG = tile->RG;
@@ -89,7 +89,7 @@ std::vector<TcTile> tc_candidates(const TreePlan& P, int d, int prec)
 {
     std::vector<TcTile> out;
     const TcGeom base = tc_geometry(P, d, prec, nullptr);
-    const int s_max = std::max(1, std::min(std::min(base.nK, 4), (160 * 1024) / base.stage_bytes));
+    const int s_max = std::max(1, std::min(std::min(base.nK, 4), (200 * 1024) / base.stage_bytes));
     for (int S = 1; S <= s_max; ++S)
         for (int RG = 32; RG <= 128; RG <<= 1) {
             TcTile t{S, RG};
