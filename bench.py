@@ -122,7 +122,7 @@ def traffic_from_csv(args, w):
         lines = [ln for ln in f if ln.startswith('"')]
     for row in csv.DictReader(lines):
         name = row.get("Kernel Name", "")
-        base = name.split("(")[0].split("<")[0].split("::")[-1].strip()
+        base = name.split("(")[0].split("<")[0].split("::")[-1].strip().split()[-1] if name.strip() else ""
         if base not in TRAFFIC_KERNELS:
             continue
         key = row["ID"]
@@ -147,7 +147,9 @@ def traffic_from_csv(args, w):
             out[kname] = {"unit": unit, "bytes_per_unit": sum(vals) / n}
         else:
             out[kname] = {"unit": "point-build", "bytes_per_unit": sum(vals) / n}
-    rec = {"workload": args.workload, "precision": args.precision, "source_hash": source_hash(),
+    if not args.traffic_hash:
+        raise SystemExit("--traffic-from needs --traffic-hash: the source_hash the profiled run printed")
+    rec = {"workload": args.workload, "precision": args.precision, "source_hash": args.traffic_hash,
            "case": {"n": n, **{k_: w[k_] for k_ in ("d", "k", "T", "g", "R")}, "centers": case["centers"]},
            "command": args.traffic_command or "", "per_unit": out}
     with open(traffic_path(args.workload, args.precision), "w") as f:
@@ -522,6 +524,8 @@ def main():
                     help="ncu --csv launch list of --profile-case with dram__bytes_{read,write}.sum: record the "
                          "kernels' DRAM bytes per unit under profiles/ and exit")
     ap.add_argument("--traffic-command", default=None, help="the ncu command line, recorded with the traffic")
+    ap.add_argument("--traffic-hash", default=None,
+                    help="source_hash printed by the profiled --profile-case run (the kernels the counts belong to)")
     args = ap.parse_args()
     if args.workload in ("batched256", "learned10m"):
         if args.impl == "reference":
@@ -555,6 +559,7 @@ def main():
         Xc = torch.from_numpy(make_data(wc, seed=args.data_seed)).cuda()
         knng.knng_build(Xc, w["k"], w["T"], w["g"], w["R"], args.seed, PRECISIONS[args.precision], 2)
         torch.cuda.synchronize()
+        print(f"source_hash={source_hash()}", flush=True)
         return 0
 
     import torch

@@ -87,11 +87,15 @@ __global__ void __launch_bounds__(kNT) leaf_knn_f32_kernel(RowLoader<kDT> L, int
             for (int c = 0; c < CT; ++c) acc[rr][c] = 0.f;
         for (int k0 = 0; k0 < L.d; k0 += kKC) {
             __syncthreads();
-            for (int idx = tid; idx < m_pad * kKC; idx += kNT) {
-                const int row = idx / kKC, kk = idx % kKC;
-                float v = 0.f;
-                if (row < m && k0 + kk < L.d) v = L.load1(sm.lid[row], k0 + kk);
-                sm.Bt[kk * mp1 + row] = v;
+            // four entries a load (zero past d), stored transposed
+            for (int idx = tid; idx < m_pad * (kKC / 4); idx += kNT) {
+                const int row = idx / (kKC / 4), kk = 4 * (idx % (kKC / 4));
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (row < m && k0 + kk < L.d) v = L.load4(sm.lid[row], k0 + kk);
+                sm.Bt[(kk + 0) * mp1 + row] = v.x;
+                sm.Bt[(kk + 1) * mp1 + row] = v.y;
+                sm.Bt[(kk + 2) * mp1 + row] = v.z;
+                sm.Bt[(kk + 3) * mp1 + row] = v.w;
             }
             __syncthreads();
 #pragma unroll 4

@@ -191,15 +191,30 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
     const int gi = lid[tid];
     int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
     float* od = out_d + ((int64_t)t * n + gi) * k;
+    // entries two at a time (8-byte stores: k is even and the row starts
+    // 8-byte aligned), else one at a time
+    const bool pairs2 = (k & 1) == 0 && (((uintptr_t)out_ids | (uintptr_t)out_d) & 7) == 0;
     uint64_t prev = 0;
+    int32_t id_lo = -1;
+    float d_lo = 0.f;
     for (int s = 0; s < k; ++s) {
         uint64_t best = kKeyMax;
 #pragma unroll
         for (int i = 0; i < KC; ++i)
             if (key[i] < best && (s == 0 || key[i] > prev)) best = key[i];
         const bool ok = s < want && best != kKeyMax;
-        oi[s] = ok ? (int32_t)(uint32_t)best : -1;
-        od[s] = ok ? unord_key((uint32_t)(best >> 32)) : __int_as_float(0x7f800000);
+        const int32_t id = ok ? (int32_t)(uint32_t)best : -1;
+        const float dv = ok ? unord_key((uint32_t)(best >> 32)) : __int_as_float(0x7f800000);
+        if (!pairs2) {
+            oi[s] = id;
+            od[s] = dv;
+        } else if (s & 1) {
+            *reinterpret_cast<int2*>(oi + s - 1) = make_int2(id_lo, id);
+            *reinterpret_cast<float2*>(od + s - 1) = make_float2(d_lo, dv);
+        } else {
+            id_lo = id;
+            d_lo = dv;
+        }
         prev = best;
     }
 }

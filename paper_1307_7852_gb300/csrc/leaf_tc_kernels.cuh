@@ -587,12 +587,33 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                     const int gi = lid[iloc];
                     int32_t* oi = out_ids + ((int64_t)t * n + gi) * k;
                     float* od = out_d + ((int64_t)t * n + gi) * k;
+                    if ((k & 3) == 0 && want == k && (((uintptr_t)out_ids | (uintptr_t)out_d) & 15) == 0) {
+                        // whole rows of 16-byte groups (row starts are 16-byte
+                        // aligned when k is a multiple of 4): four entries a store
 #pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        if (r0s + e < want) {
-                            oi[r0s + e] = lid[(uint32_t)v[e]];
-                            od[r0s + e] = unord_key((uint32_t)(v[e] >> 32));
-                        }
+                        for (int e = 0; e < 16; e += 4)
+                            if (r0s + e < want) {
+                                int4 iv;
+                                float4 dv4;
+                                iv.x = lid[(uint32_t)v[e]];
+                                iv.y = lid[(uint32_t)v[e + 1]];
+                                iv.z = lid[(uint32_t)v[e + 2]];
+                                iv.w = lid[(uint32_t)v[e + 3]];
+                                dv4.x = unord_key((uint32_t)(v[e] >> 32));
+                                dv4.y = unord_key((uint32_t)(v[e + 1] >> 32));
+                                dv4.z = unord_key((uint32_t)(v[e + 2] >> 32));
+                                dv4.w = unord_key((uint32_t)(v[e + 3] >> 32));
+                                *reinterpret_cast<int4*>(oi + r0s + e) = iv;
+                                *reinterpret_cast<float4*>(od + r0s + e) = dv4;
+                            }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            if (r0s + e < want) {
+                                oi[r0s + e] = lid[(uint32_t)v[e]];
+                                od[r0s + e] = unord_key((uint32_t)(v[e] >> 32));
+                            }
+                    }
                     if (half == 0)
                         for (int s2 = want; s2 < k; ++s2) {
                             oi[s2] = -1;
@@ -600,9 +621,21 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                         }
                 } else if (to_cands) {
                     uint16_t* oc = cand_out + (rowbase + iloc) * kp;
+                    if ((kp & 3) == 0 && want == kp) {
+                        // four local indices a store (row starts 8-byte aligned)
 #pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        if (r0s + e < want) oc[r0s + e] = (uint16_t)(uint32_t)v[e];
+                        for (int e = 0; e < 16; e += 4)
+                            if (r0s + e < want) {
+                                uint2 u;
+                                u.x = ((uint32_t)v[e] & 0xFFFFu) | ((uint32_t)v[e + 1] << 16);
+                                u.y = ((uint32_t)v[e + 2] & 0xFFFFu) | ((uint32_t)v[e + 3] << 16);
+                                *reinterpret_cast<uint2*>(oc + r0s + e) = u;
+                            }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            if (r0s + e < want) oc[r0s + e] = (uint16_t)(uint32_t)v[e];
+                    }
                 } else {
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
