@@ -114,8 +114,10 @@ def traffic_from_csv(args, w):
     dram__bytes_read.sum,dram__bytes_write.sum, --csv) of `bench.py
     --profile-case` to profiles/dram_traffic_<workload>_<precision>.json."""
     import csv
-    case = PROFILE_CASE[args.workload]
+    case = dict(n=w["n"], centers=w["centers"]) if args.traffic_full else PROFILE_CASE[args.workload]
     n, T, R = case["n"], w["T"], w["R"]
+    # launches in order; a build starts with init_perm_kernel, and only the
+    # last build's launches count (a full-size run also holds its warm-up)
     launches = {}
     order = []
     with open(args.traffic_from) as f:
@@ -123,8 +125,6 @@ def traffic_from_csv(args, w):
     for row in csv.DictReader(lines):
         name = row.get("Kernel Name", "")
         base = name.split("(")[0].split("<")[0].split("::")[-1].strip().split()[-1] if name.strip() else ""
-        if base not in TRAFFIC_KERNELS:
-            continue
         key = row["ID"]
         if key not in launches:
             launches[key] = {"kernel": base, "bytes": 0.0}
@@ -133,6 +133,10 @@ def traffic_from_csv(args, w):
         scale = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}.get(unit, 1)
         if row["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             launches[key]["bytes"] += float(row["Metric Value"].replace(",", "")) * scale
+    starts = [i for i, key in enumerate(order) if launches[key]["kernel"] == "init_perm_kernel"]
+    if starts:
+        order = order[starts[-1]:]
+    order = [key for key in order if launches[key]["kernel"] in TRAFFIC_KERNELS]
     per = {}
     for key in order:
         per.setdefault(launches[key]["kernel"], []).append(launches[key]["bytes"])
@@ -140,7 +144,7 @@ def traffic_from_csv(args, w):
     for kname, vals in per.items():
         unit = TRAFFIC_KERNELS[kname]
         if unit == "point-round":
-            out[kname] = {"unit": unit, "bytes_per_unit": [v / n for v in vals[-R:]]}
+            out[kname] = {"unit": unit, "bytes_per_unit": [v / n for v in vals]}
         elif unit == "point-tree":
             out[kname] = {"unit": unit, "bytes_per_unit": sum(vals) / (n * T)}
         elif unit == "point":
@@ -524,6 +528,8 @@ def main():
                     help="ncu --csv launch list of --profile-case with dram__bytes_{read,write}.sum: record the "
                          "kernels' DRAM bytes per unit under profiles/ and exit")
     ap.add_argument("--traffic-command", default=None, help="the ncu command line, recorded with the traffic")
+    ap.add_argument("--traffic-full", action="store_true",
+                    help="--traffic-from holds a capture of the full workload (not of --profile-case)")
     ap.add_argument("--traffic-hash", default=None,
                     help="source_hash printed by the profiled --profile-case run (the kernels the counts belong to)")
     args = ap.parse_args()

@@ -61,6 +61,22 @@ __device__ __forceinline__ uint64_t pack_key(float dist, uint32_t id)
     return ((uint64_t)ord_key(dist) << 32) | id;
 }
 
+// Asynchronous global-to-shared copies (cp.async): 16 bytes (zero-filled past
+// src_bytes) or 4 bytes; completion by commit groups.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------------------
 // Row loads.  Point i of X starts at element i*ld; d entries.  load4 returns
 // entries j..j+3 (zero past d) widened to FP32.  Element types: FP32, FP16
@@ -151,6 +167,18 @@ struct RowLoader {
     // every partial sum of the canonical FP32 distance is then an exact
     // integer, so integer arithmetic in any order gives the same value
     __device__ __forceinline__ bool int_exact() const { return kDT == kDtU8 && d <= 256; }
+
+    // L2 prefetch of row i, one 128-byte line per lane (the lines that hold
+    // the row's d entries only)
+    __device__ __forceinline__ void prefetch_l2(int64_t i, int lane) const
+    {
+        constexpr int es = kDT == kDtF16 ? 2 : kDT == kDtU8 ? 1 : 4;
+        const char* row = static_cast<const char*>(X) + row_off(i) * es;
+        const uintptr_t first = (uintptr_t)row & ~(uintptr_t)127;
+        const uintptr_t end = (uintptr_t)row + (uintptr_t)d * es;
+        for (uintptr_t a = first + 128 * (uintptr_t)lane; a < end; a += 4096)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a < (uintptr_t)row ? (uintptr_t)row : a));
+    }
 
     __device__ __forceinline__ float load1(int64_t i, int j) const
     {

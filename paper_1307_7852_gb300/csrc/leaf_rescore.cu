@@ -30,15 +30,6 @@ constexpr int kSlice = 32;       // floats per row and slice (one block of the d
 constexpr int kMaxCand = 32;     // candidates per row handled here
 }  // namespace
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // Canonical block value of a pair: own slice a (columns in the order
 // u ^ x, u = 0..7, already in registers), candidate slice b in shared
 // memory.  s[u] is the partial of column u ^ x; since the block's butterfly

@@ -59,6 +59,8 @@ __device__ __forceinline__ void gather_quant_body(const Loader& L, int64_t rows,
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = gw; r < rows; r += nw) {
         const int32_t id = perm[r];
+        // the warp's next row streams into L2 while this one is converted
+        if (r + nw < rows) L.prefetch_l2(perm[r + nw], lane);
         float s = 0.f;
         bool ex = true;
         if (PREC == 1) {

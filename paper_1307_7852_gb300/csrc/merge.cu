@@ -9,8 +9,8 @@
 // has equal keys, so its copies go together); a neighbour seen again with
 // a different distance is dropped by the id check against the entries
 // already taken, and p itself is skipped.  A warp's rows (32 / GS points,
-// contiguous for every tree) are staged in shared memory with coalesced
-// loads; output slot s of a point is held by lane s % GS of its group.
+// contiguous for every tree) are staged in shared memory; output slot s of a
+// point is held by lane s % GS of its group.
 // With eight lanes a group also records, per output entry, the trees whose
 // rows held it (the lanes that advanced on it).
 #include "knng_common.cuh"
@@ -20,6 +20,8 @@ namespace knng {
 
 constexpr int kMergeThreads = 128;
 
+// Staging: the ids and distances of a warp's rows land in shared memory by
+// 4-byte cp.async copies, all of a batch in flight at once.
 template <int GS, int R>
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, int k,
                                                               const int32_t* __restrict__ ids_in,
@@ -30,26 +32,30 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
 {
     constexpr int PPW = 32 / GS;  // points per warp
     constexpr int NW = kMergeThreads / 32;
-    extern __shared__ unsigned long long mstage[];
+    extern __shared__ __align__(16) int32_t mraw[];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int grp = lane / GS, j = lane % GS;
-    const int ks = k | 1;  // odd row stride (in keys): 64-bit accesses of a half warp avoid bank conflicts
-    unsigned long long* wk = mstage + (size_t)wq * 32 * ks;  // [PPW][GS][ks]
+    const int ks = k | 1;  // odd row stride: a group's lanes read rows in different banks
+    const int buf_words = 2 * 32 * ks;  // ids [PPW][GS][ks], then distances
+    int32_t* wbuf = mraw + (size_t)wq * buf_words;
     const unsigned gmask = GS == 32 ? 0xFFFFFFFFu : (((1u << GS) - 1u) << (grp * GS));
     const int64_t step = (int64_t)gridDim.x * NW * PPW;
     // tree masks (GS == 8) only when every leaf list was exact
     const bool masks = GS == 8 && tmask && all_exact && *all_exact != 0;
-    for (int64_t wbase = ((int64_t)blockIdx.x * NW + wq) * PPW; wbase < n; wbase += step) {
+    const int dpp = 32 / k, dh = 32 - (32 / k) * k;
+    // for every tree the rows of a batch's points are contiguous; entry
+    // e = pp k + h of them, advanced by 32 without division
+    auto stage = [&](int64_t wbase) {
+        int32_t* sid = wbuf;
+        float* sd = reinterpret_cast<float*>(sid + 32 * ks);
         const int np = (int)(n - wbase < PPW ? n - wbase : PPW);
-        // stage: for every tree the rows of the warp's points are contiguous;
-        // entry e = pp k + h of them, advanced by 32 without division
-        const int dpp = 32 / k, dh = 32 - (32 / k) * k;
         for (int t = 0; t < T; ++t) {
             const int64_t src = ((int64_t)t * n + wbase) * k;
             int pp = lane / k, h = lane - (lane / k) * k;
             for (int e = lane; e < np * k; e += 32) {
-                const int32_t id = ids_in[src + e];
-                wk[(pp * GS + t) * ks + h] = id >= 0 ? pack_key(d_in[src + e], (uint32_t)id) : kKeyMax;
+                const int o = (pp * GS + t) * ks + h;
+                cp_async4(sid + o, ids_in + src + e);
+                cp_async4(sd + o, d_in + src + e);
                 pp += dpp;
                 h += dh;
                 if (h >= k) {
@@ -58,13 +64,24 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
                 }
             }
         }
+    };
+    for (int64_t wbase = ((int64_t)blockIdx.x * NW + wq) * PPW; wbase < n; wbase += step) {
+        stage(wbase);
+        cp_async_commit();
+        cp_async_wait<0>();
         __syncwarp();
+        const int np = (int)(n - wbase < PPW ? n - wbase : PPW);
         const int64_t p = wbase + grp;
         const bool live = grp < np;
-        const unsigned long long* row = wk + (grp * GS + j) * ks;
+        const int32_t* rid = wbuf + (grp * GS + j) * ks;
+        const float* rd = reinterpret_cast<const float*>(wbuf + 32 * ks) + (grp * GS + j) * ks;
+        auto row = [&](int h) -> unsigned long long {
+            const int32_t id = rid[h];
+            return id >= 0 ? pack_key(rd[h], (uint32_t)id) : kKeyMax;
+        };
         int h = 0;
         // a row ends at its first empty entry (kKeyMax); trees j >= T are empty
-        unsigned long long key = (live && j < T) ? row[0] : kKeyMax;
+        unsigned long long key = (live && j < T) ? row(0) : kKeyMax;
         unsigned long long o[R];
         uint32_t om[R];  // trees of the held entries
 #pragma unroll
@@ -93,7 +110,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
                     if constexpr (GS == 8) trees = (__ballot_sync(gmask, hit) >> (grp * GS)) & 0xFFu;
                     if (hit) {
                         ++h;
-                        key = h < k ? row[h] : kKeyMax;
+                        key = h < k ? row(h) : kKeyMax;
                     }
                     const int32_t id = (int32_t)(uint32_t)best;
                     const unsigned long long bit = 1ull << (((uint32_t)id * 0x9E3779B1u) >> 26);
@@ -129,7 +146,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(int64_t n, int T, 
                 }
             }
         }
-        __syncwarp();  // the staged rows are read before the next batch lands
+        __syncwarp();  // the rows are read before the next batch lands
     }
 }
 
@@ -141,14 +158,20 @@ static cudaError_t launch_merge(int64_t n, int T, int k, const int32_t* ids_in, 
     if (!attr) {
         const cudaError_t e =
             cudaFuncSetAttribute(merge_kernel<GS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((kMergeThreads / 32) * 32 * (kMaxK | 1) * sizeof(unsigned long long)));
+                                 (int)((kMergeThreads / 32) * 2 * 32 * (kMaxK | 1) * sizeof(int32_t)));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const size_t smem = (size_t)(kMergeThreads / 32) * 32 * (k | 1) * sizeof(unsigned long long);
+    const size_t smem = (size_t)(kMergeThreads / 32) * 2 * 32 * (k | 1) * sizeof(int32_t);
     const int64_t per_block = (int64_t)(kMergeThreads / 32) * (32 / GS);
     const int64_t want = (n + per_block - 1) / per_block;
-    const int grid = (int)(want < (1 << 20) ? want : (1 << 20));
+    // resident blocks only: each warp then merges many batches, with the
+    // next batch's copies in flight
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, merge_kernel<GS, R>, kMergeThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t resident = (int64_t)num_sms() * per_sm;
+    const int grid = (int)(want < resident ? want : resident);
     merge_kernel<GS, R><<<grid, kMergeThreads, smem, st>>>(n, T, k, ids_in, d_in, ids, dists, tmask, all_exact);
     return cudaSuccess;
 }

@@ -316,6 +316,9 @@ __device__ __forceinline__ void project_body(const Loader& L, int64_t n, int T, 
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < n; i += nwarps) {
+        // the warp's next row streams into L2 while this one is projected: the
+        // chunk loads below then wait on L2, not on DRAM
+        if (i + nwarps < n) L.prefetch_l2(i + nwarps, lane);
         for (int t0 = 0; t0 < T; t0 += 8) {
             const int tl = t0 + lane;
             const int my_s = (lane < 8 && tl < T) ? node_of[(int64_t)tl * n + i] : -1;
