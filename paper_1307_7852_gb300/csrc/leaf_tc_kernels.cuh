@@ -405,12 +405,11 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
     // ---- epilogue -------------------------------------------------------
     // Row per thread first: thread (quad, half) owns row 32 quad + lane and
     // the column chunks 32 half + 64 i of it.  Pass 1 takes the minimum of
-    // the distance parts (high 32 bits of the keys) over the columns with
-    // the same position in their chunk (32 groups per thread), sorts them;
-    // the want-th smallest of the 64 minima of a row (both halves) bounds the
-    // row's answer.  Pass 2 lists the columns up to that bound, and the
-    // half-0 thread sorts the union of the row's two lists (at most 32) with
-    // a register network.  Rows whose lists overflow, and all rows when more
+    // the distances over the columns with the same position in their chunk
+    // (32 groups per thread), sorts them; the want-th smallest of the 64
+    // minima of a row (both halves) bounds the row's answer.  Pass 2 lists
+    // the columns up to that bound, and the half-0 thread sorts the union of
+    // the row's two lists (at most 32) with a register network.  Rows whose lists overflow, and all rows when more
     // than 32 candidates are wanted, take the warp-per-row path below.
     if (!abort_flag) {
         const int quad = w & 3, half = w >> 2;
@@ -431,76 +430,77 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
         const int il = min(iloc, G.N_load - 1);
         const float ni = qn[il], si = qs[il];
         const uint32_t trow = tbase + ((uint32_t)(32 * quad) << 16);
-        auto hi_of = [&](uint32_t raw, int j) -> uint32_t {
-            const int jj = min(j, G.N_load - 1);
-            const float sdot = __uint_as_float(raw);
-            float dv;
-            if (PREC == 1) dv = ni + qn[jj] - 2.f * sdot;
-            else dv = si * si * ni + qs[jj] * qs[jj] * qn[jj] - 2.f * si * qs[jj] * sdot;
-            const bool valid = row_ok && j < m && j != iloc;
-            return valid ? ord_key(dv) : 0xFFFFFFFFu;
-        };
-        // the distance parts of one chunk of 32 columns (BF16): the norms of
-        // the columns read as float4; only the self column and, in the last
-        // chunk, columns past the leaf are invalid (rows past the leaf are
-        // never output, so their values do not matter)
-        auto chunk_hi = [&](const uint32_t (&r)[32], int c0, uint32_t (&h)[32]) {
-            const bool tail = c0 + 32 > m;
+        // the distances of one chunk of 32 columns (FP32, as the keys take
+        // them); columns past the leaf (last chunk) and the row's own column
+        // read +inf.  The own column is column `lane` of the chunk r0 + 32 quad,
+        // the same chunk for the whole warp.
+        const int cself = r0 + 32 * quad;
+        const float kInf = __int_as_float(0x7f800000);
+        auto chunk_dv = [&](const uint32_t (&r)[32], int c0, float (&dv)[32]) {
+            if (PREC == 1) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 q = *reinterpret_cast<const float4*>(qn + c0 + 4 * i);
-                const float qv[4] = {q.x, q.y, q.z, q.w};
+                for (int i = 0; i < 8; ++i) {
+                    const float4 q = *reinterpret_cast<const float4*>(qn + c0 + 4 * i);
+                    const float qv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int e2 = 0; e2 < 4; ++e2) {
-                    const int e = 4 * i + e2;
-                    const float dv = ni + qv[e2] - 2.f * __uint_as_float(r[e]);
-                    uint32_t x = ord_key(dv);
-                    x = (c0 + e == iloc) ? 0xFFFFFFFFu : x;
-                    if (tail) x = (c0 + e < m) ? x : 0xFFFFFFFFu;
-                    h[e] = x;
+                    for (int e2 = 0; e2 < 4; ++e2)
+                        dv[4 * i + e2] = ni + qv[e2] - 2.f * __uint_as_float(r[4 * i + e2]);
                 }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const int jj = min(c0 + e, G.N_load - 1);
+                    dv[e] = si * si * ni + qs[jj] * qs[jj] * qn[jj] - 2.f * si * qs[jj] * __uint_as_float(r[e]);
+                }
+            }
+            if (c0 + 32 > m) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) dv[e] = (c0 + e < m) ? dv[e] : kInf;
+            }
+            if (c0 == cself) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) dv[e] = (e == lane) ? kInf : dv[e];
             }
         };
         if (fast) {
-            // pass 1: group minima
-            uint32_t gm[32];
+            // pass 1: group minima of the distances (a float bound: keys
+            // order as their distances do, so the want-th smallest minimum
+            // bounds the row's answer as its key would)
+            float gm[32];
 #pragma unroll
-            for (int e = 0; e < 32; ++e) gm[e] = 0xFFFFFFFFu;
+            for (int e = 0; e < 32; ++e) gm[e] = kInf;
             for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
                 uint32_t r[32];
                 tc::tmem_ld32(trow + (uint32_t)c0, r);
                 tc::tmem_ld_wait();
-                if (PREC == 1) {
-                    uint32_t h[32];
-                    chunk_hi(r, c0, h);
+                float dv[32];
+                chunk_dv(r, c0, dv);
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) gm[e] = min(gm[e], h[e]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) gm[e] = min(gm[e], hi_of(r[e], c0 + e));
-                }
+                for (int e = 0; e < 32; ++e) gm[e] = fminf(gm[e], dv[e]);
             }
             reg_bitonic_sort(gm);
+            float* gshf = reinterpret_cast<float*>(gsh);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) gsh[e * kTcThreads + tid] = gm[e];
+            for (int e = 0; e < 32; ++e) gshf[e * kTcThreads + tid] = gm[e];
             __syncthreads();
             // the want-th smallest of the row's 64 minima (two sorted lists
             // A, B): binary search for the number i of them taken from A, the
             // smallest i with A[i] >= B[want - i - 1]
             const int ptid = tid ^ 128;
-            uint32_t tau;
+            float tau;
             {
                 int lo = max(0, want - 32), hi = min(want, 32);
                 while (lo < hi) {
                     const int i = (lo + hi) >> 1;
-                    const uint32_t a = gsh[i * kTcThreads + tid];  // i < hi <= 32
-                    const uint32_t b = gsh[(want - i - 1) * kTcThreads + ptid];
+                    const float a = gshf[i * kTcThreads + tid];  // i < hi <= 32
+                    const float b = gshf[(want - i - 1) * kTcThreads + ptid];
                     if (a >= b) hi = i;
                     else lo = i + 1;
                 }
-                const uint32_t ta = lo > 0 ? gsh[(lo - 1) * kTcThreads + tid] : 0u;
-                const uint32_t tb = want - lo > 0 ? gsh[(want - lo - 1) * kTcThreads + ptid] : 0u;
-                tau = max(ta, tb);
+                const float ta = lo > 0 ? gshf[(lo - 1) * kTcThreads + tid] : -kInf;
+                const float tb = want - lo > 0 ? gshf[(want - lo - 1) * kTcThreads + ptid] : -kInf;
+                tau = fmaxf(ta, tb);
+                if (tau == kInf) tau = __int_as_float(0x7f7fffff);  // the invalid columns stay out
             }
             // pass 2: the candidates up to the bound
             int c = 0;
@@ -508,17 +508,12 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 uint32_t r[32];
                 tc::tmem_ld32(trow + (uint32_t)c0, r);
                 tc::tmem_ld_wait();
-                uint32_t h[32];
-                if (PREC == 1) {
-                    chunk_hi(r, c0, h);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) h[e] = hi_of(r[e], c0 + e);
-                }
+                float dv[32];
+                chunk_dv(r, c0, dv);
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
-                    if (h[e] != 0xFFFFFFFFu && h[e] <= tau) {
-                        if (c < 32) cand[c * kTcThreads + tid] = ((uint64_t)h[e] << 32) | (uint32_t)(c0 + e);
+                    if (dv[e] <= tau) {
+                        if (c < 32) cand[c * kTcThreads + tid] = ((uint64_t)ord_key(dv[e]) << 32) | (uint32_t)(c0 + e);
                         ++c;
                     }
                 }
