@@ -702,7 +702,11 @@ def main():
                 "list_slots_per_point": [float(counts[r, 1]) / n for r in range(R)],
                 "unique_candidates_per_point": u, "ms": sum(t_prop) * 1e3 / R,
                 "basis": "achieved = scored_bytes (rows scored and list slots loaded, counted on the device, "
-                         "+ each point's list, row and output) per launch / launch time"}
+                         "+ each point's list, row and output) per launch / launch time; rows that L2 serves "
+                         "(points run in leaf order) count here but not in dram_bytes, so frac may pass 1"}
+            if dram:
+                roof["propagate"]["dram_gbs"] = sum(dram) / sum(t_prop) / 1e9
+                roof["propagate"]["dram_frac"] = sum(dram) / sum(t_prop) / 1e9 / hbm
         # ---- leaf graphs: Gram flops of the distinct pairs (tensor pipe or
         # FP32 ALU), and the bytes the stage reads and writes
         gram_flops = T * float(np.sum(2.0 * d * m * (m - 1) / 2.0))

@@ -59,8 +59,6 @@ __device__ __forceinline__ void gather_quant_body(const Loader& L, int64_t rows,
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = gw; r < rows; r += nw) {
         const int32_t id = perm[r];
-        // the warp's next row streams into L2 while this one is converted
-        if (r + nw < rows) L.prefetch_l2(perm[r + nw], lane);
         float s = 0.f;
         bool ex = true;
         if (PREC == 1) {
@@ -265,7 +263,7 @@ __device__ __forceinline__ void reg_bitonic_sort(T (&v)[N])
 constexpr int kFastSmem = 32 * kTcThreads * 4 + 32 * kTcThreads * 8;
 
 template <int PREC, int PER, int kDT>
-__global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(kTcThreads, PER == 16 ? 1 : 2) leaf_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 RowLoader<kDT> L, int64_t n,
                                                                 const int32_t* __restrict__ perm,
                                                                 const int32_t* __restrict__ leaf_off,
@@ -462,6 +460,36 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                 for (int e = 0; e < 32; ++e) dv[e] = (e == lane) ? kInf : dv[e];
             }
         };
+        // the thread's chunks c0 = 32 half + 64 i in order; with leaves of
+        // more than 256 points (one CTA per SM, registers to spare) the next
+        // chunk's tensor-memory load is in flight while one is processed
+        auto for_chunks = [&](auto&& body) {
+            if constexpr (PER == 16) {
+                uint32_t ra[32], rb[32];
+                int c0 = 32 * half;
+                if (c0 < Nm) {
+                    tc::tmem_ld32(trow + (uint32_t)c0, ra);
+                    tc::tmem_ld_wait(ra);
+                }
+                for (; c0 < Nm; c0 += 128) {
+                    const int c1 = c0 + 64, c2 = c0 + 128;
+                    if (c1 < Nm) tc::tmem_ld32(trow + (uint32_t)c1, rb);
+                    body(ra, c0);
+                    if (c1 >= Nm) break;
+                    tc::tmem_ld_wait(rb);
+                    if (c2 < Nm) tc::tmem_ld32(trow + (uint32_t)c2, ra);
+                    body(rb, c1);
+                    if (c2 < Nm) tc::tmem_ld_wait(ra);
+                }
+            } else {
+                for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(trow + (uint32_t)c0, r);
+                    tc::tmem_ld_wait();
+                    body(r, c0);
+                }
+            }
+        };
         if (fast) {
             // pass 1: group minima of the distances (a float bound: keys
             // order as their distances do, so the want-th smallest minimum
@@ -469,15 +497,12 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
             float gm[32];
 #pragma unroll
             for (int e = 0; e < 32; ++e) gm[e] = kInf;
-            for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
-                uint32_t r[32];
-                tc::tmem_ld32(trow + (uint32_t)c0, r);
-                tc::tmem_ld_wait();
+            for_chunks([&](const uint32_t (&r)[32], int c0) {
                 float dv[32];
                 chunk_dv(r, c0, dv);
 #pragma unroll
                 for (int e = 0; e < 32; ++e) gm[e] = fminf(gm[e], dv[e]);
-            }
+            });
             reg_bitonic_sort(gm);
             float* gshf = reinterpret_cast<float*>(gsh);
 #pragma unroll
@@ -504,10 +529,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
             }
             // pass 2: the candidates up to the bound
             int c = 0;
-            for (int c0 = 32 * half; c0 < Nm; c0 += 64) {
-                uint32_t r[32];
-                tc::tmem_ld32(trow + (uint32_t)c0, r);
-                tc::tmem_ld_wait();
+            for_chunks([&](const uint32_t (&r)[32], int c0) {
                 float dv[32];
                 chunk_dv(r, c0, dv);
 #pragma unroll
@@ -517,7 +539,7 @@ __global__ void __launch_bounds__(kTcThreads) leaf_tc_kernel(const __grid_consta
                         ++c;
                     }
                 }
-            }
+            });
             if (c > 32 && row_ok) {
                 rowflag[lr] = 1;
                 any_overflow = 1;
