@@ -740,8 +740,14 @@ def main():
         rows_read = depth * n * d * s_el * (T if byte_rows else 1)
         part_read = rows_read + T * depth * 16 * n
         t_part = stage_ms["partition"] / 1e3
+        # DRAM bytes of the projection kernels (the select and scatter
+        # kernels are not in the record)
+        pdram = None
+        if traffic and plain:
+            pk = [tr[kn]["bytes_per_unit"] * n for kn in ("project_kernel", "project_bytes_tma_kernel") if kn in tr]
+            pdram = sum(pk) if pk else None
         roof["partition"] = {"bound": "hbm", "achieved": part_read / t_part / 1e9, "peak": hbm, "unit": "GB/s",
-                             "frac": part_read / t_part / 1e9 / hbm, "traffic": None,
+                             "frac": part_read / t_part / 1e9 / hbm, "traffic": pdram,
                              "read_bytes": part_read, "survey_bytes": part_survey,
                              "survey_achieved": part_survey / t_part / 1e9, "levels": depth}
         if traffic:
