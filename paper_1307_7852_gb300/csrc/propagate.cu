@@ -63,6 +63,10 @@ static PropLayout prop_layout(int k)
     return L;
 }
 
+// Live list slots a later round can gather compactly (the per-warp key
+// scratch, 192 64-bit words, holds them until the selection).
+constexpr int kLiveCap = 384;
+
 // kMode: 1 = the first round after the merge, with the merge's tree masks
 // and no flags; 2 = a later first-order round, with flags; 0 = any other
 // (flags optional, pairwise offers possible).  Separate instantiations, so
@@ -139,12 +143,68 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         if (kMode == 1)
             for (int e = lane; e < k; e += 32) own_tm[e] = tm_in[(int64_t)p * k + e];
         __syncwarp();
-        // the neighbours' lists, lanes over (neighbour e, slot f) with
+        constexpr int G = 4;  // list loads in flight per lane before the hash inserts
+        // with flags, the live slots (q new in p's list, or c new in q's) are
+        // listed first, (e << 8) | f, so the loop below runs over them only:
+        // a later round loads about a third of the k*k slots
+        int nlive = kLiveCap + 1;  // no list: the loop over all slots below
+        int* live = reinterpret_cast<int*>(keys);  // free until the selection
+        if (use_flags) {
+            const unsigned long long kmask = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
+            nlive = 0;
+            for (int e0 = 0; e0 < k; e0 += 32) {
+                const int e = e0 + lane;
+                unsigned long long msk = 0ull;
+                if (e < k) {
+                    const int32_t q = own[e];
+                    if (q >= 0 && q != p) msk = ((pf >> e) & 1ull) ? kmask : (own_fl[e] & kmask);
+                }
+                const int c = __popcll(msk);
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(KNNG_FULL_MASK, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                int j = nlive + incl - c;
+                nlive += __shfl_sync(KNNG_FULL_MASK, incl, 31);
+                if (j + c <= kLiveCap)
+                    while (msk) {
+                        live[j++] = (e << 8) | (__ffsll((long long)msk) - 1);
+                        msk &= msk - 1ull;
+                    }
+            }
+            __syncwarp();
+        }
+        if (nlive <= kLiveCap) {
+            for (int i0 = 0; i0 < nlive; i0 += 32 * G) {
+                int32_t o[G];
+#pragma unroll
+                for (int gi = 0; gi < G; ++gi) {
+                    o[gi] = -1;
+                    const int i = i0 + 32 * gi + lane;
+                    if (i < nlive) {
+                        const int v = live[i];
+                        o[gi] = ids_in[(int64_t)own[v >> 8] * k + (v & 255)];
+                        if (stats) ++n_slots;
+                    }
+                }
+#pragma unroll
+                for (int gi = 0; gi < G; ++gi) {
+                    const int32_t oo = o[gi] < n ? o[gi] : -1;
+                    const bool ins = oo >= 0 && hash_insert(tab, (uint32_t)hshift, hmask, oo);
+                    const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
+                    if (ins) cid[cnt + __popc(b & lanemask_lt())] = oo;
+                    cnt += __popc(b);
+                }
+            }
+            nlive = -1;  // done
+        }
+        // otherwise lanes over (neighbour e, slot f) with
         // i = e*k + f = lane + 32*step, advanced without division
         int e = lane / k, f = lane - (lane / k) * k;
         const int de = 32 / k, df = 32 - (32 / k) * k;
-        constexpr int G = 4;  // list loads in flight per lane before the hash inserts
-        for (int i0 = 0; i0 < kk; i0 += 32 * G) {
+        for (int i0 = 0; i0 < (nlive < 0 ? 0 : kk); i0 += 32 * G) {
             int32_t o[G];
 #pragma unroll
             for (int gi = 0; gi < G; ++gi) {
