@@ -63,10 +63,6 @@ static PropLayout prop_layout(int k)
     return L;
 }
 
-// Live list slots a later round can gather compactly (the per-warp key
-// scratch, 192 64-bit words, holds them until the selection).
-constexpr int kLiveCap = 384;
-
 // kMode: 1 = the first round after the merge, with the merge's tree masks
 // and no flags; 2 = a later first-order round, with flags; 0 = any other
 // (flags optional, pairwise offers possible).  Separate instantiations, so
@@ -144,12 +140,17 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
             for (int e = lane; e < k; e += 32) own_tm[e] = tm_in[(int64_t)p * k + e];
         __syncwarp();
         constexpr int G = 4;  // list loads in flight per lane before the hash inserts
-        // with flags, the live slots (q new in p's list, or c new in q's) are
-        // listed first, (e << 8) | f, so the loop below runs over them only:
-        // a later round loads about a third of the k*k slots
-        int nlive = kLiveCap + 1;  // no list: the loop over all slots below
-        int* live = reinterpret_cast<int*>(keys);  // free until the selection
-        if (use_flags) {
+        // The live slots are listed first, (e << 8) | f, so the loop below
+        // runs over them only: with flags, q new in p's list or c new in q's
+        // (a later round loads about a third of the k*k slots); in the first
+        // round, c not sharing an exact leaf with p and q (the lane of
+        // neighbour q reads q's k tree masks, and only the live ids are
+        // loaded)
+        int nlive = -1;  // no list: the loop over all slots below
+        // the list sits in the candidate-distance array past p's own entries
+        // (free until the scoring, room for all k*k slots)
+        int* live = reinterpret_cast<int*>(cd) + nknown;
+        if (use_flags || kMode == 1) {
             const unsigned long long kmask = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
             nlive = 0;
             for (int e0 = 0; e0 < k; e0 += 32) {
@@ -157,7 +158,28 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                 unsigned long long msk = 0ull;
                 if (e < k) {
                     const int32_t q = own[e];
-                    if (q >= 0 && q != p) msk = ((pf >> e) & 1ull) ? kmask : (own_fl[e] & kmask);
+                    if (q >= 0 && q != p) {
+                        const int ot = kMode == 1 ? own_tm[e] : 0;
+                        if (ot == 0) {
+                            // no shared leaf known (or no masks: some leaf
+                            // was not exact): every slot, and with flags the
+                            // new ones
+                            msk = (!use_flags || ((pf >> e) & 1ull)) ? kmask : (own_fl[e] & kmask);
+                        } else {
+                            const uint8_t* tq = tm_in + (int64_t)q * k;
+                            if ((k & 3) == 0) {
+                                for (int f0 = 0; f0 < k; f0 += 4) {
+                                    const uint32_t w4 = *reinterpret_cast<const uint32_t*>(tq + f0);
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b)
+                                        if ((((w4 >> (8 * b)) & 0xFFu) & (uint32_t)ot) == 0u) msk |= 1ull << (f0 + b);
+                                }
+                            } else {
+                                for (int f = 0; f < k; ++f)
+                                    if ((tq[f] & ot) == 0) msk |= 1ull << f;
+                            }
+                        }
+                    }
                 }
                 const int c = __popcll(msk);
                 int incl = c;
@@ -168,15 +190,14 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                 }
                 int j = nlive + incl - c;
                 nlive += __shfl_sync(KNNG_FULL_MASK, incl, 31);
-                if (j + c <= kLiveCap)
-                    while (msk) {
-                        live[j++] = (e << 8) | (__ffsll((long long)msk) - 1);
-                        msk &= msk - 1ull;
-                    }
+                while (msk) {
+                    live[j++] = (e << 8) | (__ffsll((long long)msk) - 1);
+                    msk &= msk - 1ull;
+                }
             }
             __syncwarp();
         }
-        if (nlive <= kLiveCap) {
+        if (nlive >= 0) {
             for (int i0 = 0; i0 < nlive; i0 += 32 * G) {
                 int32_t o[G];
 #pragma unroll
@@ -198,13 +219,12 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                     cnt += __popc(b);
                 }
             }
-            nlive = -1;  // done
         }
         // otherwise lanes over (neighbour e, slot f) with
         // i = e*k + f = lane + 32*step, advanced without division
         int e = lane / k, f = lane - (lane / k) * k;
         const int de = 32 / k, df = 32 - (32 / k) * k;
-        for (int i0 = 0; i0 < (nlive < 0 ? 0 : kk); i0 += 32 * G) {
+        for (int i0 = 0; i0 < (nlive >= 0 ? 0 : kk); i0 += 32 * G) {
             int32_t o[G];
 #pragma unroll
             for (int gi = 0; gi < G; ++gi) {
