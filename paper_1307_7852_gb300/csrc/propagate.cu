@@ -99,25 +99,60 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long n_rows = 0, n_slots = 0;  // what this lane read (stats)
+    const bool use_flags = kMode == 2 || (kMode == 0 && flags_in != nullptr);
+    // The warp's next point, its own list, flags and tree masks are fetched
+    // while the current point is processed (and the point after it is
+    // looked up in the order), so a point starts with them in registers.
+    auto point_at = [&](int64_t w2) -> int32_t {
+        return w2 < n ? (order ? order[w2] : (int32_t)w2) : -1;
+    };
+    int32_t nid[E], ntm[E];
+    float nd[E];
+    unsigned long long npf = ~0ull;
+    auto fetch = [&](int32_t p2) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int e = 32 * q + lane;
+            const bool v = p2 >= 0 && e < k;
+            nid[q] = v ? ids_in[(int64_t)p2 * k + e] : -1;
+            nd[q] = v ? d_in[(int64_t)p2 * k + e] : 0.f;
+            ntm[q] = (kMode == 1 && v) ? (int)tm_in[(int64_t)p2 * k + e] : 0;
+        }
+        npf = (use_flags && p2 >= 0) ? flags_in[p2] : ~0ull;
+    };
+    int32_t p_next = point_at(gw), p_next2 = point_at(gw + nw);
+    fetch(p_next);
     for (int64_t wi = gw; wi < n; wi += nw) {
-        const int32_t p = order ? order[wi] : (int32_t)wi;
+        const int32_t p = p_next;
+        int32_t myid[E], mytm[E];
+        float myd[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            myid[q] = nid[q];
+            myd[q] = nd[q];
+            mytm[q] = ntm[q];
+        }
+        const unsigned long long pf = npf;
+        p_next = p_next2;
+        p_next2 = point_at(wi + 2 * nw);
+        fetch(p_next);
         for (int s = lane * 4; s < H; s += 128) *reinterpret_cast<int4*>(tab + s) = make_int4(-1, -1, -1, -1);
         __syncwarp();
         if (lane == 0) hash_insert(tab, (uint32_t)hshift, hmask, p);
-        const bool use_flags = kMode == 2 || (kMode == 0 && flags_in != nullptr);
-        const unsigned long long pf = use_flags ? flags_in[p] : ~0ull;
         __syncwarp();
         // p's own list: ids keep their distances
         int cnt = 0;
-        for (int e0 = 0; e0 < k; e0 += 32) {
-            const int e = e0 + lane;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int e = 32 * q + lane;
             int32_t id = -1;
             float dd = 0.f;
             if (e < k) {
-                id = ids_in[(int64_t)p * k + e];
-                dd = d_in[(int64_t)p * k + e];
+                id = myid[q];
+                dd = myd[q];
                 if (id >= n) id = -1;  // ids outside [0, n) are treated as empty slots
                 own[e] = id;
+                if (kMode == 1) own_tm[e] = mytm[q];
             }
             const bool ins = id >= 0 && hash_insert(tab, (uint32_t)hshift, hmask, id);
             const uint32_t b = __ballot_sync(KNNG_FULL_MASK, ins);
@@ -135,9 +170,6 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
                 const int32_t q = own[e];
                 own_fl[e] = q >= 0 ? flags_in[q] : 0ull;
             }
-        // trees whose (exact) leaf lists held p's entries
-        if (kMode == 1)
-            for (int e = lane; e < k; e += 32) own_tm[e] = tm_in[(int64_t)p * k + e];
         __syncwarp();
         constexpr int G = 4;  // list loads in flight per lane before the hash inserts
         // The live slots are listed first, (e << 8) | f, so the loop below
