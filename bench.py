@@ -156,6 +156,20 @@ def traffic_from_csv(args, w):
     rec = {"workload": args.workload, "precision": args.precision, "source_hash": args.traffic_hash,
            "case": {"n": n, **{k_: w[k_] for k_ in ("d", "k", "T", "g", "R")}, "centers": case["centers"]},
            "command": args.traffic_command or "", "per_unit": out}
+    if args.traffic_full:
+        # a full-size capture of some kernels (-k) refines the record of the
+        # profiling case for those kernels
+        try:
+            with open(traffic_path(args.workload, args.precision)) as f:
+                old = json.load(f)
+        except Exception:
+            old = None
+        if old and old.get("source_hash") == args.traffic_hash:
+            for kname in out:
+                old["per_unit"][kname] = dict(out[kname], n=n, command=args.traffic_command or "")
+            old.setdefault("full_size", [])
+            old["full_size"] = sorted(set(old["full_size"]) | set(out))
+            rec = old
     with open(traffic_path(args.workload, args.precision), "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))

@@ -109,6 +109,18 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
     int32_t nid[E], ntm[E];
     float nd[E];
     unsigned long long npf = ~0ull;
+    // and, with flags, once its list has arrived (fetched half way through
+    // a point), the flags of its neighbours' lists
+    unsigned long long nfl[E];
+    bool have_next = false;  // nfl holds the current point's
+    auto fetch_neigh = [&]() {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int e = 32 * q + lane;
+            const int32_t id = (e < k && nid[q] < n) ? nid[q] : -1;
+            nfl[q] = id >= 0 ? flags_in[id] : 0ull;
+        }
+    };
     auto fetch = [&](int32_t p2) {
 #pragma unroll
         for (int q = 0; q < E; ++q) {
@@ -133,6 +145,11 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
             mytm[q] = ntm[q];
         }
         const unsigned long long pf = npf;
+        unsigned long long myfl[E];
+        const bool have = have_next;
+#pragma unroll
+        for (int q = 0; q < E; ++q) myfl[q] = nfl[q];
+        have_next = false;
         p_next = p_next2;
         p_next2 = point_at(wi + 2 * nw);
         fetch(p_next);
@@ -165,11 +182,18 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
         }
         const int nknown = cnt;
         // flags of the neighbours' lists (entries of a list that are new)
-        if (use_flags)
-            for (int e = lane; e < k; e += 32) {
-                const int32_t q = own[e];
-                own_fl[e] = q >= 0 ? flags_in[q] : 0ull;
+        if (use_flags) {
+            if (have) {
+#pragma unroll
+                for (int q = 0; q < E; ++q)
+                    if (32 * q + lane < k) own_fl[32 * q + lane] = myfl[q];
+            } else {
+                for (int e = lane; e < k; e += 32) {
+                    const int32_t q = own[e];
+                    own_fl[e] = q >= 0 ? flags_in[q] : 0ull;
+                }
             }
+        }
         __syncwarp();
         constexpr int G = 4;  // list loads in flight per lane before the hash inserts
         // The live slots are listed first, (e << 8) | f, so the loop below
@@ -291,6 +315,12 @@ __global__ void __launch_bounds__(256, KNNG_PROP_MINBLOCKS) propagate_kernel(Row
             }
         }
         __syncwarp();
+        // the next point's list has arrived by now: fetch its neighbours'
+        // flags
+        if (use_flags && p_next >= 0) {
+            fetch_neigh();
+            have_next = true;
+        }
         if (stats && lane == 0) n_rows += (unsigned long long)(cnt - nknown);
         // score the new candidates, 32 at a time
         if (lane_X && (kDT == kDtU8 || bytes)) {
