@@ -81,3 +81,15 @@ def test_bf16_build_integer_matches_oracle():
     oi, od = oracle.build_graph(X, 10, 4, 64, 1, 7)
     assert_lists_exact(host(gi), host(gd), oi, od)
     knng().knng_sync()
+
+
+@pytest.mark.parametrize("k,T,g,R", [(12, 4, 64, 3), (40, 3, 128, 2)])
+def test_bf16_build_tree_masks_and_flags_exact(k, T, g, R):
+    # exact leaves: the first round skips by the merge's tree masks (k-byte
+    # mask rows read per neighbour, four to a word when k is a multiple of
+    # 4; two keys per lane when k > 32), later rounds by flags
+    X = synthetic.sift_like(8000, 64, centers=32, seed=21)
+    gi, gd = knng().knng_build(dev(X), k, T, g, R, 5, precision=BF16)
+    oi, od = oracle.build_graph(X, k, T, g, R, 5)
+    assert_lists_exact(host(gi), host(gd), oi, od)
+    knng().knng_sync()
