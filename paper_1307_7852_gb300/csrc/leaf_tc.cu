@@ -105,7 +105,12 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     const int elem = prec == 1 ? 2 : 1;
     const int slice = 128 / elem;
     const int dq = (x.d + slice - 1) / slice * slice;
-    const int64_t rows = (int64_t)T * x.n;
+    // rows of at least 1 KB in leaves of more than 256 points: one quantised
+    // copy in point order that the leaf kernel gathers from (the per-tree
+    // leaf-ordered copies would move T times the bytes through HBM); else a
+    // leaf-ordered copy per tree, streamed by the tensor map
+    const bool by_point = (int64_t)dq * elem >= 1024 && P.max_leaf > 256;
+    const int64_t rows = by_point ? x.n : (int64_t)T * x.n;
     uint8_t* Xq = ar.take<uint8_t>((size_t)rows * dq * elem);
     float* qn = ar.take<float>((size_t)rows);
     float* qs = ar.take<float>((size_t)rows);
@@ -115,11 +120,15 @@ cudaError_t run_leaf_knn_tc(const XDesc& x, const TreePlan& P, const DevPlan& dp
     // (their candidates in [rows][kp] local indices, a flag per leaf)
     const bool staged = leaf_rescore_staged_ok(x, kp, P.max_leaf);
     const int nleaves = (int)P.leaf_off.size() - 1;
-    uint16_t* cand = staged ? ar.take<uint16_t>((size_t)rows * kp) : nullptr;
+    uint16_t* cand = staged ? ar.take<uint16_t>((size_t)T * x.n * kp) : nullptr;
     uint8_t* leaf_flag = staged ? ar.take<uint8_t>((size_t)T * nleaves) : nullptr;
     if (!ar.base) return cudaSuccess;
     TcGeom G = tc_geometry(P, x.d, prec, tile);
     G.wait = wait_cycles > 0 ? wait_cycles : kWaitCycles;
+    if (by_point) {
+        G.xg = Xq;
+        G.xg_ld = (int64_t)dq * elem;
+    }
     if (G.smem > 227 * 1024) return cudaErrorInvalidConfiguration;
 
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();

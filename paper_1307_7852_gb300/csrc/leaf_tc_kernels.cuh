@@ -58,7 +58,7 @@ __device__ __forceinline__ void gather_quant_body(const Loader& L, int64_t rows,
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = gw; r < rows; r += nw) {
-        const int32_t id = perm[r];
+        const int32_t id = perm ? perm[r] : (int32_t)r;
         float s = 0.f;
         bool ex = true;
         if (PREC == 1) {
@@ -143,8 +143,8 @@ __device__ __forceinline__ void gather_bytes_bf16(const RowLoader<kDtU8>& Lb, in
     for (int64_t r0 = grp; r0 < rows; r0 += 2 * ngrp) {
         const int64_t r1 = r0 + ngrp;
         const bool two = r1 < rows;
-        const int32_t id0 = perm[r0];
-        const int32_t id1 = two ? perm[r1] : id0;
+        const int32_t id0 = perm ? perm[r0] : (int32_t)r0;
+        const int32_t id1 = two ? (perm ? perm[r1] : (int32_t)r1) : id0;
         uint4 u[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
         if (has) {
             u[0] = __ldg(reinterpret_cast<const uint4*>(X + Lb.row_off(id0) + 16 * q));
@@ -230,6 +230,8 @@ struct TcGeom {
     int wsc_off;     // offset of the warps' selection scratch in the pipeline region
     int smem;
     long long wait;  // limit of the producer's waits (copies landed, stage released)
+    const uint8_t* xg = nullptr;  // quantised rows in point order (else the leaf-ordered copy)
+    int64_t xg_ld = 0;            // their stride in bytes
 };
 
 // Bitonic sorting network on a thread's own registers (N a power of two;
@@ -276,6 +278,10 @@ __global__ void __launch_bounds__(kTcThreads, PER == 16 ? 1 : 2) leaf_tc_kernel(
                                                                 uint8_t* __restrict__ leaf_flag)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // the quantised rows in point order (null: the leaf-ordered copy of the
+    // tensor map; leaves of more than 256 points only)
+    const uint8_t* __restrict__ xg = PER == 16 ? G.xg : nullptr;
+    const int64_t xg_ld = G.xg_ld;
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* pipe = base;
     float* Dblk = reinterpret_cast<float*>(pipe);
@@ -305,13 +311,15 @@ __global__ void __launch_bounds__(kTcThreads, PER == 16 ? 1 : 2) leaf_tc_kernel(
 
     if (tid == 0) {
         for (int s = 0; s < G.S; ++s) {
-            tc::mbar_init(&full[s], 1);
+            // copies by the tensor map: one arrival (with the bytes); copies
+            // of the rows by the threads: every thread arrives
+            tc::mbar_init(&full[s], xg ? kTcThreads : 1);
             tc::mbar_init(&empty[s], 1);
         }
         tc::mbar_init(done, 1);
         tc::fence_mbar_init();
         abort_flag = 0;
-        tc::prefetch_tmap(&tmap);
+        if (!xg) tc::prefetch_tmap(&tmap);
     }
     if (w == 0) {
         tc::tmem_alloc(tslot, ncols);
@@ -321,10 +329,14 @@ __global__ void __launch_bounds__(kTcThreads, PER == 16 ? 1 : 2) leaf_tc_kernel(
     bool ex = PREC == 1;
     for (int j = tid; j < G.N_load; j += kTcThreads) {
         const bool v = j < m;
-        lid[j] = v ? perm[rowbase + j] : 0;
-        qn[j] = v ? qnrm[rowbase + j] : 0.f;
-        qs[j] = (PREC == 2 && v) ? qscl[rowbase + j] : 1.f;
-        if (v) ex = ex && qexact[rowbase + j];
+        const int32_t id = v ? perm[rowbase + j] : 0;
+        lid[j] = id;
+        // norms, scales and exactness by leaf position (leaf-ordered copy)
+        // or by point (the copy in point order)
+        const int64_t qi = xg ? (int64_t)id : rowbase + j;
+        qn[j] = v ? qnrm[qi] : 0.f;
+        qs[j] = (PREC == 2 && v) ? qscl[qi] : 1.f;
+        if (v) ex = ex && qexact[qi];
     }
     tc::fence_before_sync();
     // the whole leaf is exact: candidate distances are final, no rescoring
@@ -337,58 +349,126 @@ __global__ void __launch_bounds__(kTcThreads, PER == 16 ? 1 : 2) leaf_tc_kernel(
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
-    // ---- producer + MMA issuer (one thread) ------------------------------
-    if (tid == 0) {
-        constexpr uint32_t fmt = PREC == 1 ? 1u : 0u;  // BF16 | E4M3
+    // ---- producer + MMA issuer ----------------------------------------------
+    constexpr uint32_t fmt = PREC == 1 ? 1u : 0u;  // BF16 | E4M3
+    // the MMAs of K slice kc in stage s (one thread), then their commit to
+    // the stage's "empty" barrier
+    auto mma_slice = [&](int kc, int s) {
         const uint32_t id0 = tc::make_idesc(fmt, 128, (uint32_t)N0);
         const uint32_t id1 = tc::make_idesc(fmt, 128, (uint32_t)(N1 > 0 ? N1 : 16));
-        const int xstep = PREC == 1 ? 64 : 128;  // elements per 128-byte K slice
-        const int64_t yrow = rowbase;
-        int loaded = 0, consumed = 0;
-        bool ok = true;
-        auto load = [&](int kc) {
-            const int s = kc % G.S;
-            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(G.nbox * G.box_rows * 128));
-            for (int b = 0; b < G.nbox; ++b)
-                tc::tma_load_2d(pipe + (size_t)s * G.stage_bytes + (size_t)b * G.box_rows * 128, &tmap, &full[s],
-                                kc * xstep, (int)(yrow + (int64_t)b * G.box_rows));
-        };
-        for (; loaded < min(G.S, G.nK); ++loaded) load(loaded);
-        for (int kc = 0; kc < G.nK; ++kc) {
-            const int s = kc % G.S;
-            const uint32_t ph = (uint32_t)(kc / G.S) & 1u;
-            if (!tc::mbar_wait(&full[s], ph, G.wait)) { ok = false; break; }
-            consumed = kc + 1;
-            tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(pipe + (size_t)s * G.stage_bytes);
+        const uint32_t sa = tc::smem_u32(pipe + (size_t)s * G.stage_bytes);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = tc::sw128_desc(sa + (uint32_t)r0 * 128u + (uint32_t)kk * 32u);
-                const uint64_t bd0 = tc::sw128_desc(sa + (uint32_t)kk * 32u);
-                const uint32_t acc = (kc | kk) ? 1u : 0u;
-                if (PREC == 1) tc::mma_f16(tbase, ad, bd0, id0, acc);
-                else tc::mma_f8(tbase, ad, bd0, id0, acc);
-                if (N1 > 0) {
-                    const uint64_t bd1 = tc::sw128_desc(sa + 256u * 128u + (uint32_t)kk * 32u);
-                    if (PREC == 1) tc::mma_f16(tbase + 256, ad, bd1, id1, acc);
-                    else tc::mma_f8(tbase + 256, ad, bd1, id1, acc);
-                }
-            }
-            tc::mma_commit(&empty[s]);
-            if (kc + G.S < G.nK) {
-                if (!tc::mbar_wait(&empty[s], ph, G.wait)) { ok = false; break; }
-                load(kc + G.S);
-                ++loaded;
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::sw128_desc(sa + (uint32_t)r0 * 128u + (uint32_t)kk * 32u);
+            const uint64_t bd0 = tc::sw128_desc(sa + (uint32_t)kk * 32u);
+            const uint32_t acc = (kc | kk) ? 1u : 0u;
+            if (PREC == 1) tc::mma_f16(tbase, ad, bd0, id0, acc);
+            else tc::mma_f8(tbase, ad, bd0, id0, acc);
+            if (N1 > 0) {
+                const uint64_t bd1 = tc::sw128_desc(sa + 256u * 128u + (uint32_t)kk * 32u);
+                if (PREC == 1) tc::mma_f16(tbase + 256, ad, bd1, id1, acc);
+                else tc::mma_f8(tbase + 256, ad, bd1, id1, acc);
             }
         }
-        tc::mma_commit(done);
+        tc::mma_commit(&empty[s]);
+    };
+    if (PER != 16 || !xg) {
+        // the leaf's rows are contiguous in the leaf-ordered copy: one thread
+        // streams the K slices by the tensor map and issues the MMAs
+        if (tid == 0) {
+            const int xstep = PREC == 1 ? 64 : 128;  // elements per 128-byte K slice
+            const int64_t yrow = rowbase;
+            int loaded = 0, consumed = 0;
+            bool ok = true;
+            auto load = [&](int kc) {
+                const int s = kc % G.S;
+                tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(G.nbox * G.box_rows * 128));
+                for (int b = 0; b < G.nbox; ++b)
+                    tc::tma_load_2d(pipe + (size_t)s * G.stage_bytes + (size_t)b * G.box_rows * 128, &tmap,
+                                    &full[s], kc * xstep, (int)(yrow + (int64_t)b * G.box_rows));
+            };
+            for (; loaded < min(G.S, G.nK); ++loaded) load(loaded);
+            for (int kc = 0; kc < G.nK; ++kc) {
+                const int s = kc % G.S;
+                const uint32_t ph = (uint32_t)(kc / G.S) & 1u;
+                if (!tc::mbar_wait(&full[s], ph, G.wait)) { ok = false; break; }
+                consumed = kc + 1;
+                tc::fence_after_sync();
+                mma_slice(kc, s);
+                if (kc + G.S < G.nK) {
+                    if (!tc::mbar_wait(&empty[s], ph, G.wait)) { ok = false; break; }
+                    load(kc + G.S);
+                    ++loaded;
+                }
+            }
+            tc::mma_commit(done);
+            if (!ok) {
+                abort_flag = 1;
+                atomicExch(err, 1);
+                // wait (bounded, under the long limit whatever G.wait is) for
+                // the copies this CTA still has in flight
+                for (int kc = consumed; kc < loaded; ++kc)
+                    tc::mbar_wait(&full[kc % G.S], (uint32_t)(kc / G.S) & 1u, kWaitCycles);
+            }
+        }
+    } else if constexpr (PER == 16) {
+        // rows from the copy in point order (rows of xg_ld bytes; leaves of
+        // more than 256 points, one CTA per SM): every
+        // thread copies 16-byte chunks of the leaf's rows into the stage, in
+        // the 128-byte swizzled layout (chunk c of row r at c ^ (r mod 8)),
+        // S - 1 slices ahead; once a slice has landed each thread fences its
+        // writes for the tensor core and arrives; one thread waits for all
+        // and issues the slice's MMAs.  Rows past the leaf read zeros.
+        // Thread tid copies chunk c = tid mod 8 of rows tid / 8 + 32 i: the
+        // same rows in every slice, so their addresses are formed once, and
+        // r mod 8 (the swizzle) is the same for all of them.
+        bool ok = true;
+        const int cq = tid & 7, rq = tid >> 3;
+        const int nri = G.R_load / 32;  // rows per thread (R_load <= 512)
+        const uint8_t* rp[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int r = rq + 32 * i;
+            rp[i] = (i < nri && r < m) ? xg + (int64_t)lid[r] * xg_ld + 16 * cq : nullptr;
+        }
+        const size_t dst0 = (size_t)rq * 128 + ((cq ^ (rq & 7)) << 4);
+        for (int kc = 0; kc < G.nK + G.S - 1; ++kc) {
+            if (kc < G.nK) {
+                const int s = kc % G.S;
+                if (kc >= G.S && !tc::mbar_wait(&empty[s], (uint32_t)((kc / G.S) - 1) & 1u, G.wait)) ok = false;
+                unsigned char* dst = pipe + (size_t)s * G.stage_bytes + dst0;
+                if (ok) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (i < nri)
+                            cp_async16(dst + (size_t)i * 4096, rp[i] ? rp[i] + (int64_t)kc * 128 : xg,
+                                       rp[i] ? 16 : 0);
+                }
+                cp_async_commit();
+            }
+            const int kd = kc - (G.S - 1);
+            if (kd >= 0) {
+                const int pend = min(G.S - 1, G.nK - 1 - kd);  // later slices may stay in flight
+                if (pend >= 3) cp_async_wait<3>();
+                else if (pend == 2) cp_async_wait<2>();
+                else if (pend == 1) cp_async_wait<1>();
+                else cp_async_wait<0>();
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(&full[kd % G.S]);
+                if (tid == 0) {
+                    if (tc::mbar_wait(&full[kd % G.S], (uint32_t)(kd / G.S) & 1u, G.wait)) {
+                        tc::fence_after_sync();
+                        mma_slice(kd, kd % G.S);
+                    } else {
+                        ok = false;
+                    }
+                }
+            }
+        }
+        if (tid == 0) tc::mma_commit(done);
         if (!ok) {
             abort_flag = 1;
             atomicExch(err, 1);
-            // wait (bounded, under the long limit whatever G.wait is) for the
-            // copies this CTA still has in flight
-            for (int kc = consumed; kc < loaded; ++kc)
-                tc::mbar_wait(&full[kc % G.S], (uint32_t)(kc / G.S) & 1u, kWaitCycles);
         }
     }
     __syncthreads();
@@ -407,8 +487,9 @@ __global__ void __launch_bounds__(kTcThreads, PER == 16 ? 1 : 2) leaf_tc_kernel(
     // (32 groups per thread), sorts them; the want-th smallest of the 64
     // minima of a row (both halves) bounds the row's answer.  Pass 2 lists
     // the columns up to that bound, and the half-0 thread sorts the union of
-    // the row's two lists (at most 32) with a register network.  Rows whose lists overflow, and all rows when more
-    // than 32 candidates are wanted, take the warp-per-row path below.
+    // the row's two lists (at most 32) with a register network.  Rows whose
+    // lists overflow, and all rows when more than 32 candidates are wanted,
+    // take the warp-per-row path below.
     if (!abort_flag) {
         const int quad = w & 3, half = w >> 2;
         const int lr = 32 * quad + lane;
@@ -756,8 +837,9 @@ static cudaError_t dispatch_tc(const CUtensorMap& map, const XDesc& x, const Tre
                                     leaf_flag, st);
 }
 
-// Gather + quantise the leaf-ordered copy, then the leaf kernel, for one
-// element type of X (explicitly instantiated per type).
+// Gather + quantise the leaf-ordered copy (or quantise the rows once in
+// point order), then the leaf kernel, for one element type of X (explicitly
+// instantiated per type).
 // cand, leaf_flag (both or neither): candidates of the rows of leaves that
 // are not exact, for run_leaf_rescore_staged, and each leaf's exactness.
 template <int kDT>
@@ -766,7 +848,11 @@ cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const 
                         const TcGeom& G, int32_t* ids, float* dists, int* err, int* all_exact, uint16_t* cand,
                         uint8_t* leaf_flag, cudaStream_t st)
 {
-    const int64_t rows = (int64_t)T * x.n;
+    // G.xg set: one quantised copy in point order (the leaf kernel gathers
+    // the leaves' rows itself), else a leaf-ordered copy per tree
+    const bool by_point = G.xg != nullptr;
+    const int64_t rows = by_point ? x.n : (int64_t)T * x.n;
+    const int32_t* gperm = by_point ? nullptr : perm;
     const int gblocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16);
     RowLoader<kDT> rl{x.X, x.ld, x.d, x.vec};
     const RowLoader<kDtU8> rb{x.Xb, x.ldb, x.d, true};
@@ -774,10 +860,10 @@ cudaError_t leaf_tc_run(int prec, const CUtensorMap& map, const XDesc& x, const 
     const bool u8_aligned =
         x.dtype == kDtU8 && ((uintptr_t)x.X % 16 == 0) && (x.ld % 16 == 0) && (x.d % 16 == 0);
     if (prec == 1)
-        gather_quant_kernel<1, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx,
+        gather_quant_kernel<1, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, gperm, dq, Xq, qn, qs, qx,
                                                              u8_aligned);
     else
-        gather_quant_kernel<2, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, perm, dq, Xq, qn, qs, qx,
+        gather_quant_kernel<2, kDT><<<gblocks, 256, 0, st>>>(rl, rb, x.xb_bad, rows, gperm, dq, Xq, qn, qs, qx,
                                                              u8_aligned);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
