@@ -673,8 +673,8 @@ def main():
         roof = {}
         # ---- propagation: what the build's rounds read, counted on the device
         # (one more, untimed build with the read counters on), next to the
-        # survey's count k^2*4 + u*d*s + k*8 per point (u measured on a
-        # sample of the graphs the rounds start from)
+        # plain first-order count k^2*4 + u*d*s + k*8 per point ("survey
+        # bytes"; u measured on a sample of the graphs the rounds start from)
         if R > 0 and args.propagation == "first_order":
             cnt = torch.zeros(2 * R, dtype=torch.int64, device=dev)
             knng.knng_set_propagation_counters(cnt, h)
@@ -740,14 +740,14 @@ def main():
         if leaf_dram:
             roof["leaf_knn"]["dram_gbs"] = leaf_dram / t_leaf / 1e9
             roof["leaf_knn"]["dram_frac"] = leaf_dram / t_leaf / 1e9 / hbm
-        # ---- merge: (T + 1) k 8 bytes per point (survey), DRAM measured
+        # ---- merge: (T + 1) k 8 bytes per point (algorithmic), DRAM measured
         merge_bytes = n * (T + 1) * k * 8
         ach = merge_bytes / (stage_ms["merge"] / 1e3) / 1e9
         mdram = tr["merge_kernel"]["bytes_per_unit"] * n if (traffic and plain and "merge_kernel" in tr) else None
         roof["merge"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                          "traffic": mdram, "algorithmic_bytes_per_launch": merge_bytes}
-        # ---- partition: the survey's depth * n * d * s per tree plus 16 bytes
-        # of keys and permutation per point and level; the rows the kernels
+        # ---- partition: depth * n * d * s per tree plus 16 bytes of keys and
+        # permutation per point and level ("survey bytes"); the rows the kernels
         # read: byte rows once per tree and level (node-major), float rows
         # once per level for all trees (point-major)
         part_survey = T * depth * (n * d * s_el + 16 * n)
