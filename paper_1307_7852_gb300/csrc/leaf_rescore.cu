@@ -27,7 +27,7 @@ namespace knng {
 
 namespace {
 constexpr int kSlice = 32;       // floats per row and slice (one block of the distance)
-constexpr int kMaxCand = 32;     // candidates per row handled here
+constexpr int kMaxCand = 40;     // candidates per row handled here
 }  // namespace
 
 // Canonical block value of a pair: own slice a (columns in the order
@@ -111,14 +111,14 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
     }
     __syncthreads();
     // the pairs this row scores: its candidate is larger, or does not list it
-    uint32_t mine = 0u;
+    uint64_t mine = 0ull;
     if (active) {
 #pragma unroll
         for (int i = 0; i < KC; ++i)
             if (i < want) {
                 const int cc = c[i];
                 const bool listed = (bits[(size_t)cc * 16 + (tid >> 5)] >> (tid & 31)) & 1u;
-                if (cc > tid || !listed) mine |= 1u << i;
+                if (cc > tid || !listed) mine |= 1ull << i;
             }
     }
 
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
             for (int u = 0; u < 8; ++u) a[u] = B[(size_t)tid * 8 + (u ^ x8)];
 #pragma unroll
             for (int i = 0; i < KC; ++i)
-                if ((mine >> i) & 1u) tot[i] = tot[i] + slice_block(a, B + (size_t)c[i] * 8, x8);
+                if ((mine >> i) & 1ull) tot[i] = tot[i] + slice_block(a, B + (size_t)c[i] * 8, x8);
         }
         __syncthreads();  // the buffer of this slice is staged again two slices on
     }
@@ -162,13 +162,13 @@ __global__ void __launch_bounds__(512, 1) leaf_rescore_staged_kernel(
     if (active) {
 #pragma unroll
         for (int i = 0; i < KC; ++i)
-            if ((mine >> i) & 1u) res[(size_t)tid * kp + i] = tot[i];
+            if ((mine >> i) & 1ull) res[(size_t)tid * kp + i] = tot[i];
     }
     __syncthreads();
     if (!active) return;
 #pragma unroll
     for (int i = 0; i < KC; ++i)
-        if (i < want && !((mine >> i) & 1u)) {
+        if (i < want && !((mine >> i) & 1ull)) {
             const int cc = c[i];
             const uint16_t* lc = cand_s + (size_t)cc * kp;
             int j = 0;
@@ -230,10 +230,11 @@ cudaError_t run_leaf_rescore_staged(const XDesc& x, const TreePlan& P, const Dev
     const int nleaves = (int)P.leaf_off.size() - 1;
     const int threads = std::max(32, (P.max_leaf + 31) & ~31);
     const size_t smem = staged_smem(P.max_leaf, kp);
-    // candidate capacity per row: the smallest of 16, 24, 32 holding k'
+    // candidate capacity per row: the smallest of 16, 24, 32, 40 holding k'
     auto kern = kp <= 16 ? leaf_rescore_staged_kernel<16>
               : kp <= 24 ? leaf_rescore_staged_kernel<24>
-                         : leaf_rescore_staged_kernel<32>;
+              : kp <= 32 ? leaf_rescore_staged_kernel<32>
+                         : leaf_rescore_staged_kernel<40>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(nleaves, T), threads, smem, st>>>(static_cast<const float*>(x.X), x.ld, x.d, x.n, perm, dp.leaf_off,
